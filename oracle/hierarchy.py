@@ -1,0 +1,286 @@
+"""Set-up phase of the spectral multigrid preconditioner, FP64.
+
+Test infrastructure only (see the package docstring).
+
+Levels are numbered l = 1 .. n_levels with W_1 = W_h the fine space and
+W_{n_levels} the coarsest (Section 3: W_L c ... c W_1 = W_h).  Elements:
+E_1 partitions the fine grid into boxes of ``block`` cells (the coarse
+elements of Section 3); E_l (l >= 2) groups ``ratio[l-2]`` elements of
+E_{l-1} per direction (coarse-coarse elements and beyond).  W_{l+1} is
+spanned by the ``n_eig[l-1]`` smallest local eigenvectors on every element
+of E_l, and its coordinates are ordered (element of E_l lexicographic, then
+eigenvector index).
+
+Per level the oracle builds:
+* R_l, the restriction with one row per local eigenvector (Section 3),
+* A_{l+1} = R_l A_l R_l^T (Section 3, the Galerkin relations stated before
+  Eq. (B_c)),
+* the smoother M_l: block Jacobi over the elements of E_l; incomplete Cholesky
+  (no fill) of each block on the fine level and exact Cholesky of each block
+  on coarse levels (Section 5 names incomplete Cholesky for both; the exact
+  coarse factor is this build's reading, recorded with the design notes),
+* the Moore-Penrose pseudo-inverse of the coarsest operator (Algorithm 1's
+  A_cc^dagger), dense.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .tpfa import (assemble, face_transmissibilities, interior_face_mask, trace_weight)
+from .spectral import coarse_eigenpairs, element_cells, level1_eigenpairs
+
+
+@dataclass
+class Options:
+    """Hierarchy parameters (Section 5: sd, nu, nu_c, L_c, L_cc generalised to
+    any number of levels)."""
+    n_levels: int = 3
+    block: tuple = (4, 4, 4)                 # E_1 element size in cells (bx, by, bz)
+    ratio: list = field(default_factory=lambda: [(2, 2, 2)])  # E_l, l >= 2, per direction
+    n_eig: list = field(default_factory=lambda: [4, 4])       # L_1 .. L_{n_levels-1}
+    nu: list = field(default_factory=lambda: [1, 1])          # sweeps on levels 1 .. n_levels-1
+    coarse_smoother: str = "chol"            # "chol" (exact block Cholesky) or "ic0"
+
+    def check(self):
+        if self.n_levels < 2:
+            raise ValueError("need at least two levels")
+        if len(self.ratio) < self.n_levels - 2 or len(self.n_eig) < self.n_levels - 1 \
+                or len(self.nu) < self.n_levels - 1:
+            raise ValueError("per-level option lists too short")
+
+
+class BlockIC0:
+    """Block-Jacobi smoother whose blocks are factorised by incomplete Cholesky
+    with no fill (Section 5).  Each block is the diagonal sub-matrix A[c, c] of
+    the global matrix over one element's cells, taken in the element's
+    lexicographic order.  The algorithm is the generic pattern-restricted
+    IC(0): a right-looking Cholesky that drops every update falling outside the
+    block's nonzero pattern.  All blocks share one pattern (same element
+    shape), so the loops run over pattern entries and vectorise over blocks."""
+
+    def __init__(self, A: sp.spmatrix, cells: np.ndarray, box):
+        A = sp.csr_matrix(A)
+        self.cells = cells
+        m, nb = cells.shape
+        bx, by, bz = box
+        # structural pattern of one block: i == j or face neighbours in the box
+        lz, ly, lx = np.unravel_index(np.arange(nb), (bz, by, bx))
+        self.nb = nb
+        lower = [[] for _ in range(nb)]       # lower[i] = columns j < i in row i
+        for i in range(nb):
+            for d, (c, n_c, step) in enumerate(((lx, bx, 1), (ly, by, bx), (lz, bz, bx * by))):
+                if c[i] > 0:
+                    lower[i].append(i - step)
+            lower[i].sort()
+        self.lower = lower
+        upper = [[] for _ in range(nb)]       # upper[j] = rows i > j with (i, j) in pattern
+        for i in range(nb):
+            for j in lower[i]:
+                upper[j].append(i)
+        self.upper = upper
+        pattern = set()
+        for i in range(nb):
+            pattern.add((i, i))
+            for j in lower[i]:
+                pattern.add((i, j))
+        # block values on the pattern, vectorised over blocks
+        W = {}
+        for (i, j) in pattern:
+            W[(i, j)] = np.asarray(A[cells[:, i], cells[:, j]]).ravel().astype(np.float64)
+        # right-looking IC(0) restricted to the pattern
+        for k in range(nb):
+            if np.any(W[(k, k)] <= 0):
+                raise FloatingPointError("IC(0) pivot is not positive")
+            W[(k, k)] = np.sqrt(W[(k, k)])
+            col = upper[k]
+            for i in col:
+                W[(i, k)] = W[(i, k)] / W[(k, k)]
+            for j in col:
+                for i in col:
+                    if i >= j and (i, j) in pattern:
+                        W[(i, j)] = W[(i, j)] - W[(i, k)] * W[(j, k)]
+        self.L = W                            # lower factor on the pattern
+
+    def factor_dense(self, e: int) -> np.ndarray:
+        """Dense lower-triangular factor of block ``e`` (for tests)."""
+        Lm = np.zeros((self.nb, self.nb))
+        for (i, j), v in self.L.items():
+            Lm[i, j] = v[e]
+        return Lm
+
+    def solve(self, r: np.ndarray) -> np.ndarray:
+        """z = M^{-1} r = L^{-T} L^{-1} r on every block (M = L L^T is
+        symmetric, so this is also M^{-T} r)."""
+        rb = r[self.cells]                    # (m, nb)
+        y = np.empty_like(rb)
+        for i in range(self.nb):
+            acc = rb[:, i].copy()
+            for j in self.lower[i]:
+                acc -= self.L[(i, j)] * y[:, j]
+            y[:, i] = acc / self.L[(i, i)]
+        z = np.empty_like(rb)
+        for i in range(self.nb - 1, -1, -1):
+            acc = y[:, i].copy()
+            for j in self.upper[i]:
+                acc -= self.L[(j, i)] * z[:, j]
+            z[:, i] = acc / self.L[(i, i)]
+        out = np.empty_like(r)
+        out[self.cells] = z
+        return out
+
+
+class BlockCholesky:
+    """Block-Jacobi smoother with an exact dense Cholesky factor of each block
+    A[idx, idx] (coarse levels)."""
+
+    def __init__(self, A: sp.spmatrix, dofs: np.ndarray):
+        A = sp.csr_matrix(A)
+        self.dofs = dofs
+        self.factors = []
+        for idx in dofs:
+            blk = A[idx][:, idx].toarray()
+            self.factors.append(sla.cho_factor(0.5 * (blk + blk.T), lower=True))
+
+    def solve(self, r: np.ndarray) -> np.ndarray:
+        out = np.empty_like(r)
+        for idx, f in zip(self.dofs, self.factors):
+            out[idx] = sla.cho_solve(f, r[idx])
+        return out
+
+
+class BlockIC0Dense:
+    """Coarse-level IC(0) option: pattern-restricted incomplete Cholesky of each
+    dense block A[idx, idx], the pattern being the block's nonzeros."""
+
+    def __init__(self, A: sp.spmatrix, dofs: np.ndarray):
+        A = sp.csr_matrix(A)
+        self.dofs = dofs
+        self.factors = []
+        for idx in dofs:
+            blk = A[idx][:, idx].toarray()
+            pat = blk != 0.0
+            n = blk.shape[0]
+            W = np.tril(blk)
+            for k in range(n):
+                if W[k, k] <= 0:
+                    raise FloatingPointError("coarse IC(0) pivot is not positive")
+                W[k, k] = np.sqrt(W[k, k])
+                for i in range(k + 1, n):
+                    if pat[i, k]:
+                        W[i, k] /= W[k, k]
+                for j in range(k + 1, n):
+                    if not pat[j, k]:
+                        continue
+                    for i in range(j, n):
+                        if pat[i, k] and pat[i, j]:
+                            W[i, j] -= W[i, k] * W[j, k]
+            self.factors.append(W)
+
+    def solve(self, r: np.ndarray) -> np.ndarray:
+        out = np.empty_like(r)
+        for idx, Lm in zip(self.dofs, self.factors):
+            y = sla.solve_triangular(Lm, r[idx], lower=True)
+            out[idx] = sla.solve_triangular(Lm.T, y, lower=False)
+        return out
+
+
+@dataclass
+class Hierarchy:
+    opts: Options
+    shape: tuple
+    h: tuple
+    T: np.ndarray                        # (3, nz, ny, nx) face coefficients
+    S: np.ndarray                        # (nz, ny, nx) Tr K~
+    A: list                              # A[l-1] = A_l (sparse), l = 1 .. n_levels
+    R: list                              # R[l-1] = R_l (n_{l+1} x n_l)
+    M: list                              # M[l-1] = smoother of level l, l < n_levels
+    lam: list                            # eigenvalues per level: lam[l-1] (m_l, L_l)
+    basis: list                          # Phi (m_1, L_1, nb) then Psi (m_l, L_l, nP)
+    grids: list                          # element grid (gz, gy, gx) of E_l
+    parent_dofs: list                    # parent_dofs[l-1] (m_l, nP) for l >= 2; None for l = 1
+    coarsest_pinv: np.ndarray            # dense A_L^dagger
+    null_vectors: list                   # null vector of A_l in level-l coordinates
+
+    @property
+    def dims(self):
+        return [a.shape[0] for a in self.A]
+
+
+def setup(kappa, h, opts: Options) -> Hierarchy:
+    """Build every level of the hierarchy from the permeability (Section 3)."""
+    opts.check()
+    kappa = np.asarray(kappa, dtype=np.float64)
+    shape = kappa.shape[-3:]
+    T = face_transmissibilities(kappa, h)
+    S = trace_weight(kappa, h)
+    A1 = assemble(T)
+    nL = opts.n_levels
+
+    # level 1 -> 2: Eq. (spepb) on the elements of E_1
+    lam1, Phi, cells = level1_eigenpairs(T, S, opts.block, opts.n_eig[0])
+    m1, L1, nb = Phi.shape
+    rows = (np.arange(m1)[:, None] * L1 + np.arange(L1)[None, :]).repeat(nb, axis=1).ravel()
+    cols = np.repeat(cells[:, None, :], L1, axis=1).ravel()
+    R1 = sp.csr_matrix((Phi.ravel(), (rows, cols)), shape=(m1 * L1, A1.shape[0]))
+    A = [A1, (R1 @ A1 @ R1.T).tocsr()]
+    R = [R1]
+    lam = [lam1]
+    basis = [Phi]
+    grids = [(shape[0] // opts.block[2], shape[1] // opts.block[1], shape[2] // opts.block[0])]
+    parent_dofs = [None]
+    B = R1.T.tocsr()                          # composed basis of W_2 in fine coordinates
+    fine_box = list(opts.block)
+    s = S.ravel()
+    z = [np.ones(A1.shape[0]), R1 @ s]        # null vector of A_l: R ... R_1 S 1 (Section 3 remark)
+
+    # levels l >= 2: Eq. (spectral cc) on the elements of E_l, posed in W_l
+    for l in range(2, nL):
+        r = opts.ratio[l - 2]
+        g = grids[-1]                          # grid of E_{l-1}
+        if g[2] % r[0] or g[1] % r[1] or g[0] % r[2]:
+            raise ValueError("ratio does not divide the element grid")
+        children = element_cells(g, r)         # (mP, r^3) indices into E_{l-1}
+        Lprev = basis[-1].shape[1]
+        pd = (children[:, :, None] * Lprev + np.arange(Lprev)[None, None, :]).reshape(children.shape[0], -1)
+        fine_box = [fine_box[d] * r[d] for d in range(3)]
+        An = assemble(T * interior_face_mask(shape, fine_box))
+        An_coarse = (B.T @ An @ B).tocsr()
+        lamP, Psi = coarse_eigenpairs(An_coarse, pd, opts.n_eig[l - 1])
+        mP, Ll, nP = Psi.shape
+        rows = (np.arange(mP)[:, None] * Ll + np.arange(Ll)[None, :]).repeat(nP, axis=1).ravel()
+        cols = np.repeat(pd[:, None, :], Ll, axis=1).ravel()
+        Rl = sp.csr_matrix((Psi.ravel(), (rows, cols)), shape=(mP * Ll, A[-1].shape[0]))
+        A.append((Rl @ A[-1] @ Rl.T).tocsr())
+        R.append(Rl)
+        lam.append(lamP)
+        basis.append(Psi)
+        grids.append((g[0] // r[2], g[1] // r[1], g[2] // r[0]))
+        parent_dofs.append(pd)
+        B = (B @ Rl.T).tocsr()
+        z.append(Rl @ z[-1])
+
+    # Block Jacobi over E_l needs at least two elements on every smoothed level:
+    # a single block would be the whole singular operator.
+    for l, g in enumerate(grids, start=1):
+        if g[0] * g[1] * g[2] < 2:
+            raise ValueError(f"level {l} has a single element; its smoother block would be singular")
+
+    # smoothers: block Jacobi over E_l on level l (Section 5)
+    M = [BlockIC0(A1, cells, opts.block)]
+    for l in range(2, nL):
+        pd = parent_dofs[l - 1]
+        if opts.coarse_smoother == "chol":
+            M.append(BlockCholesky(A[l - 1], pd))
+        else:
+            M.append(BlockIC0Dense(A[l - 1], pd))
+
+    # coarsest: Moore-Penrose pseudo-inverse (Algorithm 1, A_cc^dagger)
+    Ac = A[-1].toarray()
+    Ac = 0.5 * (Ac + Ac.T)
+    pinv = np.linalg.pinv(Ac, rcond=1e-13, hermitian=True)
+    return Hierarchy(opts, tuple(shape), tuple(h), T, S, A, R, M, lam, basis, grids,
+                     parent_dofs, pinv, z)

@@ -1,0 +1,242 @@
+"""Pins for the oracle's hierarchy: Galerkin operators against face-by-face
+constructions, the null vector and S-orthonormality of Section 3, the
+level-2 local operator by an independent (recursive face-term) route,
+piecewise-constant aggregation for L = 1, the IC(0) one-pivot identity and
+the pseudo-inverse."""
+import numpy as np
+import pytest
+
+import oracle
+
+
+def make(shape=(8, 8, 8), box=(2, 2, 2), L=(3, 4), n_levels=3, seed=1, sigma=2.0, comps=3):
+    rng = np.random.default_rng(seed)
+    kap = np.exp(rng.normal(0, sigma, size=(comps,) + shape))
+    h = (1.0 / shape[2], 1.0 / shape[1], 1.0 / shape[0])
+    opts = oracle.Options(n_levels=n_levels, block=box, ratio=[(2, 2, 2)] * (n_levels - 2),
+                          n_eig=list(L), nu=[1] * (n_levels - 1))
+    return oracle.setup(kap, h, opts), kap, h
+
+
+def boundary_diag(T, shape, box):
+    """For every cell: sum of the coefficients of its faces that cross the
+    boundary of its element (computed face by face)."""
+    nz, ny, nx = shape
+    D = np.zeros(shape)
+    bx, by, bz = box
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                for d, (di, dj, dk, c, b) in enumerate(((1, 0, 0, i, bx), (0, 1, 0, j, by), (0, 0, 1, k, bz))):
+                    # + face
+                    if (c + 1) % b == 0:
+                        D[k, j, i] += T[d, k, j, i]
+                    # - face
+                    if c % b == 0 and c > 0:
+                        D[k, j, i] += T[d, k - dk, j - dj, i - di]
+    return D.ravel()
+
+
+def test_dimensions():
+    H, _, _ = make()
+    assert H.dims == [512, 64 * 3, 8 * 4]
+
+
+def test_galerkin_diagonal_block_identity():
+    # diagonal block of A_2 = Lambda_a + Phi_a^T D_a Phi_a, D_a = faces crossing the element boundary
+    H, kap, h = make()
+    D = boundary_diag(H.T, H.shape, H.opts.block)
+    Phi, cells = H.basis[0], oracle.element_cells(H.shape, H.opts.block)
+    A2 = H.A[1].toarray()
+    L = Phi.shape[1]
+    for e in range(cells.shape[0]):
+        V = Phi[e]
+        ref = np.diag(H.lam[0][e]) + V @ (D[cells[e]][:, None] * V.T)
+        np.testing.assert_allclose(A2[e * L:(e + 1) * L, e * L:(e + 1) * L], ref,
+                                   atol=1e-10 * np.abs(ref).max())
+
+
+def test_galerkin_off_diagonal_face_sum():
+    # A_2[a, b] = - sum over faces (c in a, c' in b) of T_f Phi_a(c) Phi_b(c')^T
+    H, kap, h = make()
+    nz, ny, nx = H.shape
+    bx, by, bz = H.opts.block
+    ex, ey, ez = nx // bx, ny // by, nz // bz
+    Phi = H.basis[0]
+    L = Phi.shape[1]
+    A2 = H.A[1].toarray()
+    cells = oracle.element_cells(H.shape, H.opts.block)
+    pos = {int(c): (e, p) for e in range(cells.shape[0]) for p, c in enumerate(cells[e])}
+    for a in [0, 5, 17, 40]:
+        ax, ay, az = a % ex, (a // ex) % ey, a // (ex * ey)
+        for d, (dx, dy, dz) in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+            if ax + dx >= ex or ay + dy >= ey or az + dz >= ez:
+                continue
+            b = (ax + dx) + ex * ((ay + dy) + ey * (az + dz))
+            ref = np.zeros((L, L))
+            stride = (1, nx, nx * ny)[d]
+            for c in cells[a]:
+                c2 = c + stride
+                e2, p2 = pos.get(int(c2), (None, None))
+                if e2 != b:
+                    continue
+                k, j, i = np.unravel_index(c, H.shape)
+                t = H.T[d, k, j, i]
+                _, p = pos[int(c)]
+                ref -= t * np.outer(Phi[a][:, p], Phi[b][:, p2])
+            np.testing.assert_allclose(A2[a * L:(a + 1) * L, b * L:(b + 1) * L], ref,
+                                       atol=1e-10 * np.abs(A2).max())
+    # non-adjacent elements do not couple
+    assert np.abs(A2[0:L, 2 * L:3 * L]).max() == 0.0
+
+
+def test_constant_lies_in_every_coarse_space():
+    # Section 3: the smallest eigenvalue is zero with a constant eigenvector, so the
+    # kernel of A is contained in every W_l; z_l = R_{l-1}..R_1 S 1 spans null(A_l)
+    H, _, _ = make(n_levels=4, shape=(8, 8, 16), box=(2, 2, 2), L=(3, 4, 3))
+    B = np.eye(H.dims[0])
+    for l in range(1, H.opts.n_levels):
+        B = B @ H.R[l - 1].T.toarray()
+        z = H.null_vectors[l]
+        np.testing.assert_allclose(B @ z, 1.0, atol=1e-10)
+        Az = H.A[l] @ z
+        assert np.abs(Az).max() < 1e-10 * abs(H.A[l]).max()
+
+
+def test_composed_basis_is_s_orthonormal():
+    # Section 3: with S-normalised level-1 vectors the right-hand matrix of every
+    # higher-level problem is the identity
+    H, _, _ = make(n_levels=4, shape=(8, 8, 16), L=(3, 4, 3))
+    s = H.S.ravel()
+    B = np.eye(H.dims[0])
+    for l in range(1, H.opts.n_levels):
+        B = B @ H.R[l - 1].T.toarray()
+        np.testing.assert_allclose(B.T @ (s[:, None] * B), np.eye(B.shape[1]), atol=1e-11)
+
+
+def test_level2_operator_by_recursive_face_terms():
+    # Independent route to the left matrix of Eq. (spectral cc) on each parent P:
+    # children blocks Lambda_a + sum over a's faces inside P of Phi_a^T diag(T_face) Phi_a,
+    # sibling blocks = A_2[a, b].  Its smallest eigenvalues must equal the oracle's.
+    H, kap, h = make()
+    nz, ny, nx = H.shape
+    bx, by, bz = H.opts.block
+    ex, ey, ez = nx // bx, ny // by, nz // bz
+    Phi = H.basis[0]
+    L = Phi.shape[1]
+    cells = oracle.element_cells(H.shape, H.opts.block)
+    A2 = H.A[1].toarray()
+    pdofs = H.parent_dofs[1]
+    for P in range(pdofs.shape[0]):
+        children = pdofs[P][::L] // L
+        N = A2[np.ix_(pdofs[P], pdofs[P])].copy()
+        for ci, a in enumerate(children):
+            ax, ay, az = a % ex, (a // ex) % ey, a // (ex * ey)
+            blk = np.diag(H.lam[0][a]).copy()
+            for c_idx, c in enumerate(cells[a]):
+                k, j, i = np.unravel_index(c, H.shape)
+                li, lj, lk = i - ax * bx, j - ay * by, k - az * bz
+                for d, (cc, b, ec) in enumerate(((li, bx, ax), (lj, by, ay), (lk, bz, az))):
+                    # + face of a at this cell: inside P iff the neighbour element is a sibling
+                    if cc == b - 1 and ec % 2 == 0:
+                        blk += H.T[d, k, j, i] * np.outer(Phi[a][:, c_idx], Phi[a][:, c_idx])
+                    if cc == 0 and ec % 2 == 1:
+                        kk, jj, ii = (k, j, i - 1) if d == 0 else ((k, j - 1, i) if d == 1 else (k - 1, j, i))
+                        blk += H.T[d, kk, jj, ii] * np.outer(Phi[a][:, c_idx], Phi[a][:, c_idx])
+            N[ci * L:(ci + 1) * L, ci * L:(ci + 1) * L] = blk
+        w = np.linalg.eigvalsh(0.5 * (N + N.T))
+        np.testing.assert_allclose(w[:H.lam[1].shape[1]], H.lam[1][P], atol=1e-9 * max(1.0, abs(w).max()))
+
+
+def test_single_eigenvector_is_aggregation():
+    # L_1 = 1: W_2 is piecewise constant; Phi_e = c_e 1 with c_e = (sum_K S)^(-1/2) and
+    # A_2[a, b] = -c_a c_b * (sum of face coefficients between a and b)
+    H, kap, h = make(L=(1, 1), n_levels=3)
+    cells = oracle.element_cells(H.shape, H.opts.block)
+    s = H.S.ravel()
+    c = 1.0 / np.sqrt(s[cells].sum(axis=1))
+    np.testing.assert_allclose(np.abs(H.basis[0][:, 0, :]), c[:, None] * np.ones(cells.shape[1]), rtol=1e-10)
+    sign = np.sign(H.basis[0][:, 0, 0])
+    A2 = H.A[1].toarray() * np.outer(sign, sign)
+    nz, ny, nx = H.shape
+    elem_of = np.empty(nx * ny * nz, dtype=int)
+    for e in range(cells.shape[0]):
+        elem_of[cells[e]] = e
+    ref = np.zeros_like(A2)
+    for d, stride in enumerate((1, nx, nx * ny)):
+        t = H.T[d].ravel()
+        for cidx in np.nonzero(t)[0]:
+            a, b = elem_of[cidx], elem_of[cidx + stride]
+            if a != b:
+                ref[a, b] -= t[cidx] * c[a] * c[b]
+                ref[b, a] -= t[cidx] * c[a] * c[b]
+                ref[a, a] += t[cidx] * c[a] * c[a]     # Phi_a^T A Phi_a: faces leaving a
+                ref[b, b] += t[cidx] * c[b] * c[b]
+    np.testing.assert_allclose(A2, ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_ic0_one_pivot_form():
+    # IC(0) of a 7-point block in natural order has no fill: L_ij = a_ij / sqrt(d_j),
+    # L_ii = sqrt(d_i), d_i = a_ii - sum_{j<i, j~i} a_ij^2 / d_j; and L L^T = A on the pattern
+    H, _, _ = make(shape=(8, 8, 16), box=(4, 4, 4), L=(4, 4))
+    M = H.M[0]
+    cells = M.cells
+    A = H.A[0].toarray()
+    for e in [0, 3, 7]:
+        Ab = A[np.ix_(cells[e], cells[e])]
+        nb = Ab.shape[0]
+        d = np.zeros(nb)
+        for i in range(nb):
+            d[i] = Ab[i, i] - sum(Ab[i, j] ** 2 / d[j] for j in range(i) if Ab[i, j] != 0)
+        Lm = M.factor_dense(e)
+        np.testing.assert_allclose(np.diag(Lm) ** 2, d, rtol=1e-12)
+        off = np.tril(Ab, -1)
+        mask = off != 0
+        np.testing.assert_allclose(Lm[mask], (off / np.sqrt(d)[None, :])[mask], rtol=1e-12)
+        LLt = Lm @ Lm.T
+        pat = Ab != 0
+        np.testing.assert_allclose(LLt[pat], Ab[pat], rtol=1e-11, atol=1e-12 * np.abs(Ab).max())
+
+
+def test_coarse_block_cholesky_inverts_blocks():
+    H, _, _ = make()
+    M = H.M[1]
+    A2 = H.A[1].toarray()
+    for P in range(3):
+        idx = H.parent_dofs[1][P]
+        e = np.zeros(A2.shape[0])
+        for col in range(4):
+            e[:] = 0
+            e[idx[col]] = 1.0
+            z = M.solve(e)
+            np.testing.assert_allclose(A2[np.ix_(idx, idx)] @ z[idx], e[idx], atol=1e-10)
+
+
+def test_pseudo_inverse():
+    H, _, _ = make()
+    Ac = H.A[-1].toarray()
+    z = H.null_vectors[-1]
+    zh = z / np.linalg.norm(z)
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(Ac.shape[0])
+    r -= zh * (zh @ r)
+    x = H.coarsest_pinv @ r
+    np.testing.assert_allclose(Ac @ x, r, atol=1e-9 * np.linalg.norm(r))
+    assert abs(zh @ x) < 1e-10 * np.linalg.norm(x)
+    # Moore-Penrose: pinv annihilates the null vector
+    assert np.linalg.norm(H.coarsest_pinv @ zh) < 1e-8 * np.linalg.norm(H.coarsest_pinv)
+
+
+def test_coarse_ic0_option_runs():
+    rng = np.random.default_rng(1)
+    kap = np.exp(rng.normal(0, 1, size=(8, 8, 8)))
+    opts = oracle.Options(n_levels=3, block=(2, 2, 2), ratio=[(2, 2, 2)], n_eig=[2, 3], nu=[1, 1],
+                          coarse_smoother="ic0")
+    H = oracle.setup(kap, (1 / 8,) * 3, opts)
+    res = oracle.solve(H, np.r_[1.0, np.zeros(510), -1.0], 1e-8)
+    assert res.converged
+
+
+def test_single_element_level_is_rejected():
+    with pytest.raises(ValueError):
+        make(shape=(8, 8, 8), box=(4, 4, 4), L=(4, 4))

@@ -1,0 +1,126 @@
+"""Pins for the oracle's V-cycle and PCG: the closed-form operators of
+Eq. (B_ITG) and Eq. (B_c), the eigenvalue bound of Section 4, the full-space
+special case, an exact cosine solution and a dense least-squares solve."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import oracle
+
+
+def make(shape=(8, 8, 8), box=(2, 2, 2), L=(3, 4), n_levels=3, seed=4, sigma=2.0):
+    rng = np.random.default_rng(seed)
+    kap = np.exp(rng.normal(0, sigma, size=shape))
+    h = (1.0 / shape[2], 1.0 / shape[1], 1.0 / shape[0])
+    opts = oracle.Options(n_levels=n_levels, block=box, ratio=[(2, 2, 2)] * (n_levels - 2),
+                          n_eig=list(L), nu=[1] * (n_levels - 1))
+    return oracle.setup(kap, h, opts)
+
+
+def dense_op(apply, n):
+    return np.column_stack([apply(np.eye(n)[:, j]) for j in range(n)])
+
+
+def test_vcycle_matches_closed_form_three_grid_operator():
+    # Eq. (B_c): B_c^{-1} = Mc^-T + Mc^-1 - Mc^-T Ac Mc^-1 + (I - Mc^-T Ac) Rcc^T Acc^+ Rcc (I - Ac Mc^-1)
+    # Eq. (B_ITG): P^{-1} = M^-T + M^-1 - M^-T A M^-1 + (I - M^-T A) Rc^T B_c^{-1} Rc (I - A M^-1)
+    H = make()
+    n, nc = H.dims[0], H.dims[1]
+    A, Ac = H.A[0].toarray(), H.A[1].toarray()
+    Rc, Rcc = H.R[0].toarray(), H.R[1].toarray()
+    Mi = dense_op(H.M[0].solve, n)
+    Mci = dense_op(H.M[1].solve, nc)
+    Ic, I = np.eye(nc), np.eye(n)
+    Bc = Mci.T + Mci - Mci.T @ Ac @ Mci + (Ic - Mci.T @ Ac) @ Rcc.T @ H.coarsest_pinv @ Rcc @ (Ic - Ac @ Mci)
+    P = Mi.T + Mi - Mi.T @ A @ Mi + (I - Mi.T @ A) @ Rc.T @ Bc @ Rc @ (I - A @ Mi)
+    V = dense_op(lambda r: oracle.vcycle(H, r), n)
+    np.testing.assert_allclose(V, P, atol=1e-9 * np.abs(P).max())
+
+
+@pytest.mark.parametrize("n_levels,L", [(2, (3,)), (3, (3, 4)), (4, (2, 3, 3))])
+def test_preconditioned_spectrum_in_unit_interval(n_levels, L):
+    # Section 4: lambda_max(P^{-1} A) <= 1 (exact two-grid: = 1; the inexact cycle stays
+    # below by induction) and lambda_min > 0 on range(A)
+    H = make(n_levels=n_levels, L=L, shape=(8, 8, 16) if n_levels == 4 else (8, 8, 8))
+    n = H.dims[0]
+    A = H.A[0].toarray()
+    V = dense_op(lambda r: oracle.vcycle(H, r), n)
+    np.testing.assert_allclose(V, V.T, atol=1e-9 * np.abs(V).max())
+    Q = np.linalg.qr(np.c_[np.ones(n), np.eye(n)[:, :n - 1]])[0][:, 1:]   # basis of range(A)
+    # eigenvalues of V A restricted to range(A): similar to V^{1/2} A V^{1/2}
+    Vr = Q.T @ V @ Q
+    Ar = Q.T @ A @ Q
+    C = np.linalg.cholesky(0.5 * (Vr + Vr.T))
+    w = np.linalg.eigvalsh(C.T @ Ar @ C)
+    assert w[-1] <= 1.0 + 1e-9
+    assert w[0] > 1e-6
+    if n_levels == 2:
+        assert w[-1] == pytest.approx(1.0, abs=1e-8)   # lambda_max(P_TG^{-1} A) = 1
+
+
+def test_full_space_two_grid_is_exact():
+    # L_1 = number of cells per element: W_2 = W_h, the two-grid cycle is A^dagger
+    H = make(shape=(4, 4, 4), box=(2, 2, 2), L=(8,), n_levels=2)
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(64)
+    res = oracle.solve(H, b, rtol=1e-10)
+    assert res.iterations == 1
+    x_ref = np.linalg.lstsq(H.A[0].toarray(), b - b.mean(), rcond=None)[0]
+    np.testing.assert_allclose(res.x, x_ref - x_ref.mean(), atol=1e-9 * np.abs(x_ref).max())
+
+
+def test_cosine_rhs_exact_solution():
+    # kappa = 1: a DCT-II mode f is an eigenvector of A, so x = f / lambda exactly
+    N = 8
+    shape = (N, N, N)
+    opts = oracle.Options(n_levels=3, block=(2, 2, 2), ratio=[(2, 2, 2)], n_eig=[4, 4], nu=[1, 1])
+    H = oracle.setup(np.ones(shape), (1 / N,) * 3, opts)
+    k = np.arange(N)
+    f = (np.cos(np.pi * 3 * (k[None, None, :] + 0.5) / N) * np.cos(np.pi * 1 * (k[:, None, None] + 0.5) / N)
+         * np.ones((1, N, 1))).ravel()
+    lam = N * N * 2 * (1 - np.cos(3 * np.pi / N)) + N * N * 2 * (1 - np.cos(np.pi / N))
+    res = oracle.solve(H, f, rtol=1e-12)
+    np.testing.assert_allclose(res.x, f / lam, atol=1e-11 * np.abs(f / lam).max())
+
+
+def test_unpreconditioned_pcg_matches_library_cg_and_lstsq():
+    H = make()
+    A = H.A[0]
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal(A.shape[0])
+    res = oracle.pcg(A, b, None, rtol=1e-10, max_iter=2000)
+    bb = b - b.mean()
+    x_ref = np.linalg.lstsq(A.toarray(), bb, rcond=None)[0]
+    x_ref -= x_ref.mean()
+    np.testing.assert_allclose(res.x, x_ref, atol=1e-7 * np.abs(x_ref).max())
+    assert res.rhs_mean == pytest.approx(b.mean())
+    # the same iterates as a library CG on the same system: compare the solution at
+    # a fixed iteration count
+    k = 15
+    r1 = oracle.pcg(A, bb, None, rtol=0.0, max_iter=k)
+    x_lib, _ = spla.cg(A, bb, rtol=0.0, atol=0.0, maxiter=k)
+    np.testing.assert_allclose(r1.x, x_lib - x_lib.mean(), atol=1e-9 * np.abs(x_lib).max())
+
+
+def test_mean_removed_and_solution_zero_mean():
+    H = make()
+    b = np.ones(H.dims[0])
+    b[0] += 5.0
+    res = oracle.solve(H, b, rtol=1e-10)
+    assert abs(res.x.mean()) < 1e-14 * np.abs(res.x).max()
+    assert res.rhs_mean == pytest.approx(b.mean())
+    assert np.linalg.norm((b - b.mean()) - H.A[0] @ res.x) <= 1e-10 * np.linalg.norm(b - b.mean()) * 1.01
+
+
+def test_more_coarse_vectors_fewer_iterations():
+    # Section 5.2 trend: enlarging the coarse-coarse space lowers the iteration count
+    rng = np.random.default_rng(9)
+    kap = np.where(rng.random((16, 16, 16)) < 0.2, 1e5, 1.0)
+    its = []
+    for Lcc in (1, 4, 8):
+        opts = oracle.Options(n_levels=3, block=(4, 4, 4), ratio=[(2, 2, 2)], n_eig=[8, Lcc], nu=[1, 1])
+        H = oracle.setup(kap, (1 / 16,) * 3, opts)
+        b = np.zeros(4096)
+        b[0], b[-1] = 1.0, -1.0
+        its.append(oracle.solve(H, b, 1e-8).iterations)
+    assert its[0] >= its[1] >= its[2]
