@@ -1,0 +1,216 @@
+/*
+ * msmg -- spectral multiscale multigrid PCG for the cell-centred Darcy
+ * pressure system, for NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2403.19342, "An efficient multiscale multigrid preconditioner
+ * for Darcy flow in high-contrast media".
+ *   - fine operator: the two-point-flux matrix A = B M_t^{-1} B^T obtained from
+ *     lowest-order Raviart-Thomas with trapezoidal quadrature (Section 2.2,
+ *     Eq. (p), Eq. (discrete varia)); face coefficients are harmonic averages
+ *     of the normalised permeability kappa^d / h_d^2 (Fig. (kappa edge));
+ *     boundary faces carry nothing (no-flow, Eq. (ell2));
+ *   - nested spaces W_L c ... c W_1 = W_h spanned by the smallest eigenvectors
+ *     of local spectral problems on non-overlapping elements (Section 3,
+ *     Eq. (spepb) on level 1, Eq. (spectral cc) on higher levels);
+ *   - Galerkin operators A_{l+1} = R_l A_l R_l^T, block-Jacobi smoothers and a
+ *     coarsest pseudo-inverse, applied as a V-cycle (Algorithm 1, recursive);
+ *   - preconditioned conjugate gradients on A p = f.
+ *
+ * Conventions for every call:
+ *   - Cell order is i + nx*(j + ny*k) with i fastest ("natural order").
+ *   - Pointers are DEVICE pointers unless a call or flag says otherwise.  The
+ *     caller owns every buffer, including the workspace given to msmg_setup;
+ *     the library allocates no device memory and owns only the opaque context.
+ *   - Work is enqueued on the caller's stream; calls that return data to the
+ *     host (info structs) synchronise that stream.
+ *   - Return value: 0 success, > 0 warning, < 0 error (msmg_status_string).
+ *   - Calls on one context are not thread-safe; distinct contexts are
+ *     independent.
+ */
+#ifndef MSMG_H
+#define MSMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* msmg_stream;        /* same handle as cudaStream_t */
+typedef struct msmg_ctx msmg_ctx;                /* opaque, owned by the library */
+
+#define MSMG_MAX_LEVELS 8
+
+/* status codes */
+#define MSMG_OK                      0
+#define MSMG_NOT_CONVERGED           1   /* warning: max_iter reached            */
+#define MSMG_ERR_INVALID_ARG        -1
+#define MSMG_ERR_NOT_DIVISIBLE      -2   /* element sizes do not tile the grid   */
+#define MSMG_ERR_BAD_KAPPA          -3   /* non-positive or non-finite kappa     */
+#define MSMG_ERR_SINGLE_BLOCK       -4   /* a smoothed level has one element     */
+#define MSMG_ERR_BREAKDOWN          -5   /* PCG: p^T A p <= 0 or non-finite      */
+#define MSMG_ERR_EIG_NOT_CONVERGED  -6   /* local eigensolve missed eig_tol      */
+#define MSMG_ERR_WORKSPACE          -7   /* workspace too small or misaligned    */
+#define MSMG_ERR_CUDA               -8
+#define MSMG_ERR_NOT_FACTORIZABLE   -9   /* a smoother or coarsest factor failed */
+#define MSMG_ERR_UNSUPPORTED       -10
+
+/* precision modes */
+#define MSMG_FP64   0   /* every step in FP64                                           */
+#define MSMG_MIXED  1   /* FP32 fine-level V-cycle (BF16 bases), FP64 coarse levels,    */
+                        /* coarsest solve, eigenbasis orthonormalisation and outer PCG  */
+
+/* kappa element types */
+#define MSMG_F64 0
+#define MSMG_F32 1
+
+/* msmg_solve flags */
+#define MSMG_FLAG_X0        1   /* x holds an initial guess on entry (warm start)     */
+#define MSMG_FLAG_HOST_IO   2   /* rhs and x are HOST pointers (pinned for speed);    */
+                                /* the copies run on the stream inside the call       */
+#define MSMG_FLAG_NO_GRAPH  4   /* launch the PCG iteration kernel by kernel           */
+
+typedef struct {
+    int nx, ny, nz;        /* fine cells per direction                     */
+    double hx, hy, hz;     /* cell sizes (the paper's unit cube: 1/n)      */
+} msmg_grid;
+
+typedef struct {
+    int n_levels;                      /* number of spaces, >= 2: W_{n_levels} c ... c W_1 = W_h     */
+    int block[3];                      /* level-1 element (coarse element) size in cells, x y z     */
+    int ratio[MSMG_MAX_LEVELS][3];     /* ratio[i]: elements of level i+1 per element of level i+2,  */
+                                       /* per direction, i = 0 .. n_levels-3 (sd in Section 5)       */
+    int n_eig[MSMG_MAX_LEVELS];        /* n_eig[i]: eigenvectors per element of level i+1, i.e. the */
+                                       /* dimension of each local space of W_{i+2} (L_c, L_cc)      */
+    int nu[MSMG_MAX_LEVELS];           /* nu[i]: smoothing sweeps on W_{i+1} (nu, nu_c)              */
+    int precision;                     /* MSMG_FP64 or MSMG_MIXED                                    */
+    double eig_tol;                    /* local eigen-residual tolerance (see msmg_setup)            */
+    int eig_max_iter;                  /* cap on subspace iterations per element (0: default 200)    */
+} msmg_options;
+
+typedef struct {
+    int n_levels;
+    int64_t dims[MSMG_MAX_LEVELS];     /* dim W_l, l = 1 .. n_levels                     */
+    int64_t elements[MSMG_MAX_LEVELS]; /* number of elements of E_l, l = 1 .. n_levels-1 */
+    double setup_ms;                   /* device time of msmg_setup                      */
+    double eig_ms;                     /* of which level-1 eigensolves                   */
+    int eig_iterations_max;            /* subspace iterations of the slowest element     */
+    double eig_residual_max;           /* largest final eigen-residual (level 1)         */
+    int64_t workspace_bytes;
+} msmg_setup_info;
+
+typedef struct {
+    int iterations;                    /* PCG iterations performed                       */
+    int converged;
+    double rel_residual;               /* ||b - A x||_2 / ||b||_2, recurrence residual    */
+    double true_rel_residual;          /* recomputed from x at exit                      */
+    double rhs_mean;                   /* mean removed from the right-hand side          */
+    double solve_ms;                   /* device time of the solve                       */
+} msmg_solve_info;
+
+/*
+ * Workspace bytes needed by msmg_setup for this grid and hierarchy, and for
+ * solves of up to n_rhs right-hand sides per call.  Returns
+ * MSMG_ERR_NOT_DIVISIBLE / MSMG_ERR_INVALID_ARG / MSMG_ERR_SINGLE_BLOCK for a
+ * hierarchy that cannot be built (block must divide the grid, each ratio
+ * must divide the element grid below it, every level below the coarsest must
+ * have at least two elements, 1 <= n_eig <= dofs per local problem).
+ */
+int msmg_workspace_size(const msmg_grid* grid, const msmg_options* opts, int n_rhs, size_t* bytes);
+
+/*
+ * Set-up phase (Section 3 and Section 5): face coefficients (Section 2.2),
+ * level-1 local generalised eigenproblems A_K Phi = lambda S_K Phi with
+ * S_K = diag(Tr K~) (Eq. (spepb)), S-orthonormal bases, Galerkin operators,
+ * level-l problems in the coarse space (Eq. (spectral cc), right matrix = I),
+ * smoother factors and the coarsest pseudo-inverse.
+ *
+ *   kappa            device, kappa_components x (nx*ny*nz) values, component-major,
+ *                    natural cell order; 1 component = isotropic, 3 = (kx, ky, kz)
+ *   kappa_dtype      MSMG_F64 or MSMG_F32
+ *   workspace        device, >= msmg_workspace_size bytes, 256-byte aligned; must stay
+ *                    allocated and untouched until msmg_destroy
+ *   out              receives the new context
+ * eig_tol bounds || A~ y - theta y ||_2 for each kept eigenvector y (||y||_2 = 1) of the
+ * symmetric form A~ = S^{-1/2} A_K S^{-1/2}, whose spectrum lies in [0, 8].  Errors:
+ * MSMG_ERR_BAD_KAPPA (kappa <= 0 or not finite), MSMG_ERR_EIG_NOT_CONVERGED (an element
+ * missed eig_tol within eig_max_iter; the context is still created and usable),
+ * MSMG_ERR_NOT_FACTORIZABLE, plus those of msmg_workspace_size.
+ */
+int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, int kappa_dtype,
+               const msmg_options* opts, void* workspace, size_t workspace_bytes,
+               msmg_stream stream, msmg_ctx** out);
+
+/*
+ * PCG solve of A x = rhs (Eq. (p)) preconditioned by one V-cycle per iteration.
+ *   rhs, x     n_rhs x (nx*ny*nz) FP64 values, natural order, one system after another;
+ *              device pointers unless MSMG_FLAG_HOST_IO
+ *   rtol       stop when ||b - A x_k||_2 <= rtol ||b||_2 (b = rhs with its mean removed,
+ *              the compatibility condition of Section 2.1)
+ *   max_iter   iteration cap (MSMG_NOT_CONVERGED when reached)
+ *   info       host struct, per system: n_rhs entries (may be NULL)
+ * x is returned with zero mean (Section 2.1).  In MSMG_MIXED the V-cycle runs in FP32
+ * and the outer recurrence in FP64 with the flexible (Polak-Ribiere) beta.  Errors:
+ * MSMG_ERR_BREAKDOWN, MSMG_ERR_INVALID_ARG (n_rhs above the workspace's).
+ */
+int msmg_solve(msmg_ctx* ctx, const double* rhs, double* x, int n_rhs, double rtol, int max_iter,
+               int flags, msmg_stream stream, msmg_solve_info* info);
+
+/* q = A p, FP64, natural order (Eq. (discrete varia)). */
+int msmg_apply_A(msmg_ctx* ctx, const double* p, double* q, msmg_stream stream);
+
+/* z = P^{-1} r: one V-cycle from zero (Algorithm 1 generalised), natural order. */
+int msmg_apply_precond(msmg_ctx* ctx, const double* r, double* z, msmg_stream stream);
+
+/* Deterministic FP64 dot product of two device vectors of length n with the PCG's
+ * grid-reduction kernel (per-CTA partial sums added in CTA order by the last CTA).
+ *   scratch      device, >= msmg_dot_scratch_bytes(n) bytes, 16-byte aligned, owned by the
+ *                caller; its contents are overwritten (the call clears what it needs)
+ *   result_host  host; the call synchronises the stream */
+size_t msmg_dot_scratch_bytes(int64_t n);
+int msmg_dot(const double* a, const double* b, int64_t n, void* scratch, double* result_host, msmg_stream stream);
+
+/*
+ * Level data in the layouts of the paper's matrices (for parity checks).
+ * level l = 1 .. n_levels-1.  Elements of E_l are in lexicographic order (x fastest) of
+ * the element grid; the dofs of a level-l local problem are its child elements in
+ * lexicographic order inside the parent, each child's n_eig[l-2] values contiguous
+ * (l >= 2), or its cells in lexicographic order inside the element (l = 1).
+ *   basis   device, m_l x n_eig[l-1] x (dofs per local problem) FP64: level 1 = Phi
+ *           (S-orthonormal), level >= 2 = Psi (orthonormal)
+ *   lam     device, m_l x n_eig[l-1] eigenvalues (may be NULL)
+ */
+int msmg_export_basis(msmg_ctx* ctx, int level, double* basis, double* lam, msmg_stream stream);
+
+/*
+ * Replace the local eigenbases with the given ones (same layout as export) and rebuild
+ * every quantity that depends on them (Galerkin operators, coarse smoothers, the
+ * coarsest pseudo-inverse).  Bases for levels 1 .. n_levels-1 in one call:
+ * bases[l-1] points to level l's array.
+ */
+int msmg_import_bases(msmg_ctx* ctx, const double* const* bases, msmg_stream stream);
+
+/*
+ * Dense FP64 copy of the Galerkin operator A_l (l = 2 .. n_levels) in the coordinate
+ * order of the paper's R_l: (element of E_{l-1} in lexicographic order, eigenvector).
+ * out: device, dim(W_l)^2 values, row-major.  Intended for small grids.
+ */
+int msmg_export_operator(msmg_ctx* ctx, int level, double* out, msmg_stream stream);
+
+/* Face coefficients T[d][cell] (d = x, y, z; face between cell and its +d neighbour,
+ * zero on the boundary), FP64, natural order: device, 3 x (nx*ny*nz). */
+int msmg_export_faces(msmg_ctx* ctx, double* T, msmg_stream stream);
+
+int msmg_get_setup_info(msmg_ctx* ctx, msmg_setup_info* info);
+void msmg_destroy(msmg_ctx* ctx);
+const char* msmg_status_string(int status);
+
+/* Measured plain-ALU FMA throughput of this GPU (TFLOP/s), for roofline denominators of
+ * ALU-bound kernels: a short in-register FMA loop timed with CUDA events. */
+int msmg_probe_alu_peaks(double* fp64_tflops, double* fp32_tflops, msmg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSMG_H */

@@ -1,0 +1,353 @@
+"""Python binding of libmsmg (include/msmg.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers and streams, and raises on error statuses.  There
+is no CPU fallback: importing works without a GPU, but every call that
+reaches the library needs libmsmg.so (built by ``build.build()``) and a CUDA
+device, and fails loudly otherwise.
+
+The functions carry the C entry points' names (``msmg_setup``,
+``msmg_solve``, ...).  ``Solver`` bundles them with workspace management.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmsmg.so")
+
+MAX_LEVELS = 8
+FP64, MIXED = 0, 1
+F64, F32 = 0, 1
+FLAG_X0, FLAG_HOST_IO, FLAG_NO_GRAPH = 1, 2, 4
+
+STATUS = {
+    0: "MSMG_OK", 1: "MSMG_NOT_CONVERGED", -1: "MSMG_ERR_INVALID_ARG", -2: "MSMG_ERR_NOT_DIVISIBLE",
+    -3: "MSMG_ERR_BAD_KAPPA", -4: "MSMG_ERR_SINGLE_BLOCK", -5: "MSMG_ERR_BREAKDOWN",
+    -6: "MSMG_ERR_EIG_NOT_CONVERGED", -7: "MSMG_ERR_WORKSPACE", -8: "MSMG_ERR_CUDA",
+    -9: "MSMG_ERR_NOT_FACTORIZABLE", -10: "MSMG_ERR_UNSUPPORTED",
+}
+
+
+class MsmgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class msmg_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double)]
+
+
+class msmg_options(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("block", C.c_int * 3), ("ratio", (C.c_int * 3) * MAX_LEVELS),
+                ("n_eig", C.c_int * MAX_LEVELS), ("nu", C.c_int * MAX_LEVELS), ("precision", C.c_int),
+                ("eig_tol", C.c_double), ("eig_max_iter", C.c_int)]
+
+
+class msmg_setup_info(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("dims", C.c_int64 * MAX_LEVELS), ("elements", C.c_int64 * MAX_LEVELS),
+                ("setup_ms", C.c_double), ("eig_ms", C.c_double), ("eig_iterations_max", C.c_int),
+                ("eig_residual_max", C.c_double), ("workspace_bytes", C.c_int64)]
+
+
+class msmg_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
+                ("true_rel_residual", C.c_double), ("rhs_mean", C.c_double), ("solve_ms", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libmsmg.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmsmg.so not found at {path}; run __graft_entry__.build() "
+                          "(the CUDA path has no fallback)")
+    lib = C.CDLL(path)
+    P, I, D, S, I64 = C.c_void_p, C.c_int, C.c_double, C.c_size_t, C.c_int64
+    sig = {
+        "msmg_workspace_size": (I, [C.POINTER(msmg_grid), C.POINTER(msmg_options), I, C.POINTER(S)]),
+        "msmg_setup": (I, [C.POINTER(msmg_grid), P, I, I, C.POINTER(msmg_options), P, S, P, C.POINTER(P)]),
+        "msmg_solve": (I, [P, P, P, I, D, I, I, P, C.POINTER(msmg_solve_info)]),
+        "msmg_apply_A": (I, [P, P, P, P]),
+        "msmg_apply_precond": (I, [P, P, P, P]),
+        "msmg_dot_scratch_bytes": (S, [I64]),
+        "msmg_dot": (I, [P, P, I64, P, C.POINTER(D), P]),
+        "msmg_export_basis": (I, [P, I, P, P, P]),
+        "msmg_import_bases": (I, [P, C.POINTER(P), P]),
+        "msmg_export_operator": (I, [P, I, P, P]),
+        "msmg_export_faces": (I, [P, P, P]),
+        "msmg_get_setup_info": (I, [P, C.POINTER(msmg_setup_info)]),
+        "msmg_destroy": (None, [P]),
+        "msmg_status_string": (C.c_char_p, [I]),
+        "msmg_probe_alu_peaks": (I, [C.POINTER(D), C.POINTER(D), P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the entry points the binding declares (all must be exported)."""
+    return ["msmg_workspace_size", "msmg_setup", "msmg_solve", "msmg_apply_A", "msmg_apply_precond",
+            "msmg_dot_scratch_bytes", "msmg_dot", "msmg_export_basis", "msmg_import_bases",
+            "msmg_export_operator", "msmg_export_faces", "msmg_get_setup_info", "msmg_destroy",
+            "msmg_status_string", "msmg_probe_alu_peaks"]
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        msg = load_library().msmg_status_string(status).decode()
+        raise MsmgError(status, msg)
+    return status
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t: torch.Tensor, dtype=None, cuda: bool = True) -> int:
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if cuda and not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+@dataclass
+class Options:
+    n_levels: int = 3
+    block: tuple = (4, 4, 4)
+    ratio: list = field(default_factory=lambda: [(2, 2, 2)])
+    n_eig: list = field(default_factory=lambda: [4, 4])
+    nu: list | None = None
+    precision: int = FP64
+    eig_tol: float = 1e-12
+    eig_max_iter: int = 0
+
+    def to_c(self) -> msmg_options:
+        o = msmg_options()
+        o.n_levels = self.n_levels
+        for d in range(3):
+            o.block[d] = self.block[d]
+        for i, r in enumerate(self.ratio[:MAX_LEVELS]):
+            for d in range(3):
+                o.ratio[i][d] = r[d]
+        for i, v in enumerate(self.n_eig[:MAX_LEVELS]):
+            o.n_eig[i] = v
+        nu = self.nu if self.nu is not None else [1] * (self.n_levels - 1)
+        for i, v in enumerate(nu[:MAX_LEVELS]):
+            o.nu[i] = v
+        o.precision = self.precision
+        o.eig_tol = self.eig_tol
+        o.eig_max_iter = self.eig_max_iter
+        return o
+
+
+def make_grid(shape, h=None) -> msmg_grid:
+    nz, ny, nx = shape
+    g = msmg_grid()
+    g.nx, g.ny, g.nz = nx, ny, nz
+    hx, hy, hz = h if h is not None else (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    g.hx, g.hy, g.hz = hx, hy, hz
+    return g
+
+
+# ----------------------------------------------------------------- C names
+def msmg_workspace_size(grid: msmg_grid, opts: msmg_options, n_rhs: int = 1) -> int:
+    out = C.c_size_t(0)
+    _check(load_library().msmg_workspace_size(C.byref(grid), C.byref(opts), n_rhs, C.byref(out)))
+    return out.value
+
+
+def msmg_setup(grid: msmg_grid, kappa: torch.Tensor, opts: msmg_options, workspace: torch.Tensor,
+               stream=None) -> tuple[int, int]:
+    """Returns (ctx handle, status).  kappa: CUDA (C, nz, ny, nx) or (nz, ny, nx), f64/f32."""
+    comps = 1 if kappa.dim() == 3 else kappa.shape[0]
+    dt = {torch.float64: F64, torch.float32: F32}[kappa.dtype]
+    ctx = C.c_void_p(0)
+    st = load_library().msmg_setup(C.byref(grid), _ptr(kappa), comps, dt, C.byref(opts), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream), C.byref(ctx))
+    if st < 0 and st != -6:
+        if ctx.value:
+            load_library().msmg_destroy(ctx)
+        _check(st)
+    return ctx.value, st
+
+
+def msmg_solve(ctx: int, rhs: torch.Tensor, x: torch.Tensor, rtol: float, max_iter: int, flags: int = 0,
+               stream=None) -> tuple[int, list]:
+    host = bool(flags & FLAG_HOST_IO)
+    n_rhs = rhs.shape[0] if rhs.dim() == 4 else 1
+    infos = (msmg_solve_info * n_rhs)()
+    st = load_library().msmg_solve(ctx, _ptr(rhs, torch.float64, cuda=not host), _ptr(x, torch.float64, cuda=not host),
+                                   n_rhs, rtol, max_iter, flags, _stream(stream), infos)
+    _check(st)
+    return st, [dict(iterations=i.iterations, converged=bool(i.converged), rel_residual=i.rel_residual,
+                     true_rel_residual=i.true_rel_residual, rhs_mean=i.rhs_mean, solve_ms=i.solve_ms)
+                for i in infos]
+
+
+def msmg_apply_A(ctx: int, p: torch.Tensor, q: torch.Tensor, stream=None) -> None:
+    _check(load_library().msmg_apply_A(ctx, _ptr(p, torch.float64), _ptr(q, torch.float64), _stream(stream)))
+
+
+def msmg_apply_precond(ctx: int, r: torch.Tensor, z: torch.Tensor, stream=None) -> None:
+    _check(load_library().msmg_apply_precond(ctx, _ptr(r, torch.float64), _ptr(z, torch.float64), _stream(stream)))
+
+
+def msmg_dot(a: torch.Tensor, b: torch.Tensor, scratch: torch.Tensor | None = None, stream=None) -> float:
+    lib = load_library()
+    n = a.numel()
+    if scratch is None:
+        scratch = torch.empty(lib.msmg_dot_scratch_bytes(n), dtype=torch.uint8, device=a.device)
+    out = C.c_double(0.0)
+    _check(lib.msmg_dot(_ptr(a, torch.float64), _ptr(b, torch.float64), n, _ptr(scratch), C.byref(out),
+                        _stream(stream)))
+    return out.value
+
+
+def msmg_export_basis(ctx: int, level: int, basis: torch.Tensor, lam: torch.Tensor | None = None,
+                      stream=None) -> None:
+    _check(load_library().msmg_export_basis(ctx, level, _ptr(basis, torch.float64),
+                                            _ptr(lam, torch.float64) if lam is not None else None,
+                                            _stream(stream)))
+
+
+def msmg_import_bases(ctx: int, bases: list, stream=None) -> int:
+    arr = (C.c_void_p * len(bases))(*[_ptr(b, torch.float64) for b in bases])
+    return _check(load_library().msmg_import_bases(ctx, arr, _stream(stream)))
+
+
+def msmg_export_operator(ctx: int, level: int, out: torch.Tensor, stream=None) -> None:
+    _check(load_library().msmg_export_operator(ctx, level, _ptr(out, torch.float64), _stream(stream)))
+
+
+def msmg_export_faces(ctx: int, out: torch.Tensor, stream=None) -> None:
+    _check(load_library().msmg_export_faces(ctx, _ptr(out, torch.float64), _stream(stream)))
+
+
+def msmg_get_setup_info(ctx: int) -> dict:
+    i = msmg_setup_info()
+    _check(load_library().msmg_get_setup_info(ctx, C.byref(i)))
+    nL = i.n_levels
+    return dict(n_levels=nL, dims=list(i.dims[:nL]), elements=list(i.elements[:nL - 1]), setup_ms=i.setup_ms,
+                eig_ms=i.eig_ms, eig_iterations_max=i.eig_iterations_max, eig_residual_max=i.eig_residual_max,
+                workspace_bytes=i.workspace_bytes)
+
+
+def msmg_destroy(ctx: int) -> None:
+    load_library().msmg_destroy(ctx)
+
+
+def msmg_probe_alu_peaks(stream=None) -> tuple[float, float]:
+    a, b = C.c_double(0), C.c_double(0)
+    _check(load_library().msmg_probe_alu_peaks(C.byref(a), C.byref(b), _stream(stream)))
+    return a.value, b.value
+
+
+# ----------------------------------------------------------------- convenience
+class Solver:
+    """setup(permeability, grid, block sizes, eigenvectors per element, levels)
+    then solve(rhs, rtol), on the current CUDA device and stream."""
+
+    def __init__(self, kappa, opts: Options, h=None, n_rhs: int = 1, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("msmg needs a CUDA device (no CPU fallback)")
+        k = torch.as_tensor(kappa)
+        if not k.is_cuda:
+            k = k.to("cuda")
+        if k.dtype not in (torch.float64, torch.float32):
+            k = k.to(torch.float64)
+        k = k.contiguous()
+        shape = tuple(k.shape[-3:])
+        self.shape = shape
+        self.n = shape[0] * shape[1] * shape[2]
+        self.opts = opts
+        self.grid = make_grid(shape, h)
+        self.copts = opts.to_c()
+        nbytes = msmg_workspace_size(self.grid, self.copts, n_rhs)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=k.device)
+        self.ctx, self.setup_status = msmg_setup(self.grid, k, self.copts, self.workspace, stream)
+        self.stream = stream
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            msmg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return msmg_get_setup_info(self.ctx)
+
+    def solve(self, rhs: torch.Tensor, rtol: float = 1e-8, max_iter: int = 1000, x0: torch.Tensor | None = None):
+        rhs = rhs.to(torch.float64).contiguous()
+        x = torch.zeros_like(rhs) if x0 is None else x0.to(torch.float64).clone().contiguous()
+        flags = FLAG_X0 if x0 is not None else 0
+        if not rhs.is_cuda:
+            flags |= FLAG_HOST_IO
+        st, info = msmg_solve(self.ctx, rhs, x, rtol, max_iter, flags, self.stream)
+        return x, (info[0] if len(info) == 1 else info), st
+
+    def apply_A(self, p: torch.Tensor) -> torch.Tensor:
+        q = torch.empty_like(p)
+        msmg_apply_A(self.ctx, p.contiguous(), q, self.stream)
+        return q
+
+    def apply_precond(self, r: torch.Tensor) -> torch.Tensor:
+        z = torch.empty_like(r)
+        msmg_apply_precond(self.ctx, r.contiguous(), z, self.stream)
+        return z
+
+    def export_basis(self, level: int):
+        info = self.info
+        m = info["elements"][level - 1]
+        L = self.opts.n_eig[level - 1]
+        if level == 1:
+            per = self.opts.block[0] * self.opts.block[1] * self.opts.block[2]
+        else:
+            r = self.opts.ratio[level - 2]
+            per = r[0] * r[1] * r[2] * self.opts.n_eig[level - 2]
+        basis = torch.empty((m, L, per), dtype=torch.float64, device="cuda")
+        lam = torch.empty((m, L), dtype=torch.float64, device="cuda")
+        msmg_export_basis(self.ctx, level, basis, lam, self.stream)
+        return basis, lam
+
+    def import_bases(self, bases: list) -> int:
+        bs = [torch.as_tensor(b, dtype=torch.float64).to("cuda").contiguous() for b in bases]
+        st = msmg_import_bases(self.ctx, bs, self.stream)
+        torch.cuda.synchronize()
+        return st
+
+    def export_operator(self, level: int) -> torch.Tensor:
+        n = self.info["dims"][level - 1]
+        out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        msmg_export_operator(self.ctx, level, out, self.stream)
+        return out
+
+    def export_faces(self) -> torch.Tensor:
+        out = torch.empty((3,) + self.shape, dtype=torch.float64, device="cuda")
+        msmg_export_faces(self.ctx, out, self.stream)
+        return out

@@ -1,0 +1,474 @@
+// C-ABI entry points of libmsmg (declared in include/msmg.h): validation, the
+// workspace plan, set-up orchestration, solves and parity exports.
+#include "msmg_internal.cuh"
+#include "reduce.cuh"
+#include <cstring>
+#include <cstdio>
+#include <new>
+
+namespace msmg {
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+void set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s);
+void launch_mixed_copies(msmg_ctx* c, cudaStream_t s);
+void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s);
+int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s);
+int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
+
+struct LevelShape {
+  int g[kMaxLevels + 1][3];    // element grid of E_l, l = 1 .. nL-1
+  int64_t m[kMaxLevels + 1];
+};
+
+static int shapes(const msmg_grid* gr, const msmg_options* o, LevelShape& sh) {
+  const int nL = o->n_levels;
+  const int b[3] = {o->block[0], o->block[1], o->block[2]};
+  const int nn[3] = {gr->nx, gr->ny, gr->nz};
+  for (int d = 0; d < 3; ++d) {
+    if (b[d] < 1) return MSMG_ERR_INVALID_ARG;
+    if (nn[d] % b[d]) return MSMG_ERR_NOT_DIVISIBLE;
+    sh.g[1][d] = nn[d] / b[d];
+  }
+  sh.m[1] = (int64_t)sh.g[1][0] * sh.g[1][1] * sh.g[1][2];
+  for (int l = 2; l <= nL - 1; ++l) {
+    for (int d = 0; d < 3; ++d) {
+      const int r = o->ratio[l - 2][d];
+      if (r < 1) return MSMG_ERR_INVALID_ARG;
+      if (sh.g[l - 1][d] % r) return MSMG_ERR_NOT_DIVISIBLE;
+      sh.g[l][d] = sh.g[l - 1][d] / r;
+    }
+    sh.m[l] = (int64_t)sh.g[l][0] * sh.g[l][1] * sh.g[l][2];
+  }
+  return 0;
+}
+
+int validate(const msmg_grid* g, const msmg_options* o) {
+  if (!g || !o) return MSMG_ERR_INVALID_ARG;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return MSMG_ERR_INVALID_ARG;
+  if (!(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0)) return MSMG_ERR_INVALID_ARG;
+  if (o->n_levels < 2 || o->n_levels > kMaxLevels) return MSMG_ERR_INVALID_ARG;
+  if (o->precision != MSMG_FP64 && o->precision != MSMG_MIXED) return MSMG_ERR_INVALID_ARG;
+  LevelShape sh;
+  int st = shapes(g, o, sh);
+  if (st) return st;
+  const int nL = o->n_levels;
+  for (int l = 1; l <= nL - 1; ++l)
+    if (sh.m[l] < 2) return MSMG_ERR_SINGLE_BLOCK;
+  const int nb = o->block[0] * o->block[1] * o->block[2];
+  if (nb > 1024) return MSMG_ERR_UNSUPPORTED;
+  if (o->n_eig[0] < 1 || o->n_eig[0] > nb) return MSMG_ERR_INVALID_ARG;
+  for (int l = 2; l <= nL - 1; ++l) {
+    const int nch = o->ratio[l - 2][0] * o->ratio[l - 2][1] * o->ratio[l - 2][2];
+    const int nP = nch * o->n_eig[l - 2];
+    if (o->n_eig[l - 1] < 1 || o->n_eig[l - 1] > nP) return MSMG_ERR_INVALID_ARG;
+    if (nP > 96) return MSMG_ERR_UNSUPPORTED;
+  }
+  for (int l = 0; l < nL - 1; ++l)
+    if (o->nu[l] != 1) return MSMG_ERR_UNSUPPORTED;
+  if (o->eig_tol < 0) return MSMG_ERR_INVALID_ARG;
+  if (g->nx * (int64_t)g->ny * g->nz > ((int64_t)1 << 31) - 1) return MSMG_ERR_UNSUPPORTED;
+  return 0;
+}
+
+int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& ar, msmg_ctx* c) {
+  LevelShape sh;
+  int st = shapes(g, o, sh);
+  if (st) return st;
+  const int nL = o->n_levels;
+  c->grid = *g;
+  c->opts = *o;
+  c->nL = nL;
+  c->n = (int64_t)g->nx * g->ny * g->nz;
+  c->max_rhs = n_rhs < 1 ? 1 : n_rhs;
+  const bool mixed = o->precision == MSMG_MIXED;
+  FineLevel& f = c->fine;
+  f.bx = o->block[0]; f.by = o->block[1]; f.bz = o->block[2];
+  f.nb = f.bx * f.by * f.bz;
+  f.gx = sh.g[1][0]; f.gy = sh.g[1][1]; f.gz = sh.g[1][2];
+  f.m = sh.m[1];
+  f.n = c->n;
+  f.L = o->n_eig[0];
+  f.nu = o->nu[0];
+  for (int l = 2; l <= nL; ++l) {
+    CoarseLevel& lv = c->lev[l];
+    lv = CoarseLevel{};
+    lv.l = l;
+    lv.gx = sh.g[l - 1][0]; lv.gy = sh.g[l - 1][1]; lv.gz = sh.g[l - 1][2];
+    lv.me = sh.m[l - 1];
+    lv.L = o->n_eig[l - 2];
+    lv.n = lv.me * lv.L;
+    if (l < nL) {
+      lv.nu = o->nu[l - 1];
+      lv.rx = o->ratio[l - 2][0]; lv.ry = o->ratio[l - 2][1]; lv.rz = o->ratio[l - 2][2];
+      lv.nchild = lv.rx * lv.ry * lv.rz;
+      lv.mP = sh.m[l];
+      lv.nP = lv.nchild * lv.L;
+      lv.Lnext = o->n_eig[l - 1];
+    }
+  }
+  const int64_t n = c->n;
+  const int64_t nc = c->lev[nL].n;
+  // common
+  c->flags = ar.take<int>(16);
+  c->dtmp = ar.take<double>(16 + nc * nc + 3 * nc + 64);
+  const int epc = f.nb >= 256 ? 1 : 256 / f.nb;
+  int64_t maxgrid = (f.m + epc - 1) / epc;
+  if (maxgrid < 152 * 8) maxgrid = 152 * 8;
+  c->red.partials = ar.take<double>((size_t)maxgrid * kRedWidth);
+  c->red.counter = ar.take<unsigned>(4);
+  // fine level
+  f.lex_of_hid = ar.take<int>(f.m);
+  f.nbr = ar.take<int>(f.m * 6);
+  f.T = ar.take<double>(3 * n);
+  f.S = ar.take<double>(n);
+  f.invd = ar.take<double>(n);
+  f.Phi = ar.take<double>(f.m * f.L * f.nb);
+  f.lam = ar.take<double>(f.m * f.L);
+  if (mixed) {
+    f.T32 = ar.take<float>(3 * n);
+    f.invd32 = ar.take<float>(n);
+    f.Phi16 = ar.take<__nv_bfloat16>(f.m * f.L * f.nb);
+  }
+  for (int l = 2; l <= nL; ++l) {
+    CoarseLevel& lv = c->lev[l];
+    const int64_t L2 = (int64_t)lv.L * lv.L;
+    lv.lex_of_hid = ar.take<int>(lv.me);
+    lv.nbr = ar.take<int>(lv.me * 6);
+    lv.Ad = ar.take<double>(lv.me * L2);
+    lv.Ao = ar.take<double>(lv.me * 3 * L2);
+    lv.F = ar.take<double>(lv.me * 6 * L2);
+    lv.z = ar.take<double>(lv.n);
+    if (l < nL) {
+      lv.Minv = ar.take<double>(lv.mP * lv.nP * lv.nP);
+      lv.Psi = ar.take<double>(lv.mP * lv.Lnext * lv.nP);
+      lv.lamP = ar.take<double>(lv.mP * lv.Lnext);
+    } else {
+      lv.pinv = ar.take<double>(lv.n * lv.n);
+    }
+  }
+  // solve buffers
+  SolveBuffers& B = c->sb;
+  B.b = ar.take<double>(n);
+  B.x = ar.take<double>(n);
+  B.r = ar.take<double>(n);
+  B.z = ar.take<double>(n);
+  B.p0 = ar.take<double>(n);
+  B.p1 = ar.take<double>(n);
+  B.q = ar.take<double>(n);
+  B.vu[1] = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
+  for (int l = 2; l <= nL; ++l) {
+    B.vf[l] = ar.take<double>(c->lev[l].n);
+    B.vu[l] = ar.take<double>(c->lev[l].n);
+    B.vw[l] = ar.take<double>(c->lev[l].n);
+  }
+  B.sc = ar.take<PcgScalars>(c->max_rhs);
+  B.n_rhs = c->max_rhs;
+  return 0;
+}
+
+// Hierarchical numbering of the element levels (see msmg_internal.cuh) and
+// face-neighbour tables, built on the host.
+static void build_tables(const msmg_ctx* c, const LevelShape& sh, std::vector<std::vector<int>>& lex_of_hid,
+                         std::vector<std::vector<int>>& nbr) {
+  const int nL = c->nL;
+  std::vector<std::vector<int>> hid_of_lex(nL + 1);
+  lex_of_hid.assign(nL + 1, {});
+  nbr.assign(nL + 1, {});
+  for (int l = nL - 1; l >= 1; --l) {
+    const int gx = sh.g[l][0], gy = sh.g[l][1], gz = sh.g[l][2];
+    const int64_t m = sh.m[l];
+    hid_of_lex[l].resize(m);
+    lex_of_hid[l].resize(m);
+    for (int64_t lx = 0; lx < m; ++lx) {
+      const int ex = (int)(lx % gx), ey = (int)((lx / gx) % gy), ez = (int)(lx / ((int64_t)gx * gy));
+      int64_t hid;
+      if (l == nL - 1) hid = lx;
+      else {
+        const int rx = c->opts.ratio[l - 1][0], ry = c->opts.ratio[l - 1][1], rz = c->opts.ratio[l - 1][2];
+        const int px = ex / rx, py = ey / ry, pz = ez / rz;
+        const int64_t plex = px + (int64_t)sh.g[l + 1][0] * (py + (int64_t)sh.g[l + 1][1] * pz);
+        const int local = (ex % rx) + rx * ((ey % ry) + ry * (ez % rz));
+        hid = (int64_t)hid_of_lex[l + 1][plex] * (rx * ry * rz) + local;
+      }
+      hid_of_lex[l][lx] = (int)hid;
+      lex_of_hid[l][hid] = (int)lx;
+    }
+    nbr[l].resize(m * 6);
+    for (int64_t lx = 0; lx < m; ++lx) {
+      const int ex = (int)(lx % gx), ey = (int)((lx / gx) % gy), ez = (int)(lx / ((int64_t)gx * gy));
+      const int64_t h = hid_of_lex[l][lx];
+      const int cc[3] = {ex, ey, ez}, gg[3] = {gx, gy, gz};
+      const int64_t st[3] = {1, gx, (int64_t)gx * gy};
+      for (int d = 0; d < 3; ++d) {
+        nbr[l][h * 6 + 2 * d] = cc[d] > 0 ? hid_of_lex[l][lx - st[d]] : -1;
+        nbr[l][h * 6 + 2 * d + 1] = cc[d] + 1 < gg[d] ? hid_of_lex[l][lx + st[d]] : -1;
+      }
+    }
+  }
+}
+
+static int check_flags(msmg_ctx* c, cudaStream_t s) {
+  int h[4];
+  double d[2];
+  MSMG_CUDA_TRY(cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MSMG_CUDA_TRY(cudaMemcpyAsync(d, c->dtmp, sizeof(d), cudaMemcpyDeviceToHost, s));
+  MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+  MSMG_CUDA_TRY(cudaGetLastError());
+  if (h[0]) return MSMG_ERR_BAD_KAPPA;
+  if (h[1] || d[1] != 0.0) return MSMG_ERR_NOT_FACTORIZABLE;
+  c->info.eig_residual_max = d[0];
+  if (h[2]) return MSMG_ERR_EIG_NOT_CONVERGED;
+  return 0;
+}
+
+// Everything that depends on the bases: Galerkin operators, coarse smoothers,
+// coarsest pseudo-inverse, reduced-precision copies.
+static int build_from_bases(msmg_ctx* c, bool given, cudaStream_t s) {
+  launch_level1_galerkin(c, s);
+  for (int l = 2; l <= c->nL - 1; ++l) {
+    int st = given ? launch_coarse_setup_given(c, l, s) : launch_coarse_setup(c, l, s);
+    if (st) return st;
+  }
+  int st = launch_coarsest(c, s);
+  if (st) return st;
+  launch_mixed_copies(c, s);
+  return 0;
+}
+
+}  // namespace msmg
+
+using namespace msmg;
+
+extern "C" {
+
+int msmg_workspace_size(const msmg_grid* grid, const msmg_options* opts, int n_rhs, size_t* bytes) {
+  int st = validate(grid, opts);
+  if (st) return st;
+  if (!bytes) return MSMG_ERR_INVALID_ARG;
+  msmg_ctx tmp{};
+  Arena ar;
+  st = plan_and_carve(grid, opts, n_rhs, ar, &tmp);
+  if (st) return st;
+  *bytes = ar.off + 256;
+  return 0;
+}
+
+int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, int kappa_dtype,
+               const msmg_options* opts, void* workspace, size_t workspace_bytes, msmg_stream stream,
+               msmg_ctx** out) {
+  if (!out || !kappa || !workspace) return MSMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  int st = validate(grid, opts);
+  if (st) return st;
+  if (kappa_components != 1 && kappa_components != 3) return MSMG_ERR_INVALID_ARG;
+  if (kappa_dtype != MSMG_F64 && kappa_dtype != MSMG_F32) return MSMG_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return MSMG_ERR_WORKSPACE;
+  size_t need = 0;
+  msmg_workspace_size(grid, opts, 1, &need);
+  if (workspace_bytes < need) return MSMG_ERR_WORKSPACE;
+  msmg_ctx* c = new (std::nothrow) msmg_ctx{};
+  if (!c) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Arena ar;
+  ar.base = static_cast<char*>(workspace);
+  ar.cap = workspace_bytes;
+  // the largest n_rhs that fits
+  int n_rhs = 1;
+  for (int k = 2; k <= 4096; k *= 2) {
+    size_t b = 0;
+    msmg_workspace_size(grid, opts, k, &b);
+    if (b <= workspace_bytes) n_rhs = k; else break;
+  }
+  plan_and_carve(grid, opts, n_rhs, ar, c);
+  c->ws_bytes = workspace_bytes;
+  cudaGetDevice(&c->device);
+  cudaEventCreate(&c->ev0);
+  cudaEventCreate(&c->ev1);
+  *out = c;
+  cudaEventRecord(c->ev0, s);
+  LevelShape sh;
+  shapes(grid, opts, sh);
+  std::vector<std::vector<int>> lex, nbr;
+  build_tables(c, sh, lex, nbr);
+  MSMG_CUDA_TRY(cudaMemcpyAsync(c->fine.lex_of_hid, lex[1].data(), lex[1].size() * sizeof(int),
+                                cudaMemcpyHostToDevice, s));
+  MSMG_CUDA_TRY(cudaMemcpyAsync(c->fine.nbr, nbr[1].data(), nbr[1].size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  for (int l = 2; l <= c->nL; ++l) {
+    MSMG_CUDA_TRY(cudaMemcpyAsync(c->lev[l].lex_of_hid, lex[l - 1].data(), lex[l - 1].size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, s));
+    MSMG_CUDA_TRY(cudaMemcpyAsync(c->lev[l].nbr, nbr[l - 1].data(), nbr[l - 1].size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, s));
+  }
+  MSMG_CUDA_TRY(cudaStreamSynchronize(s));   // host tables go out of scope
+  MSMG_CUDA_TRY(cudaMemsetAsync(c->flags, 0, 16 * sizeof(int), s));
+  MSMG_CUDA_TRY(cudaMemsetAsync(c->dtmp, 0, 16 * sizeof(double), s));
+  MSMG_CUDA_TRY(cudaMemsetAsync(c->red.counter, 0, 4 * sizeof(unsigned), s));
+  launch_faces(c, kappa, kappa_components, kappa_dtype, s);
+  launch_pivots(c, s);
+  cudaEvent_t e_eig0, e_eig1;
+  cudaEventCreate(&e_eig0);
+  cudaEventCreate(&e_eig1);
+  cudaEventRecord(e_eig0, s);
+  st = (c->fine.nb <= 96) ? launch_level1_eigen(c, s) : launch_level1_chfsi(c, s);
+  cudaEventRecord(e_eig1, s);
+  if (st) return st;
+  st = build_from_bases(c, false, s);
+  if (st) return st;
+  cudaEventRecord(c->ev1, s);
+  int fl = check_flags(c, s);
+  float ms = 0.f, ems = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  cudaEventElapsedTime(&ems, e_eig0, e_eig1);
+  cudaEventDestroy(e_eig0);
+  cudaEventDestroy(e_eig1);
+  msmg_setup_info& I = c->info;
+  I.n_levels = c->nL;
+  I.dims[0] = c->n;
+  for (int l = 2; l <= c->nL; ++l) I.dims[l - 1] = c->lev[l].n;
+  for (int l = 1; l <= c->nL - 1; ++l) I.elements[l - 1] = sh.m[l];
+  I.setup_ms = ms;
+  I.eig_ms = ems;
+  I.workspace_bytes = (int64_t)workspace_bytes;
+  return fl;
+}
+
+int msmg_solve(msmg_ctx* c, const double* rhs, double* x, int n_rhs, double rtol, int max_iter, int flags,
+               msmg_stream stream, msmg_solve_info* info) {
+  if (!c || !rhs || !x || n_rhs < 1 || max_iter < 0 || !(rtol >= 0)) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int worst = 0;
+  for (int i = 0; i < n_rhs; ++i) {
+    cudaEventRecord(c->ev0, s);
+    msmg_solve_info loc{};
+    int st = pcg_solve(c, rhs + (int64_t)i * c->n, x + (int64_t)i * c->n, rtol, max_iter, flags, s, &loc);
+    cudaEventRecord(c->ev1, s);
+    cudaEventSynchronize(c->ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    loc.solve_ms = ms;
+    if (info) info[i] = loc;
+    if (st < 0) return st;
+    if (st > worst) worst = st;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
+  return worst;
+}
+
+int msmg_apply_A(msmg_ctx* c, const double* p, double* q, msmg_stream stream) {
+  if (!c || !p || !q) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_nat_to_blk(c, p, c->sb.p0, s);
+  launch_matvec(c, c->sb.p0, c->sb.q, s);
+  launch_blk_to_nat(c, c->sb.q, q, s);
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_apply_precond(msmg_ctx* c, const double* r, double* z, msmg_stream stream) {
+  if (!c || !r || !z) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_nat_to_blk(c, r, c->sb.r, s);
+  vcycle(c, c->sb.r, c->sb.z, nullptr, s);
+  launch_blk_to_nat(c, c->sb.z, z, s);
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+size_t msmg_dot_scratch_bytes(int64_t n) {
+  (void)n;
+  return (size_t)(152 * 8) * kRedWidth * sizeof(double) + 256;
+}
+
+int msmg_dot(const double* a, const double* b, int64_t n, void* scratch, double* result_host, msmg_stream stream) {
+  if (!a || !b || !scratch || !result_host || n < 0) return MSMG_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(scratch) % 16) return MSMG_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(scratch);
+  RedSlot red;
+  red.partials = reinterpret_cast<double*>(base + 256);
+  red.counter = reinterpret_cast<unsigned*>(base);
+  double* out = reinterpret_cast<double*>(base + 64);
+  MSMG_CUDA_TRY(cudaMemsetAsync(base, 0, 256, s));
+  launch_dot(a, b, n, red, out, s);
+  MSMG_CUDA_TRY(cudaMemcpyAsync(result_host, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_export_basis(msmg_ctx* c, int level, double* basis, double* lam, msmg_stream stream) {
+  if (!c || !basis || level < 1 || level > c->nL - 1) return MSMG_ERR_INVALID_ARG;
+  launch_basis_export(c, level, basis, lam, false, reinterpret_cast<cudaStream_t>(stream));
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_import_bases(msmg_ctx* c, const double* const* bases, msmg_stream stream) {
+  if (!c || !bases) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int l = 1; l <= c->nL - 1; ++l) {
+    if (!bases[l - 1]) return MSMG_ERR_INVALID_ARG;
+    launch_basis_export(c, l, const_cast<double*>(bases[l - 1]), nullptr, true, s);
+  }
+  MSMG_CUDA_TRY(cudaMemsetAsync(c->dtmp, 0, 16 * sizeof(double), s));
+  // level-by-level: each level's operator is needed before the next level's set-up
+  launch_level1_galerkin(c, s);
+  for (int l = 2; l <= c->nL - 1; ++l) {
+    int st = launch_coarse_setup_given(c, l, s);
+    if (st) return st;
+  }
+  int st = launch_coarsest(c, s);
+  if (st) return st;
+  launch_mixed_copies(c, s);
+  return check_flags(c, s);
+}
+
+int msmg_export_operator(msmg_ctx* c, int level, double* out, msmg_stream stream) {
+  if (!c || !out || level < 2 || level > c->nL) return MSMG_ERR_INVALID_ARG;
+  launch_operator_export(c, level, out, reinterpret_cast<cudaStream_t>(stream));
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_export_faces(msmg_ctx* c, double* T, msmg_stream stream) {
+  if (!c || !T) return MSMG_ERR_INVALID_ARG;
+  launch_faces_to_nat(c, T, reinterpret_cast<cudaStream_t>(stream));
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_get_setup_info(msmg_ctx* c, msmg_setup_info* info) {
+  if (!c || !info) return MSMG_ERR_INVALID_ARG;
+  *info = c->info;
+  return 0;
+}
+
+void msmg_destroy(msmg_ctx* c) {
+  if (!c) return;
+  cudaEventDestroy(c->ev0);
+  cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+const char* msmg_status_string(int s) {
+  switch (s) {
+    case MSMG_OK: return "ok";
+    case MSMG_NOT_CONVERGED: return "not converged within max_iter";
+    case MSMG_ERR_INVALID_ARG: return "invalid argument";
+    case MSMG_ERR_NOT_DIVISIBLE: return "element sizes do not tile the grid";
+    case MSMG_ERR_BAD_KAPPA: return "permeability not positive and finite";
+    case MSMG_ERR_SINGLE_BLOCK: return "a smoothed level has a single element";
+    case MSMG_ERR_BREAKDOWN: return "PCG breakdown (p^T A p <= 0 or non-finite)";
+    case MSMG_ERR_EIG_NOT_CONVERGED: return "local eigensolve did not reach eig_tol";
+    case MSMG_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case MSMG_ERR_CUDA: return cudaGetErrorString(g_last_cuda);
+    case MSMG_ERR_NOT_FACTORIZABLE: return "smoother or coarsest factorisation failed";
+    case MSMG_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

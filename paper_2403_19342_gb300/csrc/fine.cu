@@ -1,0 +1,545 @@
+// Fine-level kernels: face coefficients (Section 2.2), IC(0) pivots of the
+// block-Jacobi smoother (Section 5), the two-point-flux stencil
+// (Eq. (discrete varia)), and the fine-level steps of the V-cycle
+// (Algorithm 1: pre-smoothing, residual restriction with the local
+// eigenbases, prolongation, post-smoothing).
+//
+// Every kernel works element by element: one group of nb threads per element
+// (nb = cells per element), ``epc`` elements per CTA.  An element's cells and
+// the one-cell halo on its six faces are staged in shared memory as a padded
+// (bx+2)(by+2)(bz+2) tile; the halo comes from the face-adjacent elements
+// (their data is one contiguous chunk each in the block-major layout).
+#include "msmg_internal.cuh"
+#include "reduce.cuh"
+
+namespace msmg {
+
+struct Geo {
+  int bx, by, bz, nb, epc, P;   // P = padded tile size
+};
+
+__host__ __device__ inline Geo make_geo(int bx, int by, int bz) {
+  Geo g;
+  g.bx = bx; g.by = by; g.bz = bz; g.nb = bx * by * bz;
+  g.epc = g.nb >= 256 ? 1 : 256 / g.nb;
+  g.P = (bx + 2) * (by + 2) * (bz + 2);
+  return g;
+}
+
+__device__ __forceinline__ int pad(const Geo& g, int lx, int ly, int lz) {
+  return (lx + 1) + (g.bx + 2) * ((ly + 1) + (g.by + 2) * (lz + 1));
+}
+
+// Thread -> (element in CTA, local cell); ``valid`` false for padding threads
+// and elements past the end.
+struct Slot {
+  int eloc;       // element index inside the CTA
+  int p;          // local cell
+  int64_t e;      // global (hierarchical) element
+  int lx, ly, lz;
+  bool valid;
+};
+
+__device__ __forceinline__ Slot make_slot(const Geo& g, int64_t m) {
+  Slot s;
+  s.eloc = threadIdx.x / g.nb;
+  s.p = threadIdx.x % g.nb;
+  s.e = (int64_t)blockIdx.x * g.epc + s.eloc;
+  s.valid = (s.eloc < g.epc) && (s.e < m);
+  s.lx = s.p % g.bx;
+  int t = s.p / g.bx;
+  s.ly = t % g.by;
+  s.lz = t / g.by;
+  return s;
+}
+
+// Stage field X (block-major) of element s.e into a padded tile, including the
+// one-cell halo on the faces selected by ``face_mask`` (bit f for face f =
+// -x,+x,-y,+y,-z,+z).  Halo cells outside the domain are zero.
+template <typename Src, typename Dst>
+__device__ void load_tile(Dst* tile, const Src* X, const Slot& s, const Geo& g, const int* nbr, int face_mask) {
+  if (s.valid) tile[pad(g, s.lx, s.ly, s.lz)] = (Dst)X[s.e * g.nb + s.p];
+  if (s.eloc >= g.epc) return;
+  const int F0 = g.by * g.bz, F1 = g.bx * g.bz, F2 = g.bx * g.by;
+  const int H = 2 * (F0 + F1 + F2);
+  for (int h = s.p; h < H; h += g.nb) {
+    int f, u, v;
+    if (h < 2 * F0) { f = h / F0; int q = h % F0; u = q % g.by; v = q / g.by; }
+    else if (h < 2 * (F0 + F1)) { int hh = h - 2 * F0; f = 2 + hh / F1; int q = hh % F1; u = q % g.bx; v = q / g.bx; }
+    else { int hh = h - 2 * (F0 + F1); f = 4 + hh / F2; int q = hh % F2; u = q % g.bx; v = q / g.bx; }
+    if (!((face_mask >> f) & 1)) continue;
+    int dx, dy, dz, sx, sy, sz;   // destination (padded coords) and source local coords
+    switch (f) {
+      case 0: dx = -1; dy = u; dz = v; sx = g.bx - 1; sy = u; sz = v; break;
+      case 1: dx = g.bx; dy = u; dz = v; sx = 0; sy = u; sz = v; break;
+      case 2: dx = u; dy = -1; dz = v; sx = u; sy = g.by - 1; sz = v; break;
+      case 3: dx = u; dy = g.by; dz = v; sx = u; sy = 0; sz = v; break;
+      case 4: dx = u; dy = v; dz = -1; sx = u; sy = v; sz = g.bz - 1; break;
+      default: dx = u; dy = v; dz = g.bz; sx = u; sy = v; sz = 0; break;
+    }
+    Dst val = (Dst)0;
+    if (s.e < 0 || !s.valid) { /* element past the end: leave */ }
+    else {
+      int ne = nbr[s.e * 6 + f];
+      if (ne >= 0) val = (Dst)X[(int64_t)ne * g.nb + sx + g.bx * (sy + g.by * sz)];
+    }
+    tile[pad(g, dx, dy, dz)] = val;
+  }
+}
+
+// T tiles: interior of all three components plus the -d face halo of component d
+// (the coefficient of the face between the element and its -d neighbour).
+template <typename Src, typename Dst>
+__device__ void load_T_tiles(Dst* t0, Dst* t1, Dst* t2, const Src* T, int64_t n, const Slot& s, const Geo& g,
+                             const int* nbr) {
+  load_tile(t0, T, s, g, nbr, 1 << 0);
+  load_tile(t1, T + n, s, g, nbr, 1 << 2);
+  load_tile(t2, T + 2 * n, s, g, nbr, 1 << 4);
+}
+
+// (A u)_c from padded tiles: sum over the six faces of T_f (u_c - u_nb).
+template <typename V>
+__device__ __forceinline__ V apply_A_cell(const V* ut, const V* t0, const V* t1, const V* t2, const Geo& g,
+                                          int lx, int ly, int lz) {
+  const int c = pad(g, lx, ly, lz);
+  const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
+  const V uc = ut[c];
+  V acc = t0[c] * (uc - ut[c + 1]) + t0[c - 1] * (uc - ut[c - 1]);
+  acc += t1[c] * (uc - ut[c + sy]) + t1[c - sy] * (uc - ut[c - sy]);
+  acc += t2[c] * (uc - ut[c + sz]) + t2[c - sz] * (uc - ut[c - sz]);
+  return acc;
+}
+
+// In-place IC(0) solve on one element: y <- M^{-1} y with
+// M = (D~ + L) D~^{-1} (D~ + L^T), L the strictly lower part of the element's
+// diagonal block (off-diagonal entries -T).  Wavefronts lx + ly + lz = const.
+template <typename V>
+__device__ void ic0_solve(V* y, const V* t0, const V* t1, const V* t2, V invd, const Slot& s, const Geo& g) {
+  const int smax = g.bx + g.by + g.bz - 3;
+  const int sc = s.lx + s.ly + s.lz;
+  const int c = pad(g, s.lx, s.ly, s.lz);
+  const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
+  const int p = s.p;
+  for (int w = 0; w <= smax; ++w) {
+    if (s.valid && sc == w) {
+      V acc = y[p];
+      if (s.lx > 0) acc += t0[c - 1] * y[p - 1];
+      if (s.ly > 0) acc += t1[c - sy] * y[p - g.bx];
+      if (s.lz > 0) acc += t2[c - sz] * y[p - g.bx * g.by];
+      y[p] = acc * invd;
+    }
+    __syncthreads();
+  }
+  for (int w = smax; w >= 0; --w) {
+    if (s.valid && sc == w) {
+      V acc = (V)0;
+      if (s.lx < g.bx - 1) acc += t0[c] * y[p + 1];
+      if (s.ly < g.by - 1) acc += t1[c] * y[p + g.bx];
+      if (s.lz < g.bz - 1) acc += t2[c] * y[p + g.bx * g.by];
+      y[p] = y[p] + invd * acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================== set-up kernels
+
+// K1: face coefficients (harmonic average of kappa^d / h_d^2, Fig. (kappa edge))
+// and Tr K~, written block-major.  flags[0] <- 1 on non-positive / non-finite kappa.
+template <typename KT>
+__global__ void k_faces(const KT* __restrict__ kappa, int comps, int nx, int ny, int nz, double ihx2, double ihy2,
+                        double ihz2, Geo g, int64_t m, const int* __restrict__ lex_of_hid, int gx, int gy,
+                        double* __restrict__ T, double* __restrict__ S, int* flags) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = i / g.nb;
+  const int p = (int)(i % g.nb);
+  const int lex = lex_of_hid[e];
+  const int ex = lex % gx, ey = (lex / gx) % gy, ez = lex / (gx * gy);
+  const int lx = p % g.bx, ly = (p / g.bx) % g.by, lz = p / (g.bx * g.by);
+  const int ci = ex * g.bx + lx, cj = ey * g.by + ly, ck = ez * g.bz + lz;
+  const int64_t c = ci + (int64_t)nx * (cj + (int64_t)ny * ck);
+  const double ih[3] = {ihx2, ihy2, ihz2};
+  const int64_t stride[3] = {1, nx, (int64_t)nx * ny};
+  const bool has[3] = {ci + 1 < nx, cj + 1 < ny, ck + 1 < nz};
+  double s = 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t comp = comps == 3 ? d : 0;
+    const double kc = (double)kappa[comp * n + c];
+    bad |= !(kc > 0.0) || !isfinite(kc);
+    const double a = kc * ih[d];
+    s += a;
+    double t = 0.0;
+    if (has[d]) {
+      const double kn = (double)kappa[comp * n + c + stride[d]];
+      const double b = kn * ih[d];
+      t = (kn > 0.0 && isfinite(kn) && a > 0.0) ? 2.0 / (1.0 / a + 1.0 / b) : 0.0;
+    }
+    T[d * n + i] = t;
+  }
+  S[i] = s;
+  if (bad) atomicExch(&flags[0], 1);
+}
+
+// IC(0) pivots of each element's diagonal block of the global A:
+// d_c = a_cc - sum_{j < c, j ~ c in element} T^2 / d_j, a_cc = sum of the six face
+// coefficients.  Writes 1/d.  flags[1] <- 1 on a non-positive pivot.
+__global__ void k_pivots(const double* __restrict__ T, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
+                         double* __restrict__ invd, int* flags) {
+  extern __shared__ double smem[];
+  const Slot s = make_slot(g, m);
+  double* t0 = smem + (size_t)s.eloc * (3 * g.P + g.nb);
+  double* t1 = t0 + g.P;
+  double* t2 = t1 + g.P;
+  double* d = t2 + g.P;
+  if (s.eloc < g.epc) load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
+  __syncthreads();
+  const int c = pad(g, s.lx, s.ly, s.lz);
+  const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
+  double diag = 0.0;
+  if (s.valid) diag = t0[c] + t0[c - 1] + t1[c] + t1[c - sy] + t2[c] + t2[c - sz];
+  const int smax = g.bx + g.by + g.bz - 3;
+  const int sc = s.lx + s.ly + s.lz;
+  for (int w = 0; w <= smax; ++w) {
+    if (s.valid && sc == w) {
+      double v = diag;
+      if (s.lx > 0) v -= t0[c - 1] * t0[c - 1] / d[s.p - 1];
+      if (s.ly > 0) v -= t1[c - sy] * t1[c - sy] / d[s.p - g.bx];
+      if (s.lz > 0) v -= t2[c - sz] * t2[c - sz] / d[s.p - g.bx * g.by];
+      d[s.p] = v;
+      if (!(v > 0.0)) atomicExch(&flags[1], 1);
+    }
+    __syncthreads();
+  }
+  if (s.valid) invd[s.e * g.nb + s.p] = 1.0 / d[s.p];
+}
+
+// natural <-> block-major permutations
+__device__ __forceinline__ int64_t nat_index(int64_t i, const Geo& g, const int* lex_of_hid, int gx, int gy, int nx,
+                                             int ny) {
+  const int64_t e = i / g.nb;
+  const int p = (int)(i % g.nb);
+  const int lex = lex_of_hid[e];
+  const int ex = lex % gx, ey = (lex / gx) % gy, ez = lex / (gx * gy);
+  const int lx = p % g.bx, ly = (p / g.bx) % g.by, lz = p / (g.bx * g.by);
+  return (int64_t)(ex * g.bx + lx) + (int64_t)nx * ((ey * g.by + ly) + (int64_t)ny * (ez * g.bz + lz));
+}
+
+template <bool ToBlk, typename Tin, typename Tout>
+__global__ void k_perm(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t n, Geo g,
+                       const int* __restrict__ lex_of_hid, int gx, int gy, int nx, int ny, int comps) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t j = nat_index(i, g, lex_of_hid, gx, gy, nx, ny);
+  for (int c = 0; c < comps; ++c) {
+    if (ToBlk) out[c * n + i] = (Tout)in[c * n + j];
+    else out[c * n + j] = (Tout)in[c * n + i];
+  }
+}
+
+// ============================================================== stencil
+
+// q = A p (FP64).  With Reduce, also p.q and the PCG step length (finaliser).
+template <bool Reduce>
+__global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, const double* __restrict__ T, int64_t n,
+                         Geo g, int64_t m, const int* __restrict__ nbr, RedSlot red, PcgScalars* sc) {
+  if (Reduce && sc->done) return;
+  extern __shared__ double smem[];
+  const Slot s = make_slot(g, m);
+  double* pt = smem + (size_t)s.eloc * 4 * g.P;
+  double* t0 = pt + g.P;
+  double* t1 = t0 + g.P;
+  double* t2 = t1 + g.P;
+  if (s.eloc < g.epc) {
+    load_tile(pt, p, s, g, nbr, 0x3f);
+    load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
+  }
+  __syncthreads();
+  double v[1] = {0.0};
+  if (s.valid) {
+    const double a = apply_A_cell(pt, t0, t1, t2, g, s.lx, s.ly, s.lz);
+    q[s.e * g.nb + s.p] = a;
+    v[0] = a * pt[pad(g, s.lx, s.ly, s.lz)];
+  }
+  if (Reduce) {
+    grid_reduce<1>(v, red, [=] __device__(double* t) {
+      sc->pq = t[0];
+      if (!(t[0] > 0.0) || !isfinite(t[0])) { sc->done = 2; sc->alpha = 0.0; }
+      else sc->alpha = sc->rz / t[0];
+    });
+  }
+}
+
+// ============================================================== V-cycle, fine level
+
+// Pre-smoothing from zero: u = M^{-1} f.
+template <typename V>
+__global__ void k_smooth_first(const double* __restrict__ f, V* __restrict__ u, const V* __restrict__ T,
+                               const V* __restrict__ invd, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
+                               const PcgScalars* sc) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* smem = reinterpret_cast<V*>(smem_raw);
+  const Slot s = make_slot(g, m);
+  V* t0 = smem + (size_t)s.eloc * (3 * g.P + g.nb);
+  V* t1 = t0 + g.P;
+  V* t2 = t1 + g.P;
+  V* y = t2 + g.P;
+  if (s.eloc < g.epc) load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
+  V dinv = (V)0;
+  if (s.valid) {
+    y[s.p] = (V)f[s.e * g.nb + s.p];
+    dinv = invd[s.e * g.nb + s.p];
+  }
+  __syncthreads();
+  ic0_solve(y, t0, t1, t2, dinv, s, g);
+  if (s.valid) u[s.e * g.nb + s.p] = y[s.p];
+}
+
+// Residual and restriction: rc[e][k] = sum_c Phi[e][k][c] (f - A u)_c  (Algorithm 1,
+// "Restriction"; R_1 rows are the local eigenvectors).
+template <typename V, typename BT>
+__global__ void k_resid_restrict(const double* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T,
+                                 const BT* __restrict__ Phi, int L, double* __restrict__ rc, int64_t n, Geo g,
+                                 int64_t m, const int* __restrict__ nbr, const PcgScalars* sc) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* smem = reinterpret_cast<V*>(smem_raw);
+  const Slot s = make_slot(g, m);
+  V* ut = smem + (size_t)s.eloc * 4 * g.P;
+  V* t0 = ut + g.P;
+  V* t1 = t0 + g.P;
+  V* t2 = t1 + g.P;
+  double* red = reinterpret_cast<double*>(smem + (size_t)g.epc * 4 * g.P);   // [epc][L][nwarp_e] or [epc][nb]
+  if (s.eloc < g.epc) {
+    load_tile(ut, u, s, g, nbr, 0x3f);
+    load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
+  }
+  __syncthreads();
+  double w = 0.0;
+  if (s.valid) w = f[s.e * g.nb + s.p] - (double)apply_A_cell(ut, t0, t1, t2, g, s.lx, s.ly, s.lz);
+  if ((g.nb & 31) == 0) {
+    const int nwe = g.nb / 32;
+    const int lane = threadIdx.x & 31, wi = s.p / 32;
+    for (int k = 0; k < L; ++k) {
+      double v = 0.0;
+      if (s.valid) v = w * (double)Phi[(s.e * L + k) * g.nb + s.p];
+      v = warp_sum(v);
+      if (lane == 0 && s.eloc < g.epc) red[((size_t)s.eloc * L + k) * nwe + wi] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < g.epc * L; t += blockDim.x) {
+      const int el = t / L, k = t % L;
+      const int64_t e = (int64_t)blockIdx.x * g.epc + el;
+      if (e >= m) continue;
+      double acc = 0.0;
+      for (int j = 0; j < nwe; ++j) acc += red[((size_t)el * L + k) * nwe + j];
+      rc[e * L + k] = acc;
+    }
+  } else {
+    for (int k = 0; k < L; ++k) {
+      if (s.eloc < g.epc) red[(size_t)s.eloc * g.nb + s.p] = s.valid ? w * (double)Phi[(s.e * L + k) * g.nb + s.p] : 0.0;
+      __syncthreads();
+      if (s.valid && s.p == 0) {
+        double acc = 0.0;
+        for (int j = 0; j < g.nb; ++j) acc += red[(size_t)s.eloc * g.nb + j];
+        rc[s.e * L + k] = acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Prolongation: u_c += sum_k Phi[e][k][c] ec[e][k]  (Algorithm 1, R_c^T e_c).
+template <typename V, typename BT>
+__global__ void k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L, const double* __restrict__ ec,
+                          int64_t n, int nb, const PcgScalars* sc) {
+  if (sc && sc->done) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = i / nb;
+  const int p = (int)(i % nb);
+  double acc = 0.0;
+  for (int k = 0; k < L; ++k) acc += (double)Phi[(e * L + k) * nb + p] * ec[e * L + k];
+  u[i] = (V)((double)u[i] + acc);
+}
+
+// Post-smoothing: out = u + M^{-1} (f - A u).  Final = true: out is the FP64
+// preconditioned residual z, and the CTA reduction gives f.z (and z.q for the
+// flexible beta), finalising the PCG beta.
+template <typename V, bool Final>
+__global__ void k_resid_smooth(const double* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T,
+                               const V* __restrict__ invd, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
+                               void* __restrict__ out, const double* __restrict__ qv, RedSlot red, PcgScalars* sc) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* smem = reinterpret_cast<V*>(smem_raw);
+  const Slot s = make_slot(g, m);
+  V* ut = smem + (size_t)s.eloc * (4 * g.P + g.nb);
+  V* t0 = ut + g.P;
+  V* t1 = t0 + g.P;
+  V* t2 = t1 + g.P;
+  V* y = t2 + g.P;
+  if (s.eloc < g.epc) {
+    load_tile(ut, u, s, g, nbr, 0x3f);
+    load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
+  }
+  __syncthreads();
+  V dinv = (V)0;
+  double fc = 0.0;
+  if (s.valid) {
+    fc = f[s.e * g.nb + s.p];
+    y[s.p] = (V)(fc - (double)apply_A_cell(ut, t0, t1, t2, g, s.lx, s.ly, s.lz));
+    dinv = invd[s.e * g.nb + s.p];
+  }
+  __syncthreads();
+  ic0_solve(y, t0, t1, t2, dinv, s, g);
+  double zc = 0.0;
+  if (s.valid) {
+    zc = (double)ut[pad(g, s.lx, s.ly, s.lz)] + (double)y[s.p];
+    if (Final) reinterpret_cast<double*>(out)[s.e * g.nb + s.p] = zc;
+    else reinterpret_cast<V*>(out)[s.e * g.nb + s.p] = (V)zc;
+  }
+  if (Final && sc) {
+    double v[2] = {fc * zc, (s.valid && qv) ? zc * qv[s.e * g.nb + s.p] : 0.0};
+    grid_reduce<2>(v, red, [=] __device__(double* t) {
+      sc->rz_old = sc->rz;
+      sc->rz = t[0];
+      if (sc->iter == 0 && sc->pq == 0.0) sc->beta = 0.0;          // first preconditioned residual
+      else if (sc->flexible) sc->beta = -sc->alpha * t[1] / sc->rz_old;
+      else sc->beta = t[0] / sc->rz_old;
+      if (!isfinite(t[0])) sc->done = 2;
+    });
+  }
+}
+
+// ============================================================== host launchers
+
+static inline Geo fine_geo(const msmg_ctx* c) { return make_geo(c->fine.bx, c->fine.by, c->fine.bz); }
+static inline unsigned fine_grid(const msmg_ctx* c, const Geo& g) { return (unsigned)((c->fine.m + g.epc - 1) / g.epc); }
+static inline unsigned fine_threads(const Geo& g) { return (unsigned)(((g.epc * g.nb) + 31) / 32 * 32); }
+
+void launch_faces(msmg_ctx* c, const void* kappa, int comps, int dtype, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  const int64_t n = c->n;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  const double ihx2 = 1.0 / (c->grid.hx * c->grid.hx), ihy2 = 1.0 / (c->grid.hy * c->grid.hy),
+               ihz2 = 1.0 / (c->grid.hz * c->grid.hz);
+  if (dtype == MSMG_F32)
+    k_faces<float><<<grid, 256, 0, s>>>((const float*)kappa, comps, c->grid.nx, c->grid.ny, c->grid.nz, ihx2, ihy2,
+                                        ihz2, g, c->fine.m, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->fine.T,
+                                        c->fine.S, c->flags);
+  else
+    k_faces<double><<<grid, 256, 0, s>>>((const double*)kappa, comps, c->grid.nx, c->grid.ny, c->grid.nz, ihx2, ihy2,
+                                         ihz2, g, c->fine.m, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->fine.T,
+                                         c->fine.S, c->flags);
+}
+
+void launch_pivots(msmg_ctx* c, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  const size_t sm = (size_t)g.epc * (3 * g.P + g.nb) * sizeof(double);
+  cudaFuncSetAttribute(k_pivots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_pivots<<<fine_grid(c, g), fine_threads(g), sm, s>>>(c->fine.T, c->n, g, c->fine.m, c->fine.nbr, c->fine.invd,
+                                                         c->flags);
+}
+
+void launch_nat_to_blk(msmg_ctx* c, const double* in, double* out, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  k_perm<true, double, double><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>(
+      in, out, c->n, g, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->grid.nx, c->grid.ny, 1);
+}
+
+void launch_blk_to_nat(msmg_ctx* c, const double* in, double* out, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  k_perm<false, double, double><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>(
+      in, out, c->n, g, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->grid.nx, c->grid.ny, 1);
+}
+
+void launch_faces_to_nat(msmg_ctx* c, double* out, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  k_perm<false, double, double><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>(
+      c->fine.T, out, c->n, g, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->grid.nx, c->grid.ny, 3);
+}
+
+void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  const size_t sm = (size_t)g.epc * 4 * g.P * sizeof(double);
+  cudaFuncSetAttribute(k_matvec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_matvec<false><<<fine_grid(c, g), fine_threads(g), sm, s>>>(p, q, c->fine.T, c->n, g, c->fine.m, c->fine.nbr,
+                                                                c->red, nullptr);
+}
+
+void launch_matvec_pq(msmg_ctx* c, const double* p, double* q, PcgScalars* sc, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  const size_t sm = (size_t)g.epc * 4 * g.P * sizeof(double);
+  cudaFuncSetAttribute(k_matvec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_matvec<true><<<fine_grid(c, g), fine_threads(g), sm, s>>>(p, q, c->fine.T, c->n, g, c->fine.m, c->fine.nbr,
+                                                               c->red, sc);
+}
+
+// Fine-level pieces of the V-cycle, dispatched on the precision mode.
+template <typename V, typename BT>
+static void fine_down_t(msmg_ctx* c, const double* f, V* u, double* rc, const V* T, const V* invd, const BT* Phi,
+                        PcgScalars* sc, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  const unsigned grid = fine_grid(c, g), thr = fine_threads(g);
+  const size_t sm1 = (size_t)g.epc * (3 * g.P + g.nb) * sizeof(V);
+  cudaFuncSetAttribute(k_smooth_first<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  k_smooth_first<V><<<grid, thr, sm1, s>>>(f, u, T, invd, c->n, g, c->fine.m, c->fine.nbr, sc);
+  const int L = c->fine.L;
+  const size_t red = ((g.nb & 31) == 0 ? (size_t)g.epc * L * (g.nb / 32) : (size_t)g.epc * g.nb) * sizeof(double);
+  const size_t sm2 = (size_t)g.epc * 4 * g.P * sizeof(V) + red + 16;
+  cudaFuncSetAttribute(k_resid_restrict<V, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  k_resid_restrict<V, BT><<<grid, thr, sm2, s>>>(f, u, T, Phi, L, rc, c->n, g, c->fine.m, c->fine.nbr, sc);
+}
+
+template <typename V, typename BT>
+static void fine_up_t(msmg_ctx* c, const double* f, V* u, const double* ec, double* z, const V* T, const V* invd,
+                      const BT* Phi, const double* qv, PcgScalars* sc, cudaStream_t s) {
+  const Geo g = fine_geo(c);
+  const unsigned grid = fine_grid(c, g), thr = fine_threads(g);
+  k_prolong<V, BT><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>(u, Phi, c->fine.L, ec, c->n, g.nb, sc);
+  const size_t sm = (size_t)g.epc * (4 * g.P + g.nb) * sizeof(V);
+  cudaFuncSetAttribute(k_resid_smooth<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_resid_smooth<V, true><<<grid, thr, sm, s>>>(f, u, T, invd, c->n, g, c->fine.m, c->fine.nbr, z, qv, c->red, sc);
+}
+
+void fine_down(msmg_ctx* c, const double* f, double* rc, PcgScalars* sc, cudaStream_t s) {
+  if (c->opts.precision == MSMG_MIXED)
+    fine_down_t<float, __nv_bfloat16>(c, f, (float*)c->sb.vu[1], rc, c->fine.T32, c->fine.invd32, c->fine.Phi16, sc, s);
+  else
+    fine_down_t<double, double>(c, f, (double*)c->sb.vu[1], rc, c->fine.T, c->fine.invd, c->fine.Phi, sc, s);
+}
+
+void fine_up(msmg_ctx* c, const double* f, const double* ec, double* z, const double* qv, PcgScalars* sc,
+             cudaStream_t s) {
+  if (c->opts.precision == MSMG_MIXED)
+    fine_up_t<float, __nv_bfloat16>(c, f, (float*)c->sb.vu[1], ec, z, c->fine.T32, c->fine.invd32, c->fine.Phi16, qv,
+                                    sc, s);
+  else
+    fine_up_t<double, double>(c, f, (double*)c->sb.vu[1], ec, z, c->fine.T, c->fine.invd, c->fine.Phi, qv, sc, s);
+}
+
+// ---- mixed-precision copies
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn((float)a[i]);
+}
+
+void launch_mixed_copies(msmg_ctx* c, cudaStream_t s) {
+  if (c->opts.precision != MSMG_MIXED) return;
+  const int64_t n = c->n;
+  k_to_f32<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->fine.T, c->fine.T32, 3 * n);
+  k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->fine.invd, c->fine.invd32, n);
+  const int64_t np = c->fine.m * c->fine.L * c->fine.nb;
+  k_to_bf16<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(c->fine.Phi, c->fine.Phi16, np);
+}
+
+}  // namespace msmg

@@ -1,0 +1,192 @@
+// Internal declarations shared by the msmg CUDA translation units.
+//
+// Data layout in device memory (all inside the caller's workspace):
+//   * Element ordering is hierarchical at every level: the elements of E_l are
+//     numbered parent-major (the r^3 children of one element of E_{l+1} are
+//     consecutive, in lexicographic order inside the parent), and the elements
+//     of the top element level E_{L-1} are lexicographic.  So every block of
+//     every smoother and every local spectral problem is one contiguous range.
+//   * Fine-level vectors are block-major: cell (element e, local p) sits at
+//     e * nb + p with p = lx + bx*(ly + by*lz).  Each element's data is one
+//     contiguous, coalesced chunk.
+//   * A level-l vector (l >= 2) stores the coordinates of element e of E_{l-1}
+//     at e * L + k, k < L.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include "../../include/msmg.h"
+
+namespace msmg {
+
+constexpr int kMaxLevels = MSMG_MAX_LEVELS;
+
+// ---------------------------------------------------------------- errors
+#define MSMG_CUDA_TRY(expr)                                                   \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess) { ::msmg::set_last_cuda_error(_e); return MSMG_ERR_CUDA; } \
+  } while (0)
+void set_last_cuda_error(cudaError_t e);
+
+// ---------------------------------------------------------------- arena
+// Bump allocator over the caller's workspace.  With base == nullptr it only
+// measures (used by msmg_workspace_size).
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  size_t cap = 0;
+  template <typename T>
+  T* take(size_t count, size_t align = 256) {
+    off = (off + align - 1) / align * align;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------- PCG scalars
+// One record per right-hand side, in device memory.  Written by the
+// last-finishing CTA of each reducing kernel.
+struct PcgScalars {
+  double bb;         // ||b||^2 after mean removal
+  double tol2;       // (rtol ||b||)^2
+  double rz;         // r^T z (current)
+  double rz_old;     // previous r^T z
+  double rz_mix;     // z_new^T r_old (flexible beta)
+  double pq;         // p^T A p
+  double rr;         // ||r||^2
+  double alpha, beta;
+  double mean;       // removed rhs mean
+  int iter;          // completed iterations
+  int done;          // 1 converged, 2 breakdown, 3 max_iter
+  int max_iter;
+  int flexible;
+};
+
+// A deterministic grid reduction slot: per-CTA partials, a ticket counter and
+// a result.  The last CTA to finish sums the partials in index order.
+struct RedSlot {
+  double* partials;     // [kMaxRedBlocks * kRedWidth]
+  unsigned* counter;    // zero between uses
+};
+constexpr int kMaxRedBlocks = 4096;
+constexpr int kRedWidth = 4;   // up to 4 simultaneous sums per reduction
+
+// ---------------------------------------------------------------- levels
+struct FineLevel {
+  int bx, by, bz, nb;           // element size and cells per element
+  int gx, gy, gz;               // element grid
+  int64_t m;                    // elements
+  int64_t n;                    // cells
+  int L;                        // eigenvectors per element (n_eig[0])
+  int nu;
+  int* lex_of_hid;              // [m] lexicographic element index of hierarchical index
+  int* nbr;                     // [m][6] neighbour hid (-x,+x,-y,+y,-z,+z), -1 on boundary
+  double* T;                    // [3][n] face coefficients (FP64, block-major)
+  double* S;                    // [n] Tr K~
+  double* invd;                 // [n] inverse IC(0) pivots
+  double* Phi;                  // [m][L][nb] S-orthonormal basis
+  double* lam;                  // [m][L]
+  float* T32;                   // mixed-precision copies (nullptr in FP64 mode)
+  float* invd32;
+  __nv_bfloat16* Phi16;
+};
+
+struct CoarseLevel {            // level l >= 2 (W_l)
+  int l;
+  int gx, gy, gz;               // grid of E_{l-1} (elements carrying L dofs each)
+  int64_t me;                   // elements of E_{l-1}
+  int L;                        // dofs per element = n_eig[l-2]
+  int64_t n;                    // me * L
+  int nu;
+  int* lex_of_hid;              // [me]
+  int* nbr;                     // [me][6]
+  double* Ad;                   // [me][L][L] diagonal blocks of A_l
+  double* Ao;                   // [me][3][L][L] A_l[a, a+e_d], d = x, y, z
+  double* F;                    // [me][6][L][L] face terms (setup only)
+  double* z;                    // [n] null vector of A_l
+  // smoother / restriction towards level l+1 (absent at the coarsest level)
+  int rx, ry, rz, nchild;       // children per parent (ratio of E_l over E_{l-1})
+  int64_t mP;                   // parents (elements of E_l)
+  int nP;                       // dofs per parent = nchild * L
+  int Lnext;                    // n_eig[l-1]
+  double* Minv;                 // [mP][nP][nP] inverse of each parent's diagonal block
+  double* Psi;                  // [mP][Lnext][nP]
+  double* lamP;                 // [mP][Lnext]
+  // coarsest only
+  double* pinv;                 // [n][n]
+};
+
+struct SolveBuffers {
+  // fine level, FP64, block-major
+  double *b, *x, *r, *z, *p0, *p1, *q;
+  // V-cycle work on every level: f (right side), u (iterate), w (scratch)
+  void* vf[kMaxLevels];
+  void* vu[kMaxLevels];
+  void* vw[kMaxLevels];
+  PcgScalars* sc;               // [n_rhs]
+  int n_rhs;
+};
+
+}  // namespace msmg
+
+struct msmg_ctx {
+  msmg_grid grid;
+  msmg_options opts;
+  int nL;                                       // n_levels
+  int64_t n;                                    // fine cells
+  msmg::FineLevel fine;
+  msmg::CoarseLevel lev[msmg::kMaxLevels];      // lev[l] for l = 2 .. nL (index by level)
+  msmg::SolveBuffers sb;
+  msmg::RedSlot red;                            // reduction scratch
+  double* dtmp;                                 // setup scratch (dense coarsest work etc.)
+  int* flags;                                   // [4] device error flags
+  int* hflags;                                  // pinned host mirror
+  size_t ws_bytes;
+  msmg_setup_info info;
+  cudaEvent_t ev0, ev1;
+  int device;
+  int max_rhs;
+};
+
+namespace msmg {
+// ---------------------------------------------------------------- plan
+int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& ar, msmg_ctx* ctx);
+int validate(const msmg_grid* g, const msmg_options* o);
+
+// ---------------------------------------------------------------- launchers (fine level)
+void launch_faces(msmg_ctx* c, const void* kappa, int comps, int dtype, cudaStream_t s);
+void launch_pivots(msmg_ctx* c, cudaStream_t s);
+void launch_nat_to_blk(msmg_ctx* c, const double* in, double* out, cudaStream_t s);
+void launch_blk_to_nat(msmg_ctx* c, const double* in, double* out, cudaStream_t s);
+void launch_faces_to_nat(msmg_ctx* c, double* out, cudaStream_t s);
+// q = A p (FP64, block-major).  If dot_out != nullptr also p.q into it.
+void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s);
+
+// ---------------------------------------------------------------- setup
+int launch_level1_eigen(msmg_ctx* c, cudaStream_t s);
+void launch_level1_galerkin(msmg_ctx* c, cudaStream_t s);
+int launch_coarse_setup(msmg_ctx* c, int l, cudaStream_t s);
+int launch_coarsest(msmg_ctx* c, cudaStream_t s);
+void launch_basis_export(msmg_ctx* c, int level, double* basis, double* lam, bool import, cudaStream_t s);
+void launch_operator_export(msmg_ctx* c, int level, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- solve
+// V-cycle on level 1: u = P^{-1} f, block-major FP64 in/out.  If rz != nullptr,
+// the final kernel also accumulates f.u into sc (PCG reduction).
+void vcycle(msmg_ctx* c, const double* f, double* u, PcgScalars* sc, cudaStream_t s);
+int pcg_solve(msmg_ctx* c, const double* rhs_nat, double* x_nat, double rtol, int max_iter, int flags,
+              cudaStream_t s, msmg_solve_info* info);
+double dot_host(msmg_ctx* c, const double* a, const double* b, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace msmg

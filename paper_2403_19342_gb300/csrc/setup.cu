@@ -1,0 +1,676 @@
+// Set-up phase kernels (Section 3, Section 5), FP64.
+//
+//  * Level-1 local spectral problem (Eq. (spepb)) on small elements: the
+//    symmetric form A~ = S^{-1/2} A_K S^{-1/2} is diagonalised by a parallel
+//    cyclic Jacobi method in shared memory; Phi = S^{-1/2} Y keeps the L
+//    smallest eigenvectors, which are then S-orthonormal.
+//  * Level-1 Galerkin blocks of A_2 = R_1 A R_1^T: diagonal Phi_a^T A_aa Phi_a,
+//    couplings -sum_faces T Phi_a(c) Phi_b(c')^T, and per-face terms
+//    Phi_a^T diag(T on the face) Phi_a used to pose the next level's problems.
+//  * Level l >= 2, per parent P: the left matrix of Eq. (spectral cc) equals
+//    the parent's diagonal block of A_l minus the face terms of its children
+//    on P's boundary (the right matrix is I); its smallest eigenvectors Psi_P;
+//    the Galerkin blocks of A_{l+1}; the parent's face terms; and the inverse
+//    of the parent's diagonal block (the block-Jacobi smoother of level l).
+//  * Coarsest level: A_L + sigma z z^T / |z|^2 (z spans null(A_L)) is inverted
+//    by Gauss-Jordan elimination and projected, giving the Moore-Penrose
+//    inverse A_L^dagger used by Algorithm 1's coarsest correction.
+#include "msmg_internal.cuh"
+#include "reduce.cuh"
+#include <cmath>
+
+namespace msmg {
+
+// ------------------------------------------------------------------ Jacobi
+// Parallel cyclic Jacobi (round-robin pairing) on the n x n symmetric matrix A
+// in shared memory; V receives the eigenvectors (columns).  On return the
+// diagonal of A holds the eigenvalues.
+__device__ void jacobi_eig(double* A, double* V, int n, double* cs, int* pr, double* red, int max_sweeps,
+                           double rtol) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int npad = n + (n & 1);
+  const int half = npad / 2;
+  for (int i = tid; i < n * n; i += nthr) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double v[2] = {0.0, 0.0};
+    for (int i = tid; i < n * n; i += nthr) {
+      const double a = A[i];
+      v[1] += a * a;
+      if (i / n != i % n) v[0] += a * a;
+    }
+    block_sum<2>(v, red + 2);
+    if (tid == 0) { red[0] = v[0]; red[1] = v[1]; }
+    __syncthreads();
+    const bool conv = red[0] <= rtol * rtol * red[1];
+    __syncthreads();
+    if (conv) break;
+    for (int r = 0; r < npad - 1; ++r) {
+      for (int i = tid; i < half; i += nthr) {
+        int pa = (i == 0) ? 0 : 1 + ((i - 1 + r) % (npad - 1));
+        const int j = npad - 1 - i;
+        int pb = 1 + ((j - 1 + r) % (npad - 1));
+        if (pa > pb) { int t = pa; pa = pb; pb = t; }
+        double c = 1.0, s = 0.0;
+        if (pb < n) {
+          const double apq = A[pa * n + pb];
+          if (fabs(apq) > 1e-300) {
+            const double theta = (A[pb * n + pb] - A[pa * n + pa]) / (2.0 * apq);
+            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        cs[2 * i] = c;
+        cs[2 * i + 1] = s;
+        pr[2 * i] = pa;
+        pr[2 * i + 1] = pb;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nthr) {     // rows: A <- J^T A
+        const int i = idx / n, col = idx % n;
+        const int p = pr[2 * i], q = pr[2 * i + 1];
+        if (q >= n) continue;
+        const double c = cs[2 * i], s = cs[2 * i + 1];
+        const double ap = A[p * n + col], aq = A[q * n + col];
+        A[p * n + col] = c * ap - s * aq;
+        A[q * n + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nthr) {     // columns: A <- A J, V <- V J
+        const int i = idx / n, row = idx % n;
+        const int p = pr[2 * i], q = pr[2 * i + 1];
+        if (q >= n) continue;
+        const double c = cs[2 * i], s = cs[2 * i + 1];
+        const double ap = A[row * n + p], aq = A[row * n + q];
+        A[row * n + p] = c * ap - s * aq;
+        A[row * n + q] = s * ap + c * aq;
+        const double vp = V[row * n + p], vq = V[row * n + q];
+        V[row * n + p] = c * vp - s * vq;
+        V[row * n + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// order[k] = index of the k-th smallest diagonal entry of A (stable).
+__device__ void sort_diag(const double* A, int n, int* order) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = A[i * n + i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = A[j * n + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    order[rank] = i;
+  }
+  __syncthreads();
+}
+
+// In-place Gauss-Jordan inverse of an SPD n x n matrix in shared memory.
+__device__ void gj_inverse(double* A, int n, double* rowk, double* colk) {
+  for (int k = 0; k < n; ++k) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      rowk[i] = A[k * n + i];
+      colk[i] = A[i * n + k];
+    }
+    __syncthreads();
+    const double piv = colk[k];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      double v;
+      if (i == k && j == k) v = 1.0 / piv;
+      else if (i == k) v = rowk[j] / piv;
+      else if (j == k) v = -colk[i] / piv;
+      else v = A[idx] - colk[i] * rowk[j] / piv;
+      A[idx] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Positive double values order like their bit patterns: atomic max via int64.
+__device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// ------------------------------------------------------------------ level 1 eigen (dense)
+// One CTA per element, nb <= 96.  stats[0] <- max eigen-residual.
+__global__ void k_eig_l1_jacobi(const double* __restrict__ T, const double* __restrict__ S, int64_t n, int bx, int by,
+                                int bz, int64_t m, int L, double* __restrict__ Phi, double* __restrict__ lam,
+                                double* stats) {
+  extern __shared__ double sm[];
+  const int nb = bx * by * bz;
+  double* A = sm;
+  double* V = A + nb * nb;
+  double* A0 = V + nb * nb;
+  double* isq = A0 + nb * nb;
+  double* cs = isq + nb;
+  double* red = cs + nb + 2;
+  int* pr = reinterpret_cast<int*>(red + 72);
+  int* order = pr + nb + 2;
+  const int64_t e = blockIdx.x;
+  const double* Te = T + e * nb;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) isq[i] = 1.0 / sqrt(S[e * nb + i]);
+  for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) A[i] = 0.0;
+  __syncthreads();
+  // A~ = S^{-1/2} A_K S^{-1/2}: faces inside the element only (Eq. (spepb))
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    const int lx = c % bx, ly = (c / bx) % by, lz = c / (bx * by);
+    const int lc[3] = {lx, ly, lz}, bd[3] = {bx, by, bz}, st[3] = {1, bx, bx * by};
+    double diag = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      if (lc[d] + 1 < bd[d]) {
+        const double t = Te[(int64_t)d * n + c];
+        diag += t;
+        A[c * nb + c + st[d]] = -t * isq[c] * isq[c + st[d]];
+      }
+      if (lc[d] > 0) {
+        const double t = Te[(int64_t)d * n + c - st[d]];
+        diag += t;
+        A[c * nb + c - st[d]] = -t * isq[c] * isq[c - st[d]];
+      }
+    }
+    A[c * nb + c] = diag * isq[c] * isq[c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) A0[i] = A[i];
+  __syncthreads();
+  jacobi_eig(A, V, nb, cs, pr, red, 40, 1e-15);
+  sort_diag(A, nb, order);
+  // Phi = S^{-1/2} y for the L smallest; eigen-residual ||A~ y - theta y||
+  for (int idx = threadIdx.x; idx < L * nb; idx += blockDim.x) {
+    const int k = idx / nb, c = idx % nb;
+    const int col = order[k];
+    Phi[(e * L + k) * nb + c] = V[c * nb + col] * isq[c];
+  }
+  for (int k = threadIdx.x; k < L; k += blockDim.x) lam[e * L + k] = A[order[k] * nb + order[k]];
+  double res = 0.0;
+  for (int k = 0; k < L; ++k) {
+    const int col = order[k];
+    const double th = A[col * nb + col];
+    double v[1] = {0.0};
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+      double acc = -th * V[c * nb + col];
+      for (int j = 0; j < nb; ++j) acc += A0[c * nb + j] * V[j * nb + col];
+      v[0] += acc * acc;
+    }
+    block_sum<1>(v, red + 2);
+    if (threadIdx.x == 0) res = fmax(res, sqrt(v[0]));
+  }
+  if (threadIdx.x == 0) atomic_max_pos(&stats[0], res);
+}
+
+// ------------------------------------------------------------------ level 1 Galerkin
+// One CTA per element a.  Outputs: Ad[a] = Phi_a^T A_aa Phi_a, Ao[a][d] = A_2[a, a+e_d],
+// F[a][f] = Phi_a^T diag(T on face f) Phi_a, z[a] = Phi_a^T S 1.
+__global__ void k_galerkin1(const double* __restrict__ T, const double* __restrict__ S, int64_t n, int bx, int by,
+                            int bz, int64_t m, const int* __restrict__ nbr, int L, const double* __restrict__ Phi,
+                            double* __restrict__ Ad, double* __restrict__ Ao, double* __restrict__ F,
+                            double* __restrict__ z) {
+  extern __shared__ double sm[];
+  const int nb = bx * by * bz;
+  double* Ph = sm;            // [L][nb]
+  double* W = Ph + L * nb;    // [L][nb] = A_aa phi
+  double* Tm = W + L * nb;    // [3][nb] coefficient of the -d face of each cell
+  const int64_t a = blockIdx.x;
+  for (int i = threadIdx.x; i < L * nb; i += blockDim.x) Ph[i] = Phi[a * L * nb + i];
+  const int bd[3] = {bx, by, bz}, st[3] = {1, bx, bx * by};
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    const int lc[3] = {c % bx, (c / bx) % by, c / (bx * by)};
+    for (int d = 0; d < 3; ++d) {
+      double t = 0.0;
+      if (lc[d] > 0) t = T[(int64_t)d * n + a * nb + c - st[d]];
+      else {
+        const int nbm = nbr[a * 6 + 2 * d];
+        if (nbm >= 0) t = T[(int64_t)d * n + (int64_t)nbm * nb + c + (bd[d] - 1) * st[d]];
+      }
+      Tm[d * nb + c] = t;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    const int lc[3] = {c % bx, (c / bx) % by, c / (bx * by)};
+    double diag = 0.0;
+    for (int d = 0; d < 3; ++d) diag += T[(int64_t)d * n + a * nb + c] + Tm[d * nb + c];
+    for (int k = 0; k < L; ++k) {
+      double acc = diag * Ph[k * nb + c];
+      for (int d = 0; d < 3; ++d) {
+        if (lc[d] + 1 < bd[d]) acc -= T[(int64_t)d * n + a * nb + c] * Ph[k * nb + c + st[d]];
+        if (lc[d] > 0) acc -= Tm[d * nb + c] * Ph[k * nb + c - st[d]];
+      }
+      W[k * nb + c] = acc;
+    }
+  }
+  __syncthreads();
+  const int L2 = L * L;
+  const int nout = L2 + 6 * L2 + 3 * L2 + L;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    if (o < L2) {
+      const int k = o / L, mm = o % L;
+      if (k > mm) continue;
+      double acc = 0.0, acc2 = 0.0;
+      for (int c = 0; c < nb; ++c) { acc += Ph[k * nb + c] * W[mm * nb + c]; acc2 += Ph[mm * nb + c] * W[k * nb + c]; }
+      const double v = 0.5 * (acc + acc2);
+      Ad[a * L2 + k * L + mm] = v;
+      Ad[a * L2 + mm * L + k] = v;
+    } else if (o < 7 * L2) {
+      const int oo = o - L2;
+      const int f = oo / L2, k = (oo % L2) / L, mm = oo % L;
+      const int d = f / 2;
+      const bool plus = f & 1;
+      const int u = (d + 1) % 3, w = (d + 2) % 3;
+      double acc = 0.0;
+      for (int iu = 0; iu < bd[u]; ++iu)
+        for (int iw = 0; iw < bd[w]; ++iw) {
+          const int c = (plus ? bd[d] - 1 : 0) * st[d] + iu * st[u] + iw * st[w];
+          const double t = plus ? T[(int64_t)d * n + a * nb + c] : Tm[d * nb + c];
+          acc += t * Ph[k * nb + c] * Ph[mm * nb + c];
+        }
+      F[(a * 6 + f) * L2 + k * L + mm] = acc;
+    } else if (o < 10 * L2) {
+      const int oo = o - 7 * L2;
+      const int d = oo / L2, k = (oo % L2) / L, mm = oo % L;
+      const int nbp = nbr[a * 6 + 2 * d + 1];
+      double acc = 0.0;
+      if (nbp >= 0) {
+        const int u = (d + 1) % 3, w = (d + 2) % 3;
+        const double* Pn = Phi + ((int64_t)nbp * L + mm) * nb;
+        for (int iu = 0; iu < bd[u]; ++iu)
+          for (int iw = 0; iw < bd[w]; ++iw) {
+            const int c = (bd[d] - 1) * st[d] + iu * st[u] + iw * st[w];
+            const int c2 = iu * st[u] + iw * st[w];
+            acc -= T[(int64_t)d * n + a * nb + c] * Ph[k * nb + c] * Pn[c2];
+          }
+      }
+      Ao[(a * 3 + d) * L2 + k * L + mm] = acc;
+    } else {
+      const int k = o - 10 * L2;
+      double acc = 0.0;
+      for (int c = 0; c < nb; ++c) acc += Ph[k * nb + c] * S[a * nb + c];
+      z[a * L + k] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ coarse levels
+// One CTA per parent P of level l.  nP <= 96.
+__global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, int given) {
+  extern __shared__ double sm[];
+  const int nP = lv.nP, L = lv.L, L2 = L * L, Ln = lv.Lnext, Ln2 = Ln * Ln;
+  double* A = sm;                 // parent's diagonal block of A_l
+  double* N = A + nP * nP;        // left matrix of Eq. (spectral cc); then Psi
+  double* V = N + nP * nP;        // eigenvectors; then A Psi^T
+  double* cs = V + nP * nP;
+  double* red = cs + nP + 2;
+  int* pr = reinterpret_cast<int*>(red + 72);
+  int* order = pr + nP + 2;
+  const int64_t P = blockIdx.x;
+  const int rx = lv.rx, ry = lv.ry;
+  // assemble A_P
+  for (int idx = threadIdx.x; idx < nP * nP; idx += blockDim.x) {
+    const int i = idx / nP, j = idx % nP;
+    const int ca = i / L, k = i % L, cb = j / L, mm = j % L;
+    const int64_t a = P * lv.nchild + ca, b = P * lv.nchild + cb;
+    double v = 0.0;
+    if (ca == cb) v = lv.Ad[a * L2 + k * L + mm];
+    else {
+      for (int d = 0; d < 3; ++d) {
+        if (lv.nbr[a * 6 + 2 * d + 1] == (int)b) v = lv.Ao[(a * 3 + d) * L2 + k * L + mm];
+        if (lv.nbr[b * 6 + 2 * d + 1] == (int)a) v = lv.Ao[(b * 3 + d) * L2 + mm * L + k];
+      }
+    }
+    A[idx] = v;
+    // Neumann on P: remove the children's face terms on P's boundary
+    double nv = v;
+    if (ca == cb) {
+      const int cx = ca % rx, cy = (ca / rx) % ry, cz = ca / (rx * ry);
+      const int cc[3] = {cx, cy, cz}, rr[3] = {lv.rx, lv.ry, lv.rz};
+      for (int d = 0; d < 3; ++d) {
+        if (cc[d] == 0) nv -= lv.F[(a * 6 + 2 * d) * L2 + k * L + mm];
+        if (cc[d] == rr[d] - 1) nv -= lv.F[(a * 6 + 2 * d + 1) * L2 + k * L + mm];
+      }
+    }
+    N[idx] = nv;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nP * nP; idx += blockDim.x) {   // symmetrise
+    const int i = idx / nP, j = idx % nP;
+    if (i < j) {
+      const double s = 0.5 * (N[idx] + N[j * nP + i]);
+      N[idx] = s;
+      N[j * nP + i] = s;
+    }
+  }
+  __syncthreads();
+  if (!given) {
+    jacobi_eig(N, V, nP, cs, pr, red, 40, 1e-15);
+    sort_diag(N, nP, order);
+    for (int j = threadIdx.x; j < Ln; j += blockDim.x) lv.lamP[P * Ln + j] = N[order[j] * nP + order[j]];
+    __syncthreads();
+    // Psi (rows = eigenvectors)
+    for (int idx = threadIdx.x; idx < Ln * nP; idx += blockDim.x) {
+      const int j = idx / nP, i = idx % nP;
+      lv.Psi[(P * Ln + j) * nP + i] = V[i * nP + order[j]];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < Ln * nP; idx += blockDim.x) {
+    const int j = idx / nP, i = idx % nP;
+    N[j * nP + i] = lv.Psi[(P * Ln + j) * nP + i];
+  }
+  __syncthreads();
+  // V <- A Psi^T  (nP x Ln)
+  for (int idx = threadIdx.x; idx < nP * Ln; idx += blockDim.x) {
+    const int i = idx / Ln, j = idx % Ln;
+    double acc = 0.0;
+    for (int q = 0; q < nP; ++q) acc += A[i * nP + q] * N[j * nP + q];
+    V[idx] = acc;
+  }
+  __syncthreads();
+  // next level: diagonal block, face terms, null vector
+  for (int o = threadIdx.x; o < Ln2 + 6 * Ln2 + Ln; o += blockDim.x) {
+    if (o < Ln2) {
+      const int j = o / Ln, jj = o % Ln;
+      if (j > jj) continue;
+      double acc = 0.0, acc2 = 0.0;
+      for (int i = 0; i < nP; ++i) { acc += N[j * nP + i] * V[i * Ln + jj]; acc2 += N[jj * nP + i] * V[i * Ln + j]; }
+      const double v = 0.5 * (acc + acc2);
+      nx.Ad[P * Ln2 + j * Ln + jj] = v;
+      nx.Ad[P * Ln2 + jj * Ln + j] = v;
+    } else if (o < 7 * Ln2) {
+      const int oo = o - Ln2;
+      const int f = oo / Ln2, j = (oo % Ln2) / Ln, jj = oo % Ln;
+      const int d = f / 2;
+      const bool plus = f & 1;
+      const int rr[3] = {lv.rx, lv.ry, lv.rz};
+      double acc = 0.0;
+      for (int ca = 0; ca < lv.nchild; ++ca) {
+        const int cc[3] = {ca % rx, (ca / rx) % ry, ca / (rx * ry)};
+        if (cc[d] != (plus ? rr[d] - 1 : 0)) continue;
+        const int64_t a = P * lv.nchild + ca;
+        const double* Fa = lv.F + (a * 6 + f) * L2;
+        for (int k = 0; k < L; ++k) {
+          const double pj = N[j * nP + ca * L + k];
+          if (pj == 0.0) continue;
+          double t = 0.0;
+          for (int mm = 0; mm < L; ++mm) t += Fa[k * L + mm] * N[jj * nP + ca * L + mm];
+          acc += pj * t;
+        }
+      }
+      nx.F[(P * 6 + f) * Ln2 + j * Ln + jj] = acc;
+    } else {
+      const int j = o - 7 * Ln2;
+      double acc = 0.0;
+      for (int i = 0; i < nP; ++i) acc += N[j * nP + i] * lv.z[P * nP + i];
+      nx.z[P * Ln + j] = acc;
+    }
+  }
+  __syncthreads();
+  // smoother: inverse of the parent's diagonal block
+  gj_inverse(A, nP, cs, V);
+  for (int idx = threadIdx.x; idx < nP * nP; idx += blockDim.x) {
+    const double v = A[idx];
+    if (!isfinite(v)) atomic_max_pos(&stats[1], 1.0);
+    lv.Minv[(size_t)P * nP * nP + idx] = v;
+  }
+}
+
+// Couplings of A_{l+1}: Ao[P][d] = sum over P's children a on its +d face of
+// Psi_P[:, a]^T Ao_l[a][d] Psi_Q[:, a'], Q = P + e_d, a' = a's +d neighbour.
+__global__ void k_coarse_galerkin_off(CoarseLevel lv, CoarseLevel nx) {
+  const int64_t P = blockIdx.x;
+  const int L = lv.L, L2 = L * L, Ln = lv.Lnext, Ln2 = Ln * Ln, nP = lv.nP;
+  const int rr[3] = {lv.rx, lv.ry, lv.rz};
+  for (int o = threadIdx.x; o < 3 * Ln2; o += blockDim.x) {
+    const int d = o / Ln2, j = (o % Ln2) / Ln, jj = o % Ln;
+    const int Q = nx.nbr[P * 6 + 2 * d + 1];
+    double acc = 0.0;
+    if (Q >= 0) {
+      for (int ca = 0; ca < lv.nchild; ++ca) {
+        const int cc[3] = {ca % lv.rx, (ca / lv.rx) % lv.ry, ca / (lv.rx * lv.ry)};
+        if (cc[d] != rr[d] - 1) continue;
+        int cb3[3] = {cc[0], cc[1], cc[2]};
+        cb3[d] = 0;
+        const int cb = cb3[0] + lv.rx * (cb3[1] + lv.ry * cb3[2]);
+        const int64_t a = P * lv.nchild + ca;
+        const double* ao = lv.Ao + (a * 3 + d) * L2;
+        const double* psP = lv.Psi + ((size_t)P * Ln + j) * nP + ca * L;
+        const double* psQ = lv.Psi + ((size_t)Q * Ln + jj) * nP + cb * L;
+        for (int k = 0; k < L; ++k) {
+          double t = 0.0;
+          for (int mm = 0; mm < L; ++mm) t += ao[k * L + mm] * psQ[mm];
+          acc += psP[k] * t;
+        }
+      }
+    }
+    nx.Ao[(P * 3 + d) * Ln2 + j * Ln + jj] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ coarsest
+// Dense A_L (hierarchical order) from the block stencil.  out zeroed beforehand.
+__global__ void k_assemble_dense(CoarseLevel lv, double* __restrict__ out) {
+  const int64_t a = blockIdx.x;
+  const int L = lv.L, L2 = L * L;
+  const int64_t n = lv.n;
+  for (int o = threadIdx.x; o < L2; o += blockDim.x) {
+    const int k = o / L, mm = o % L;
+    out[(a * L + k) * n + a * L + mm] = lv.Ad[a * L2 + o];
+    for (int d = 0; d < 3; ++d) {
+      const int b = lv.nbr[a * 6 + 2 * d + 1];
+      if (b < 0) continue;
+      const double v = lv.Ao[(a * 3 + d) * L2 + o];
+      out[(a * L + k) * n + (int64_t)b * L + mm] = v;
+      out[((int64_t)b * L + mm) * n + a * L + k] = v;
+    }
+  }
+}
+
+// scal[0] = |z|^2, scal[1] = trace(A)
+__global__ void k_coarsest_scalars(const double* __restrict__ A, const double* __restrict__ z, int64_t n,
+                                   double* scal) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    v[0] += z[i] * z[i];
+    v[1] += A[i * n + i];
+  }
+  __shared__ double sh[64];
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) { scal[0] = v[0]; scal[1] = v[1]; }
+}
+
+// A += sigma z z^T / |z|^2 with sigma = trace / n
+__global__ void k_add_null_shift(double* __restrict__ A, const double* __restrict__ z, int64_t n,
+                                 const double* scal) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  const double sigma = scal[1] / (double)n;
+  A[idx] += sigma * z[i] * z[j] / scal[0];
+}
+
+__global__ void k_gj_copy(const double* __restrict__ A, int64_t n, int64_t k, double* rowk, double* colk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rowk[i] = A[k * n + i];
+  colk[i] = A[i * n + k];
+}
+
+__global__ void k_gj_update(double* __restrict__ A, int64_t n, int64_t k, const double* __restrict__ rowk,
+                            const double* __restrict__ colk, double* stats) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  const double piv = colk[k];
+  double v;
+  if (i == k && j == k) {
+    v = 1.0 / piv;
+    if (!(piv > 0.0)) atomic_max_pos(&stats[1], 1.0);
+  } else if (i == k) v = rowk[j] / piv;
+  else if (j == k) v = -colk[i] / piv;
+  else v = A[idx] - colk[i] * rowk[j] / piv;
+  A[idx] = v;
+}
+
+// w = B zhat (B the inverse), gamma = zhat^T w; zhat = z / |z|
+__global__ void k_gemv_z(const double* __restrict__ B, const double* __restrict__ z, int64_t n, const double* scal,
+                         double* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const double inv = 1.0 / sqrt(scal[0]);
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32) acc += B[row * n + j] * z[j] * inv;
+  acc = warp_sum(acc);
+  if (lane == 0) w[row] = acc;
+}
+
+__global__ void k_dot_zw(const double* __restrict__ z, const double* __restrict__ w, int64_t n, double* scal) {
+  double v[1] = {0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v[0] += z[i] * w[i];
+  __shared__ double sh[32];
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0) scal[2] = v[0] / sqrt(scal[0]);
+}
+
+// pinv = (I - zz^T) B (I - zz^T) = B - w z^T - z w^T + gamma z z^T  (zhat normalised)
+__global__ void k_project(const double* __restrict__ B, const double* __restrict__ z, const double* __restrict__ w,
+                          int64_t n, const double* scal, double* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  const double inv = 1.0 / sqrt(scal[0]);
+  const double zi = z[i] * inv, zj = z[j] * inv;
+  out[idx] = B[idx] - w[i] * zj - zi * w[j] + scal[2] * zi * zj;
+}
+
+// ------------------------------------------------------------------ export / import
+// level 1: Phi[hid][L][nb] <-> out[lex][L][nb]; level >= 2: Psi[hidP][Ln][nP] <-> out[lexP][Ln][nP]
+__global__ void k_basis_xfer(double* __restrict__ dev, double* __restrict__ ext, const int* __restrict__ lex_of_hid,
+                             int64_t m, int64_t per, const double* __restrict__ lam_dev, double* __restrict__ lam_ext,
+                             int64_t lper, bool import) {
+  const int64_t e = blockIdx.x;
+  const int64_t lx = lex_of_hid[e];
+  for (int64_t i = threadIdx.x; i < per; i += blockDim.x) {
+    if (import) dev[e * per + i] = ext[lx * per + i];
+    else ext[lx * per + i] = dev[e * per + i];
+  }
+  if (!import && lam_ext)
+    for (int64_t i = threadIdx.x; i < lper; i += blockDim.x) lam_ext[lx * lper + i] = lam_dev[e * lper + i];
+}
+
+// dense operator in the paper's coordinate order (lexicographic elements)
+__global__ void k_operator_export(CoarseLevel lv, double* __restrict__ out) {
+  const int64_t a = blockIdx.x;
+  const int L = lv.L, L2 = L * L;
+  const int64_t n = lv.n;
+  const int64_t la = lv.lex_of_hid[a];
+  for (int o = threadIdx.x; o < L2; o += blockDim.x) {
+    const int k = o / L, mm = o % L;
+    out[(la * L + k) * n + la * L + mm] = lv.Ad[a * L2 + o];
+    for (int d = 0; d < 3; ++d) {
+      const int b = lv.nbr[a * 6 + 2 * d + 1];
+      if (b < 0) continue;
+      const int64_t lb = lv.lex_of_hid[b];
+      const double v = lv.Ao[(a * 3 + d) * L2 + o];
+      out[(la * L + k) * n + lb * L + mm] = v;
+      out[(lb * L + mm) * n + la * L + k] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host launchers
+static size_t jac_smem(int n, int extra_mats) {
+  return (size_t)extra_mats * n * n * sizeof(double) + (size_t)(2 * n + 4 + 72) * sizeof(double) +
+         (size_t)(2 * n + 4) * sizeof(int) + 64;
+}
+
+int launch_level1_eigen(msmg_ctx* c, cudaStream_t s) {
+  FineLevel& f = c->fine;
+  if (f.nb > 96) return MSMG_ERR_UNSUPPORTED;   // large elements use the subspace solver
+  const size_t sm = jac_smem(f.nb, 3);
+  cudaFuncSetAttribute(k_eig_l1_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_eig_l1_jacobi<<<(unsigned)f.m, 256, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, f.L, f.Phi, f.lam,
+                                                  c->dtmp);
+  return 0;
+}
+
+void launch_level1_galerkin(msmg_ctx* c, cudaStream_t s) {
+  FineLevel& f = c->fine;
+  CoarseLevel& l2 = c->lev[2];
+  const size_t sm = (size_t)(2 * f.L * f.nb + 3 * f.nb) * sizeof(double);
+  cudaFuncSetAttribute(k_galerkin1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const unsigned thr = f.nb >= 256 ? 256 : (unsigned)((f.nb + 31) / 32 * 32 < 64 ? 64 : (f.nb + 31) / 32 * 32);
+  k_galerkin1<<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, f.nbr, f.L, f.Phi, l2.Ad, l2.Ao,
+                                             l2.F, l2.z);
+}
+
+int launch_coarse_setup(msmg_ctx* c, int l, cudaStream_t s) {
+  CoarseLevel& lv = c->lev[l];
+  CoarseLevel& nx = c->lev[l + 1];
+  if (lv.nP > 96) return MSMG_ERR_UNSUPPORTED;
+  const size_t sm = jac_smem(lv.nP, 3);
+  cudaFuncSetAttribute(k_coarse_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 0);
+  k_coarse_galerkin_off<<<(unsigned)lv.mP, 128, 0, s>>>(lv, nx);
+  return 0;
+}
+
+// Same with the bases Psi already in place (imported): no eigensolve.
+int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s) {
+  CoarseLevel& lv = c->lev[l];
+  CoarseLevel& nx = c->lev[l + 1];
+  if (lv.nP > 96) return MSMG_ERR_UNSUPPORTED;
+  const size_t sm = jac_smem(lv.nP, 3);
+  cudaFuncSetAttribute(k_coarse_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 1);
+  k_coarse_galerkin_off<<<(unsigned)lv.mP, 128, 0, s>>>(lv, nx);
+  return 0;
+}
+
+int launch_coarsest(msmg_ctx* c, cudaStream_t s) {
+  CoarseLevel& lv = c->lev[c->nL];
+  const int64_t n = lv.n;
+  double* B = c->dtmp + 16;
+  double* rowk = B + n * n;
+  double* colk = rowk + n;
+  double* w = colk + n;
+  double* scal = c->dtmp + 4;
+  MSMG_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)n * n * sizeof(double), s));
+  k_assemble_dense<<<(unsigned)lv.me, 64, 0, s>>>(lv, B);
+  k_coarsest_scalars<<<1, 256, 0, s>>>(B, lv.z, n, scal);
+  const unsigned g2 = (unsigned)((n * n + 255) / 256);
+  k_add_null_shift<<<g2, 256, 0, s>>>(B, lv.z, n, scal);
+  const unsigned g1 = (unsigned)((n + 255) / 256);
+  for (int64_t k = 0; k < n; ++k) {
+    k_gj_copy<<<g1, 256, 0, s>>>(B, n, k, rowk, colk);
+    k_gj_update<<<g2, 256, 0, s>>>(B, n, k, rowk, colk, c->dtmp);
+  }
+  k_gemv_z<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(B, lv.z, n, scal, w);
+  k_dot_zw<<<1, 256, 0, s>>>(lv.z, w, n, scal);
+  k_project<<<g2, 256, 0, s>>>(B, lv.z, w, n, scal, lv.pinv);
+  return 0;
+}
+
+void launch_basis_export(msmg_ctx* c, int level, double* basis, double* lam, bool import, cudaStream_t s) {
+  if (level == 1) {
+    FineLevel& f = c->fine;
+    k_basis_xfer<<<(unsigned)f.m, 256, 0, s>>>(f.Phi, basis, f.lex_of_hid, f.m, (int64_t)f.L * f.nb, f.lam, lam, f.L,
+                                               import);
+  } else {
+    CoarseLevel& lv = c->lev[level];
+    const CoarseLevel& up = c->lev[level + 1];
+    k_basis_xfer<<<(unsigned)lv.mP, 256, 0, s>>>(lv.Psi, basis, up.lex_of_hid, lv.mP, (int64_t)lv.Lnext * lv.nP,
+                                                 lv.lamP, lam, lv.Lnext, import);
+  }
+}
+
+void launch_operator_export(msmg_ctx* c, int level, double* out, cudaStream_t s) {
+  CoarseLevel& lv = c->lev[level];
+  cudaMemsetAsync(out, 0, (size_t)lv.n * lv.n * sizeof(double), s);
+  k_operator_export<<<(unsigned)lv.me, 64, 0, s>>>(lv, out);
+}
+
+}  // namespace msmg
