@@ -188,6 +188,8 @@ def msmg_setup(grid: msmg_grid, kappa: torch.Tensor, opts: msmg_options, workspa
         if ctx.value:
             load_library().msmg_destroy(ctx)
         _check(st)
+    if st == -6 and not ctx.value:
+        _check(st)
     return ctx.value, st
 
 

@@ -306,6 +306,13 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   MSMG_CUDA_TRY(cudaMemsetAsync(c->dtmp, 0, 16 * sizeof(double), s));
   MSMG_CUDA_TRY(cudaMemsetAsync(c->red.counter, 0, 4 * sizeof(unsigned), s));
   launch_faces(c, kappa, kappa_components, kappa_dtype, s);
+  {
+    // stop before any eigensolve when the permeability is not positive and finite
+    int h0 = 0;
+    MSMG_CUDA_TRY(cudaMemcpyAsync(&h0, c->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h0) return MSMG_ERR_BAD_KAPPA;
+  }
   launch_pivots(c, s);
   cudaEvent_t e_eig0, e_eig1;
   cudaEventCreate(&e_eig0);
@@ -383,7 +390,7 @@ size_t msmg_dot_scratch_bytes(int64_t n) {
 }
 
 int msmg_dot(const double* a, const double* b, int64_t n, void* scratch, double* result_host, msmg_stream stream) {
-  if (!a || !b || !scratch || !result_host || n < 0) return MSMG_ERR_INVALID_ARG;
+  if ((n > 0 && (!a || !b)) || !scratch || !result_host || n < 0) return MSMG_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(scratch) % 16) return MSMG_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* base = static_cast<char*>(scratch);

@@ -94,13 +94,15 @@ __device__ void jacobi_eig(double* A, double* V, int n, double* cs, int* pr, dou
   }
 }
 
-// order[k] = index of the k-th smallest diagonal entry of A (stable).
+// order[k] = index of the k-th smallest diagonal entry of A (stable).  NaN
+// entries sort as +infinity, so the ranks always form a permutation of 0..n-1.
+__device__ __forceinline__ double sort_key(double v) { return isnan(v) ? INFINITY : v; }
 __device__ void sort_diag(const double* A, int n, int* order) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double di = A[i * n + i];
+    const double di = sort_key(A[i * n + i]);
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double dj = A[j * n + j];
+      const double dj = sort_key(A[j * n + j]);
       rank += (dj < di) || (dj == di && j < i);
     }
     order[rank] = i;
