@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the spectral multigrid PCG solve on one GB300 per rank.
+
+Metric: solve DOF/s to rtol 1e-8 (mixed vs FP64 form) and the V-cycle's HBM
+fraction of peak.  A step is one complete PCG solve (to ||b - A x|| <=
+1e-8 ||b||) of the default workload: a 128^3 high-contrast inclusion field
+(background 1, 200 random spheres and 20 full-length 2x2 channels at 1e6),
+8^3 elements, 4 levels, 6 eigenvectors per local problem.  Set-up is done
+once before timing and reported separately.  Inputs are synthetic and
+seeded; they are resident in HBM when the timed region starts, and L2 is
+flushed (256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank solves its own replica of the workload (the
+problem does not shard across the one-GPU machines of this pool): weak scaling,
+no data-path collective; value = DOF solved by all ranks / max time.
+``--impl reference`` times the FP64 CPU oracle (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve DOF/s to rtol 1e-8 (mixed vs FP64 form); V-cycle HBM % of peak"
+WORKLOAD = ("128^3 unit-cube inclusion field: background 1, 200 spheres (radius 1.5h-6h) and 20 axis-aligned "
+            "2x2-cell channels at 1e6 (seed 1); corner source/sink; 8^3 elements, 4 levels (ratio 2), "
+            "6 eigenvectors per local problem; PCG rtol 1e-8")
+N_GRID = 128
+BLOCK = (8, 8, 8)
+N_LEVELS = 4
+N_EIG = [6, 6, 6]
+RATIO = [(2, 2, 2), (2, 2, 2)]
+RTOL = 1e-8
+
+
+def field():
+    import fields
+    return fields.inclusions(N_GRID, seed=1, n_spheres=200, n_channels=20, k_hi=1e6)
+
+
+def rhs(shape):
+    import fields
+    return fields.rhs_corners(shape)
+
+
+# Algorithmic bytes per fine cell and launch of each fine-level kernel of one PCG
+# iteration (halos excluded), by form; L = eigenvectors per element.
+#   pre:      x, r read+write, p, q read (FP64); r copy and u written (V); T (3), 1/d read (V)
+#   restrict: r copy, u, T (3) read (V); basis (L values)
+#   prolong:  u read+write (V); basis (L values)
+#   post:     r copy, u, T (3), 1/d read (V); r read (FP64); q read (FP64, flexible beta only); z write (V)
+#   pmatvec:  z read (V); p_old read, p_new write, q write, T (3) read (FP64)
+def kernel_bytes(form: str, L: int) -> dict:
+    v = 4 if form == "mixed" else 8
+    b = 4 if form == "mixed" else 8
+    flex = 8 if form == "mixed" else 0
+    return {"pre": 48 + 2 * v + 4 * v, "restrict": 2 * v + 3 * v + L * b, "prolong": 2 * v + L * b,
+            "post": 5 * v + 8 + flex + v, "pmatvec": v + 24 + 24}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """Per-launch DRAM bytes of ``kernel`` from the committed ncu summary, if it
+    was captured on the current source of the kernel file."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = os.path.join(ROOT, "paper_2403_19342_gb300", "csrc", rec["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        ent = rec["kernels"].get(kernel)
+        if ent and rec.get("source_sha") == sha:
+            return ent["dram_bytes_per_launch_full_size"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ reference arm / CPU baseline
+CROP = 64
+
+
+def oracle_sample(steps: int = 1):
+    """The FP64 oracle as it stands on a bounded sample of the workload: the
+    64^3 corner crop of the same field, same hierarchy parameters, same RHS
+    pattern; setup excluded from the metric."""
+    import oracle
+    kappa = field()[:CROP, :CROP, :CROP].copy()
+    f = rhs(kappa.shape).ravel()
+    opts = oracle.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, nu=[1] * (N_LEVELS - 1))
+    t0 = time.perf_counter()
+    H = oracle.setup(kappa, (1.0 / N_GRID,) * 3, opts)
+    t1 = time.perf_counter()
+    times, its = [], []
+    for _ in range(steps):
+        s0 = time.perf_counter()
+        res = oracle.solve(H, f, rtol=RTOL)
+        times.append(time.perf_counter() - s0)
+        its.append(res.iterations)
+    n = kappa.size
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": n / float(np.mean(times)), "unit": "DOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{CROP}^3 corner crop of the same field and hierarchy, full PCG solve to rtol 1e-8 "
+                      f"({its[0]} iterations); oracle setup {t1 - t0:.1f} s excluded like the GPU setup",
+            "setup_s": t1 - t0, "solve_s": float(np.mean(times)), "iterations": its[0]}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    steps = max(1, min(args.steps, 3))
+    rec = oracle_sample(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rec["value"], "unit": "DOF/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": rec["solve_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": rec["sample"]},
+            "cpu_baseline": {k: rec[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": rec["value"], "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, world, rank, local):
+    import torch
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    _build.build()
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kappa_np = field()
+    shape = kappa_np.shape
+    n = int(np.prod(shape))
+    kappa = torch.tensor(kappa_np, device=dev)
+    f_np = rhs(shape)
+    f_dev = torch.tensor(f_np, device=dev)
+    x_dev = torch.zeros_like(f_dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    forms = {}
+    kernel_times = {}
+    sampler = ClockSampler(local)
+    launches = 0
+    for form, prec in (("fp64", pkg.FP64), ("mixed", pkg.MIXED)):
+        opts = pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec, eig_tol=1e-8)
+        S = pkg.Solver(kappa, opts)
+        info0 = S.info
+        for _ in range(args.warmup):
+            pkg.msmg_solve(S.ctx, f_dev, x_dev, RTOL, 1000, 0)
+        torch.cuda.synchronize()
+        barrier(world)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if form == "mixed":
+            sampler.start()
+        torch.cuda.synchronize()
+        infos = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            st, info = pkg.msmg_solve(S.ctx, f_dev, x_dev, RTOL, 1000, 0)
+            ev[k][1].record(stream)
+            infos.append(info[0])
+        torch.cuda.synchronize()
+        barrier(world)
+        if form == "mixed":
+            clocks = sampler.stop()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        ms_step = max_over_ranks(world, float(np.mean(ms)))
+        inf = infos[-1]
+        if form == "mixed":
+            launches = int(sum(i["kernel_launches"] for i in infos))
+        forms[form] = {"value": world * n / (ms_step * 1e-3), "unit": "DOF/s", "ms_per_step": ms_step,
+                       "iterations": inf["iterations"], "true_rel_residual": inf["true_rel_residual"],
+                       "converged": bool(inf["converged"]), "setup_ms": info0["setup_ms"],
+                       "eig_ms": info0["eig_ms"], "eig_residual_max": info0["eig_residual_max"],
+                       "eig_iterations_max": info0["eig_iterations_max"]}
+        kernel_times[form] = S.time_kernels(reps=10)
+        if form == "mixed":
+            # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+            f_host = torch.tensor(f_np).pin_memory()
+            x_host = torch.zeros_like(f_host).pin_memory()
+            pkg.msmg_solve(S.ctx, f_host, x_host, RTOL, 1000, pkg.FLAG_HOST_IO)
+            torch.cuda.synchronize()
+            e2e_ms = []
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pkg.msmg_solve(S.ctx, f_host, x_host, RTOL, 1000, pkg.FLAG_HOST_IO)
+                b.record(stream)
+                torch.cuda.synchronize()
+                e2e_ms.append(a.elapsed_time(b))
+            e2e_step = max_over_ranks(world, float(np.mean(e2e_ms)))
+            e2e = {"value": world * n / (e2e_step * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_step}
+        S.close()
+        del S
+    # roofline of the dominant fine-level kernel of the mixed V-cycle
+    peak, peak_kind = load_peaks()
+    L = N_EIG[0]
+    kb = kernel_bytes("mixed", L)
+    kt = kernel_times["mixed"]
+    fine = {k: kt[k] for k in ("pre", "restrict", "prolong", "post", "pmatvec")}
+    dom = max(fine, key=fine.get)
+    achieved = kb[dom] * n / (kt[dom] * 1e-3) / 1e9
+    traffic = traffic_record(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": kb[dom] * n, "avg_launch_ms": kt[dom]}
+    vc_keys = ("pre", "restrict", "prolong", "post")
+    vc_bytes = sum(kb[k] for k in vc_keys) * n
+    vc_frac = vc_bytes / (kt["vcycle"] * 1e-3) / 1e9 / peak
+    vc64 = sum(kernel_bytes("fp64", L)[k] for k in vc_keys) * n / (kernel_times["fp64"]["vcycle"] * 1e-3) / 1e9 / peak
+    line = {"metric": METRIC, "value": forms["mixed"]["value"], "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms["mixed"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed before each step (256 MiB write); working set > L2",
+                       "form": "mixed: FP32 fine V-cycle and bases, FP64 coarse levels and outer PCG",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "forms": forms,
+            "vcycle_hbm_frac": {"mixed": vc_frac, "fp64": vc64, "peak_gbs": peak},
+            "kernel_ms": kernel_times,
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rec = oracle_sample(1)
+        line["cpu_baseline"] = {k: rec[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile(args):
+    """Short run for ncu: set-up of the default workload, then one solve capped at
+    ``--max-iter`` PCG iterations in the chosen form."""
+    import torch
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    _build.build()
+    kappa = torch.tensor(field(), device="cuda")
+    f = torch.tensor(rhs(kappa.shape), device="cuda")
+    x = torch.zeros_like(f)
+    prec = pkg.MIXED if args.form == "mixed" else pkg.FP64
+    S = pkg.Solver(kappa, pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec,
+                                      eig_tol=1e-8))
+    st, info = pkg.msmg_solve(S.ctx, f, x, RTOL, args.max_iter, 0)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.form, "iterations": info[0]["iterations"],
+                      "kernel_launches": info[0]["kernel_launches"]}))
+    S.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="short run for ncu (no timing output)")
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--max-iter", type=int, default=4)
+    args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
+    world, rank, local = dist_setup() if args.impl == "gpu" else (int(os.environ.get("WORLD_SIZE", "1")),
+                                                                   int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    rc = run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -58,7 +58,7 @@ typedef struct msmg_ctx msmg_ctx;                /* opaque, owned by the library
 
 /* precision modes */
 #define MSMG_FP64   0   /* every step in FP64                                           */
-#define MSMG_MIXED  1   /* FP32 fine-level V-cycle (BF16 bases), FP64 coarse levels,    */
+#define MSMG_MIXED  1   /* FP32 fine-level V-cycle and bases, FP64 coarse levels,       */
                         /* coarsest solve, eigenbasis orthonormalisation and outer PCG  */
 
 /* kappa element types */
@@ -107,6 +107,7 @@ typedef struct {
     double true_rel_residual;          /* recomputed from x at exit                      */
     double rhs_mean;                   /* mean removed from the right-hand side          */
     double solve_ms;                   /* device time of the solve                       */
+    int64_t kernel_launches;           /* library kernels launched by the solve          */
 } msmg_solve_info;
 
 /*
@@ -205,6 +206,18 @@ int msmg_export_faces(msmg_ctx* ctx, double* T, msmg_stream stream);
 int msmg_get_setup_info(msmg_ctx* ctx, msmg_setup_info* info);
 void msmg_destroy(msmg_ctx* ctx);
 const char* msmg_status_string(int status);
+
+/*
+ * Average device time (ms) per launch of the fine-level kernels of one PCG iteration,
+ * measured with CUDA events around each launch on the given stream over reps repetitions on
+ * the context's own buffers (fixed synthetic data).  ms_out[0 .. n_out) receives:
+ *   [0] PCG update of x and r fused with the pre-smoothing   [1] residual + restriction
+ *   [2] prolongation   [3] residual + post-smoothing (with the r.z reduction)
+ *   [4] all coarse levels (levels >= 2)   [5] search-direction update fused with q = A p
+ *   [6] [0]..[3] and [4] together (one preconditioner application)
+ * Used for roofline figures; no effect on results.
+ */
+int msmg_time_kernels(msmg_ctx* ctx, int reps, double* ms_out, int n_out, msmg_stream stream);
 
 /* Measured plain-ALU FMA throughput of this GPU (TFLOP/s), for roofline denominators of
  * ALU-bound kernels: a short in-register FMA loop timed with CUDA events. */

@@ -58,7 +58,8 @@ class msmg_setup_info(C.Structure):
 
 class msmg_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
-                ("true_rel_residual", C.c_double), ("rhs_mean", C.c_double), ("solve_ms", C.c_double)]
+                ("true_rel_residual", C.c_double), ("rhs_mean", C.c_double), ("solve_ms", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_destroy": (None, [P]),
         "msmg_status_string": (C.c_char_p, [I]),
         "msmg_probe_alu_peaks": (I, [C.POINTER(D), C.POINTER(D), P]),
+        "msmg_time_kernels": (I, [P, I, C.POINTER(D), I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -104,7 +106,7 @@ def exported_symbols():
     return ["msmg_workspace_size", "msmg_setup", "msmg_solve", "msmg_apply_A", "msmg_apply_precond",
             "msmg_dot_scratch_bytes", "msmg_dot", "msmg_export_basis", "msmg_import_bases",
             "msmg_export_operator", "msmg_export_faces", "msmg_get_setup_info", "msmg_destroy",
-            "msmg_status_string", "msmg_probe_alu_peaks"]
+            "msmg_status_string", "msmg_probe_alu_peaks", "msmg_time_kernels"]
 
 
 def _check(status: int) -> int:
@@ -202,7 +204,8 @@ def msmg_solve(ctx: int, rhs: torch.Tensor, x: torch.Tensor, rtol: float, max_it
                                    n_rhs, rtol, max_iter, flags, _stream(stream), infos)
     _check(st)
     return st, [dict(iterations=i.iterations, converged=bool(i.converged), rel_residual=i.rel_residual,
-                     true_rel_residual=i.true_rel_residual, rhs_mean=i.rhs_mean, solve_ms=i.solve_ms)
+                     true_rel_residual=i.true_rel_residual, rhs_mean=i.rhs_mean, solve_ms=i.solve_ms,
+                     kernel_launches=i.kernel_launches)
                 for i in infos]
 
 
@@ -256,6 +259,12 @@ def msmg_get_setup_info(ctx: int) -> dict:
 
 def msmg_destroy(ctx: int) -> None:
     load_library().msmg_destroy(ctx)
+
+
+def msmg_time_kernels(ctx: int, reps: int = 20, stream=None) -> list:
+    out = (C.c_double * 7)()
+    _check(load_library().msmg_time_kernels(ctx, reps, out, 7, _stream(stream)))
+    return list(out)
 
 
 def msmg_probe_alu_peaks(stream=None) -> tuple[float, float]:
@@ -348,6 +357,11 @@ class Solver:
         out = torch.empty((n, n), dtype=torch.float64, device="cuda")
         msmg_export_operator(self.ctx, level, out, self.stream)
         return out
+
+    def time_kernels(self, reps: int = 20) -> dict:
+        v = msmg_time_kernels(self.ctx, reps, self.stream)
+        keys = ["pre", "restrict", "prolong", "post", "coarse_levels", "pmatvec", "vcycle"]
+        return dict(zip(keys, v))
 
     def export_faces(self) -> torch.Tensor:
         out = torch.empty((3,) + self.shape, dtype=torch.float64, device="cuda")

@@ -16,6 +16,9 @@ void launch_mixed_copies(msmg_ctx* c, cudaStream_t s);
 void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s);
 int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s);
 int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
+int time_kernels(msmg_ctx* c, int reps, double* acc, cudaStream_t s);
+void apply_vcycle_fp64_out(msmg_ctx* c, cudaStream_t s);
+void prepare_fine_kernels(msmg_ctx* c);
 
 struct LevelShape {
   int g[kMaxLevels + 1][3];    // element grid of E_l, l = 1 .. nL-1
@@ -57,8 +60,9 @@ int validate(const msmg_grid* g, const msmg_options* o) {
   for (int l = 1; l <= nL - 1; ++l)
     if (sh.m[l] < 2) return MSMG_ERR_SINGLE_BLOCK;
   const int nb = o->block[0] * o->block[1] * o->block[2];
-  if (nb > 1024) return MSMG_ERR_UNSUPPORTED;
+  if (nb > 512) return MSMG_ERR_UNSUPPORTED;
   if (o->n_eig[0] < 1 || o->n_eig[0] > nb) return MSMG_ERR_INVALID_ARG;
+  if (nb > 96 && o->n_eig[0] >= 16) return MSMG_ERR_UNSUPPORTED;   // subspace solver block limit
   for (int l = 2; l <= nL - 1; ++l) {
     const int nch = o->ratio[l - 2][0] * o->ratio[l - 2][1] * o->ratio[l - 2][2];
     const int nP = nch * o->n_eig[l - 2];
@@ -113,8 +117,9 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   // common
   c->flags = ar.take<int>(16);
   c->dtmp = ar.take<double>(16 + nc * nc + 3 * nc + 64);
-  const int epc = f.nb >= 256 ? 1 : 256 / f.nb;
-  int64_t maxgrid = (f.m + epc - 1) / epc;
+  // every reducing kernel launches at most one CTA per element, or 1216 CTAs for
+  // the grid-stride vector kernels
+  int64_t maxgrid = f.m;
   if (maxgrid < 152 * 8) maxgrid = 152 * 8;
   c->red.partials = ar.take<double>((size_t)maxgrid * kRedWidth);
   c->red.counter = ar.take<unsigned>(4);
@@ -129,7 +134,7 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   if (mixed) {
     f.T32 = ar.take<float>(3 * n);
     f.invd32 = ar.take<float>(n);
-    f.Phi16 = ar.take<__nv_bfloat16>(f.m * f.L * f.nb);
+    f.Phi32 = ar.take<float>(f.m * f.L * f.nb);
   }
   for (int l = 2; l <= nL; ++l) {
     CoarseLevel& lv = c->lev[l];
@@ -158,6 +163,8 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   B.p1 = ar.take<double>(n);
   B.q = ar.take<double>(n);
   B.vu[1] = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
+  B.rv = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
+  B.zv = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
   for (int l = 2; l <= nL; ++l) {
     B.vf[l] = ar.take<double>(c->lev[l].n);
     B.vu[l] = ar.take<double>(c->lev[l].n);
@@ -219,6 +226,7 @@ static int check_flags(msmg_ctx* c, cudaStream_t s) {
   if (h[0]) return MSMG_ERR_BAD_KAPPA;
   if (h[1] || d[1] != 0.0) return MSMG_ERR_NOT_FACTORIZABLE;
   c->info.eig_residual_max = d[0];
+  c->info.eig_iterations_max = h[3];
   if (h[2]) return MSMG_ERR_EIG_NOT_CONVERGED;
   return 0;
 }
@@ -234,6 +242,7 @@ static int build_from_bases(msmg_ctx* c, bool given, cudaStream_t s) {
   int st = launch_coarsest(c, s);
   if (st) return st;
   launch_mixed_copies(c, s);
+  prepare_fine_kernels(c);
   return 0;
 }
 
@@ -378,7 +387,7 @@ int msmg_apply_precond(msmg_ctx* c, const double* r, double* z, msmg_stream stre
   if (!c || !r || !z) return MSMG_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   launch_nat_to_blk(c, r, c->sb.r, s);
-  vcycle(c, c->sb.r, c->sb.z, nullptr, s);
+  apply_vcycle_fp64_out(c, s);
   launch_blk_to_nat(c, c->sb.z, z, s);
   MSMG_CUDA_TRY(cudaGetLastError());
   return 0;
@@ -430,6 +439,7 @@ int msmg_import_bases(msmg_ctx* c, const double* const* bases, msmg_stream strea
   int st = launch_coarsest(c, s);
   if (st) return st;
   launch_mixed_copies(c, s);
+  prepare_fine_kernels(c);
   return check_flags(c, s);
 }
 
@@ -455,9 +465,20 @@ int msmg_get_setup_info(msmg_ctx* c, msmg_setup_info* info) {
 
 void msmg_destroy(msmg_ctx* c) {
   if (!c) return;
+  if (c->graph_state == 1) cudaGraphExecDestroy(c->iter_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaEventDestroy(c->ev0);
   cudaEventDestroy(c->ev1);
   delete c;
+}
+
+int msmg_time_kernels(msmg_ctx* c, int reps, double* ms_out, int n_out, msmg_stream stream) {
+  if (!c || !ms_out || reps < 1 || n_out < 1) return MSMG_ERR_INVALID_ARG;
+  double acc[7];
+  int st = time_kernels(c, reps, acc, reinterpret_cast<cudaStream_t>(stream));
+  if (st) return st;
+  for (int i = 0; i < n_out && i < 7; ++i) ms_out[i] = acc[i];
+  return 0;
 }
 
 const char* msmg_status_string(int s) {

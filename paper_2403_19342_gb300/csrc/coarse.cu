@@ -151,14 +151,4 @@ const double* coarse_cycle(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t s) {
   return w;
 }
 
-void fine_down(msmg_ctx* c, const double* f, double* rc, PcgScalars* sc, cudaStream_t s);
-void fine_up(msmg_ctx* c, const double* f, const double* ec, double* z, const double* qv, PcgScalars* sc,
-             cudaStream_t s);
-
-void vcycle_impl(msmg_ctx* c, const double* f, double* z, const double* qv, PcgScalars* sc, cudaStream_t s) {
-  fine_down(c, f, (double*)c->sb.vf[2], sc, s);
-  const double* e = coarse_cycle(c, 2, sc, s);
-  fine_up(c, f, e, z, qv, sc, s);
-}
-
 }  // namespace msmg

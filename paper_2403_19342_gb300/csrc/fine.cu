@@ -110,38 +110,6 @@ __device__ __forceinline__ V apply_A_cell(const V* ut, const V* t0, const V* t1,
   return acc;
 }
 
-// In-place IC(0) solve on one element: y <- M^{-1} y with
-// M = (D~ + L) D~^{-1} (D~ + L^T), L the strictly lower part of the element's
-// diagonal block (off-diagonal entries -T).  Wavefronts lx + ly + lz = const.
-template <typename V>
-__device__ void ic0_solve(V* y, const V* t0, const V* t1, const V* t2, V invd, const Slot& s, const Geo& g) {
-  const int smax = g.bx + g.by + g.bz - 3;
-  const int sc = s.lx + s.ly + s.lz;
-  const int c = pad(g, s.lx, s.ly, s.lz);
-  const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
-  const int p = s.p;
-  for (int w = 0; w <= smax; ++w) {
-    if (s.valid && sc == w) {
-      V acc = y[p];
-      if (s.lx > 0) acc += t0[c - 1] * y[p - 1];
-      if (s.ly > 0) acc += t1[c - sy] * y[p - g.bx];
-      if (s.lz > 0) acc += t2[c - sz] * y[p - g.bx * g.by];
-      y[p] = acc * invd;
-    }
-    __syncthreads();
-  }
-  for (int w = smax; w >= 0; --w) {
-    if (s.valid && sc == w) {
-      V acc = (V)0;
-      if (s.lx < g.bx - 1) acc += t0[c] * y[p + 1];
-      if (s.ly < g.by - 1) acc += t1[c] * y[p + g.bx];
-      if (s.lz < g.bz - 1) acc += t2[c] * y[p + g.bx * g.by];
-      y[p] = y[p] + invd * acc;
-    }
-    __syncthreads();
-  }
-}
-
 // ============================================================== set-up kernels
 
 // K1: face coefficients (harmonic average of kappa^d / h_d^2, Fig. (kappa edge))
@@ -275,84 +243,6 @@ __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, c
 
 // ============================================================== V-cycle, fine level
 
-// Pre-smoothing from zero: u = M^{-1} f.
-template <typename V>
-__global__ void k_smooth_first(const double* __restrict__ f, V* __restrict__ u, const V* __restrict__ T,
-                               const V* __restrict__ invd, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
-                               const PcgScalars* sc) {
-  if (sc && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* smem = reinterpret_cast<V*>(smem_raw);
-  const Slot s = make_slot(g, m);
-  V* t0 = smem + (size_t)s.eloc * (3 * g.P + g.nb);
-  V* t1 = t0 + g.P;
-  V* t2 = t1 + g.P;
-  V* y = t2 + g.P;
-  if (s.eloc < g.epc) load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
-  V dinv = (V)0;
-  if (s.valid) {
-    y[s.p] = (V)f[s.e * g.nb + s.p];
-    dinv = invd[s.e * g.nb + s.p];
-  }
-  __syncthreads();
-  ic0_solve(y, t0, t1, t2, dinv, s, g);
-  if (s.valid) u[s.e * g.nb + s.p] = y[s.p];
-}
-
-// Residual and restriction: rc[e][k] = sum_c Phi[e][k][c] (f - A u)_c  (Algorithm 1,
-// "Restriction"; R_1 rows are the local eigenvectors).
-template <typename V, typename BT>
-__global__ void k_resid_restrict(const double* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T,
-                                 const BT* __restrict__ Phi, int L, double* __restrict__ rc, int64_t n, Geo g,
-                                 int64_t m, const int* __restrict__ nbr, const PcgScalars* sc) {
-  if (sc && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* smem = reinterpret_cast<V*>(smem_raw);
-  const Slot s = make_slot(g, m);
-  V* ut = smem + (size_t)s.eloc * 4 * g.P;
-  V* t0 = ut + g.P;
-  V* t1 = t0 + g.P;
-  V* t2 = t1 + g.P;
-  double* red = reinterpret_cast<double*>(smem + (size_t)g.epc * 4 * g.P);   // [epc][L][nwarp_e] or [epc][nb]
-  if (s.eloc < g.epc) {
-    load_tile(ut, u, s, g, nbr, 0x3f);
-    load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
-  }
-  __syncthreads();
-  double w = 0.0;
-  if (s.valid) w = f[s.e * g.nb + s.p] - (double)apply_A_cell(ut, t0, t1, t2, g, s.lx, s.ly, s.lz);
-  if ((g.nb & 31) == 0) {
-    const int nwe = g.nb / 32;
-    const int lane = threadIdx.x & 31, wi = s.p / 32;
-    for (int k = 0; k < L; ++k) {
-      double v = 0.0;
-      if (s.valid) v = w * (double)Phi[(s.e * L + k) * g.nb + s.p];
-      v = warp_sum(v);
-      if (lane == 0 && s.eloc < g.epc) red[((size_t)s.eloc * L + k) * nwe + wi] = v;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < g.epc * L; t += blockDim.x) {
-      const int el = t / L, k = t % L;
-      const int64_t e = (int64_t)blockIdx.x * g.epc + el;
-      if (e >= m) continue;
-      double acc = 0.0;
-      for (int j = 0; j < nwe; ++j) acc += red[((size_t)el * L + k) * nwe + j];
-      rc[e * L + k] = acc;
-    }
-  } else {
-    for (int k = 0; k < L; ++k) {
-      if (s.eloc < g.epc) red[(size_t)s.eloc * g.nb + s.p] = s.valid ? w * (double)Phi[(s.e * L + k) * g.nb + s.p] : 0.0;
-      __syncthreads();
-      if (s.valid && s.p == 0) {
-        double acc = 0.0;
-        for (int j = 0; j < g.nb; ++j) acc += red[(size_t)s.eloc * g.nb + j];
-        rc[s.e * L + k] = acc;
-      }
-      __syncthreads();
-    }
-  }
-}
-
 // Prolongation: u_c += sum_k Phi[e][k][c] ec[e][k]  (Algorithm 1, R_c^T e_c).
 template <typename V, typename BT>
 __global__ void k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L, const double* __restrict__ ec,
@@ -362,58 +252,9 @@ __global__ void k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L, 
   if (i >= n) return;
   const int64_t e = i / nb;
   const int p = (int)(i % nb);
-  double acc = 0.0;
-  for (int k = 0; k < L; ++k) acc += (double)Phi[(e * L + k) * nb + p] * ec[e * L + k];
-  u[i] = (V)((double)u[i] + acc);
-}
-
-// Post-smoothing: out = u + M^{-1} (f - A u).  Final = true: out is the FP64
-// preconditioned residual z, and the CTA reduction gives f.z (and z.q for the
-// flexible beta), finalising the PCG beta.
-template <typename V, bool Final>
-__global__ void k_resid_smooth(const double* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T,
-                               const V* __restrict__ invd, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
-                               void* __restrict__ out, const double* __restrict__ qv, RedSlot red, PcgScalars* sc) {
-  if (sc && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* smem = reinterpret_cast<V*>(smem_raw);
-  const Slot s = make_slot(g, m);
-  V* ut = smem + (size_t)s.eloc * (4 * g.P + g.nb);
-  V* t0 = ut + g.P;
-  V* t1 = t0 + g.P;
-  V* t2 = t1 + g.P;
-  V* y = t2 + g.P;
-  if (s.eloc < g.epc) {
-    load_tile(ut, u, s, g, nbr, 0x3f);
-    load_T_tiles(t0, t1, t2, T, n, s, g, nbr);
-  }
-  __syncthreads();
-  V dinv = (V)0;
-  double fc = 0.0;
-  if (s.valid) {
-    fc = f[s.e * g.nb + s.p];
-    y[s.p] = (V)(fc - (double)apply_A_cell(ut, t0, t1, t2, g, s.lx, s.ly, s.lz));
-    dinv = invd[s.e * g.nb + s.p];
-  }
-  __syncthreads();
-  ic0_solve(y, t0, t1, t2, dinv, s, g);
-  double zc = 0.0;
-  if (s.valid) {
-    zc = (double)ut[pad(g, s.lx, s.ly, s.lz)] + (double)y[s.p];
-    if (Final) reinterpret_cast<double*>(out)[s.e * g.nb + s.p] = zc;
-    else reinterpret_cast<V*>(out)[s.e * g.nb + s.p] = (V)zc;
-  }
-  if (Final && sc) {
-    double v[2] = {fc * zc, (s.valid && qv) ? zc * qv[s.e * g.nb + s.p] : 0.0};
-    grid_reduce<2>(v, red, [=] __device__(double* t) {
-      sc->rz_old = sc->rz;
-      sc->rz = t[0];
-      if (sc->iter == 0 && sc->pq == 0.0) sc->beta = 0.0;          // first preconditioned residual
-      else if (sc->flexible) sc->beta = -sc->alpha * t[1] / sc->rz_old;
-      else sc->beta = t[0] / sc->rz_old;
-      if (!isfinite(t[0])) sc->done = 2;
-    });
-  }
+  V acc = (V)0;
+  for (int k = 0; k < L; ++k) acc += (V)Phi[(e * L + k) * nb + p] * (V)ec[e * L + k];
+  u[i] += acc;
 }
 
 // ============================================================== host launchers
@@ -472,55 +313,74 @@ void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s) {
                                                                 c->red, nullptr);
 }
 
-void launch_matvec_pq(msmg_ctx* c, const double* p, double* q, PcgScalars* sc, cudaStream_t s) {
-  const Geo g = fine_geo(c);
-  const size_t sm = (size_t)g.epc * 4 * g.P * sizeof(double);
-  cudaFuncSetAttribute(k_matvec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_matvec<true><<<fine_grid(c, g), fine_threads(g), sm, s>>>(p, q, c->fine.T, c->n, g, c->fine.m, c->fine.nbr,
-                                                               c->red, sc);
-}
-
-// Fine-level pieces of the V-cycle, dispatched on the precision mode.
+// Prolongation on the fine level (Algorithm 1: u += R_1^T e_c).
 template <typename V, typename BT>
-static void fine_down_t(msmg_ctx* c, const double* f, V* u, double* rc, const V* T, const V* invd, const BT* Phi,
-                        PcgScalars* sc, cudaStream_t s) {
-  const Geo g = fine_geo(c);
-  const unsigned grid = fine_grid(c, g), thr = fine_threads(g);
-  const size_t sm1 = (size_t)g.epc * (3 * g.P + g.nb) * sizeof(V);
-  cudaFuncSetAttribute(k_smooth_first<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-  k_smooth_first<V><<<grid, thr, sm1, s>>>(f, u, T, invd, c->n, g, c->fine.m, c->fine.nbr, sc);
-  const int L = c->fine.L;
-  const size_t red = ((g.nb & 31) == 0 ? (size_t)g.epc * L * (g.nb / 32) : (size_t)g.epc * g.nb) * sizeof(double);
-  const size_t sm2 = (size_t)g.epc * 4 * g.P * sizeof(V) + red + 16;
-  cudaFuncSetAttribute(k_resid_restrict<V, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-  k_resid_restrict<V, BT><<<grid, thr, sm2, s>>>(f, u, T, Phi, L, rc, c->n, g, c->fine.m, c->fine.nbr, sc);
+void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const double* ec, PcgScalars* sc, cudaStream_t s) {
+  k_prolong<V, BT><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>((V*)c->sb.vu[1], Phi, c->fine.L, ec, c->n,
+                                                                  c->fine.nb, sc);
+}
+template void launch_prolong_fine<float, float>(msmg_ctx*, const float*, const double*, PcgScalars*, cudaStream_t);
+template void launch_prolong_fine<double, double>(msmg_ctx*, const double*, const double*, PcgScalars*, cudaStream_t);
+
+// ---- kernel timing (roofline figures)
+__global__ void k_fill_pattern(double* __restrict__ v, int64_t n, double phase) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = sin(0.001 * (double)i + phase) + 0.25 * cos(0.0173 * (double)i);
+}
+__global__ void k_reset_scalars(PcgScalars* sc) {
+  sc->done = 0;
+  sc->iter = 1;
+  sc->max_iter = 1 << 30;
+  sc->tol2 = -1.0;
+  sc->pq = 1.0;
+  sc->rz = 1.0;
+  sc->rz_old = 1.0;
+  sc->alpha = 0.0;
+  sc->beta = 0.0;
 }
 
-template <typename V, typename BT>
-static void fine_up_t(msmg_ctx* c, const double* f, V* u, const double* ec, double* z, const V* T, const V* invd,
-                      const BT* Phi, const double* qv, PcgScalars* sc, cudaStream_t s) {
-  const Geo g = fine_geo(c);
-  const unsigned grid = fine_grid(c, g), thr = fine_threads(g);
-  k_prolong<V, BT><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>(u, Phi, c->fine.L, ec, c->n, g.nb, sc);
-  const size_t sm = (size_t)g.epc * (4 * g.P + g.nb) * sizeof(V);
-  cudaFuncSetAttribute(k_resid_smooth<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_resid_smooth<V, true><<<grid, thr, sm, s>>>(f, u, T, invd, c->n, g, c->fine.m, c->fine.nbr, z, qv, c->red, sc);
-}
+void pcg_step_vcycle_timed(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s,
+                           cudaEvent_t* ev);
+void pcg_step_pmatvec(msmg_ctx* c, PcgScalars* sc, cudaStream_t s);
 
-void fine_down(msmg_ctx* c, const double* f, double* rc, PcgScalars* sc, cudaStream_t s) {
-  if (c->opts.precision == MSMG_MIXED)
-    fine_down_t<float, __nv_bfloat16>(c, f, (float*)c->sb.vu[1], rc, c->fine.T32, c->fine.invd32, c->fine.Phi16, sc, s);
-  else
-    fine_down_t<double, double>(c, f, (double*)c->sb.vu[1], rc, c->fine.T, c->fine.invd, c->fine.Phi, sc, s);
-}
-
-void fine_up(msmg_ctx* c, const double* f, const double* ec, double* z, const double* qv, PcgScalars* sc,
-             cudaStream_t s) {
-  if (c->opts.precision == MSMG_MIXED)
-    fine_up_t<float, __nv_bfloat16>(c, f, (float*)c->sb.vu[1], ec, z, c->fine.T32, c->fine.invd32, c->fine.Phi16, qv,
-                                    sc, s);
-  else
-    fine_up_t<double, double>(c, f, (double*)c->sb.vu[1], ec, z, c->fine.T, c->fine.invd, c->fine.Phi, qv, sc, s);
+// Per-kernel device times of one PCG iteration's fine-level work (events on s).
+int time_kernels(msmg_ctx* c, int reps, double* acc, cudaStream_t s) {
+  SolveBuffers& B = c->sb;
+  const int64_t n = c->n;
+  const unsigned g1 = (unsigned)((n + 255) / 256);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.r, n, 0.3);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.p0, n, 1.1);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.q, n, 2.0);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.x, n, 0.7);
+  B.pcur = B.p0;
+  B.pnext = B.p1;
+  cudaEvent_t ev[8];
+  for (int i = 0; i < 8; ++i) cudaEventCreate(&ev[i]);
+  for (int i = 0; i < 7; ++i) acc[i] = 0.0;
+  const bool flexible = c->opts.precision == MSMG_MIXED;
+  for (int r = 0; r < reps; ++r) {
+    k_reset_scalars<<<1, 1, 0, s>>>(B.sc);
+    pcg_step_vcycle_timed(c, 1, flexible ? B.q : nullptr, B.sc, s, ev);   // ev[0..5]
+    k_reset_scalars<<<1, 1, 0, s>>>(B.sc);
+    cudaEventRecord(ev[6], s);
+    pcg_step_pmatvec(c, B.sc, s);
+    cudaEventRecord(ev[7], s);
+    cudaError_t e = cudaEventSynchronize(ev[7]);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
+    float ms;
+    const int seg[5][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {2, 3}};
+    for (int k = 0; k < 5; ++k) {
+      cudaEventElapsedTime(&ms, ev[seg[k][0]], ev[seg[k][1]]);
+      acc[k] += ms;
+    }
+    cudaEventElapsedTime(&ms, ev[6], ev[7]);
+    acc[5] += ms;
+    cudaEventElapsedTime(&ms, ev[0], ev[5]);
+    acc[6] += ms;
+  }
+  for (int i = 0; i < 7; ++i) acc[i] /= reps;
+  for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+  return 0;
 }
 
 // ---- mixed-precision copies
@@ -528,18 +388,13 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
-__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = __float2bfloat16_rn((float)a[i]);
-}
-
 void launch_mixed_copies(msmg_ctx* c, cudaStream_t s) {
   if (c->opts.precision != MSMG_MIXED) return;
   const int64_t n = c->n;
   k_to_f32<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->fine.T, c->fine.T32, 3 * n);
   k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->fine.invd, c->fine.invd32, n);
   const int64_t np = c->fine.m * c->fine.L * c->fine.nb;
-  k_to_bf16<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(c->fine.Phi, c->fine.Phi16, np);
+  k_to_f32<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(c->fine.Phi, c->fine.Phi32, np);
 }
 
 }  // namespace msmg

@@ -69,10 +69,9 @@ struct PcgScalars {
 // A deterministic grid reduction slot: per-CTA partials, a ticket counter and
 // a result.  The last CTA to finish sums the partials in index order.
 struct RedSlot {
-  double* partials;     // [kMaxRedBlocks * kRedWidth]
+  double* partials;     // [max CTAs of a reducing launch][kRedWidth]
   unsigned* counter;    // zero between uses
 };
-constexpr int kMaxRedBlocks = 4096;
 constexpr int kRedWidth = 4;   // up to 4 simultaneous sums per reduction
 
 // ---------------------------------------------------------------- levels
@@ -92,7 +91,7 @@ struct FineLevel {
   double* lam;                  // [m][L]
   float* T32;                   // mixed-precision copies (nullptr in FP64 mode)
   float* invd32;
-  __nv_bfloat16* Phi16;
+  float* Phi32;
 };
 
 struct CoarseLevel {            // level l >= 2 (W_l)
@@ -123,6 +122,9 @@ struct CoarseLevel {            // level l >= 2 (W_l)
 struct SolveBuffers {
   // fine level, FP64, block-major
   double *b, *x, *r, *z, *p0, *p1, *q;
+  double *pcur, *pnext;         // ping-pong search directions of the current iteration
+  void* rv;                     // residual in V-cycle precision
+  void* zv;                     // preconditioned residual in V-cycle precision
   // V-cycle work on every level: f (right side), u (iterate), w (scratch)
   void* vf[kMaxLevels];
   void* vu[kMaxLevels];
@@ -150,6 +152,9 @@ struct msmg_ctx {
   cudaEvent_t ev0, ev1;
   int device;
   int max_rhs;
+  cudaStream_t cap_stream;                      // private stream for graph capture
+  cudaGraphExec_t iter_graph;                   // two captured PCG iterations
+  int graph_state;                              // 0 not built, 1 ready, -1 capture failed
 };
 
 namespace msmg {
@@ -175,14 +180,17 @@ void launch_basis_export(msmg_ctx* c, int level, double* basis, double* lam, boo
 void launch_operator_export(msmg_ctx* c, int level, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- solve
-// V-cycle on level 1: u = P^{-1} f, block-major FP64 in/out.  If rz != nullptr,
-// the final kernel also accumulates f.u into sc (PCG reduction).
-void vcycle(msmg_ctx* c, const double* f, double* u, PcgScalars* sc, cudaStream_t s);
 int pcg_solve(msmg_ctx* c, const double* rhs_nat, double* x_nat, double rtol, int max_iter, int flags,
               cudaStream_t s, msmg_solve_info* info);
 double dot_host(msmg_ctx* c, const double* a, const double* b, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -11,8 +11,8 @@
 
 namespace msmg {
 
-void launch_matvec_pq(msmg_ctx* c, const double* p, double* q, PcgScalars* sc, cudaStream_t s);
-void vcycle_impl(msmg_ctx* c, const double* f, double* z, const double* qv, PcgScalars* sc, cudaStream_t s);
+void pcg_step_vcycle(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s);
+void pcg_step_pmatvec(msmg_ctx* c, PcgScalars* sc, cudaStream_t s);
 
 static constexpr int kVecThreads = 256;
 static inline unsigned vec_grid(int64_t n) {
@@ -150,13 +150,44 @@ void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double
   k_dot<<<vec_grid(n), kVecThreads, 0, s>>>(a, b, n, red, out);
 }
 
-void vcycle(msmg_ctx* c, const double* f, double* u, PcgScalars* sc, cudaStream_t s) {
-  vcycle_impl(c, f, u, nullptr, sc, s);
+// Capture two consecutive PCG iterations (p0 -> p1 -> p0) into a CUDA graph on a
+// private stream.  Returns 1 when the graph is ready, -1 when capture is not
+// possible (the caller then launches kernel by kernel).
+static int build_iteration_graph(msmg_ctx* c) {
+  if (c->graph_state != 0) return c->graph_state;
+  SolveBuffers& B = c->sb;
+  const bool flexible = c->opts.precision == MSMG_MIXED;
+  c->graph_state = -1;
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return -1;
+  B.pcur = B.p0;
+  B.pnext = B.p1;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1;
+  for (int k = 0; k < 2; ++k) {
+    pcg_step_pmatvec(c, B.sc, c->cap_stream);
+    double* t = B.pcur; B.pcur = B.pnext; B.pnext = t;
+    pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, B.sc, c->cap_stream);
+  }
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  B.pcur = B.p0;
+  B.pnext = B.p1;
+  if (e != cudaSuccess || !g) { cudaGetLastError(); return -1; }
+  e = cudaGraphInstantiate(&c->iter_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { cudaGetLastError(); return -1; }
+  c->graph_state = 1;
+  return 1;
 }
 
 // One PCG solve for a single right-hand side already in block-major order in
 // c->sb.b (FP64); x in c->sb.x (initial guess if use_x0).
-static int pcg_one(msmg_ctx* c, double rtol, int max_iter, bool use_x0, cudaStream_t s, msmg_solve_info* info) {
+//   init:      r0 = b - A x0 (mean removed), z0 = P^{-1} r0, beta = 0
+//   iteration: p = z + beta p; q = A p; alpha = r.z / p.q        (k_pmatvec)
+//              x += alpha p; r -= alpha q; stop on ||r|| <= rtol ||b||   (k_pre)
+//              z = P^{-1} r; beta = r.z / r_old.z_old, or the flexible
+//              (Polak-Ribiere) beta in the mixed form                (V-cycle)
+static int pcg_one(msmg_ctx* c, double rtol, int max_iter, bool use_x0, int flags, cudaStream_t s,
+                   msmg_solve_info* info) {
   SolveBuffers& B = c->sb;
   PcgScalars* sc = B.sc;
   const int64_t n = c->n;
@@ -170,23 +201,37 @@ static int pcg_one(msmg_ctx* c, double rtol, int max_iter, bool use_x0, cudaStre
   } else {
     k_init_zero<<<vg, kVecThreads, 0, s>>>(B.b, B.r, B.x, n, c->red, sc, rtol * rtol);
   }
-  // z0 = P^{-1} r0; p0 = z0
-  vcycle_impl(c, B.r, B.z, nullptr, sc, s);
-  k_copy<<<vg, kVecThreads, 0, s>>>(B.z, B.p0, n, sc);
-  double* p = B.p0;
-  double* pn = B.p1;
+  MSMG_CUDA_TRY(cudaMemsetAsync(B.p0, 0, n * sizeof(double), s));
+  B.pcur = B.p0;
+  B.pnext = B.p1;
+  pcg_step_vcycle(c, 0, nullptr, sc, s);
   PcgScalars hsc;
-  int it = 0;
-  for (; it < max_iter; ++it) {
-    launch_matvec_pq(c, p, B.q, sc, s);
-    k_update<<<vg, kVecThreads, 0, s>>>(B.x, B.r, p, B.q, n, c->red, sc);
-    vcycle_impl(c, B.r, B.z, flexible ? B.q : nullptr, sc, s);
-    k_pupdate<<<vg, kVecThreads, 0, s>>>(B.z, p, pn, n, sc);
-    double* t = p; p = pn; pn = t;
-    if ((it & 3) == 3 || it + 1 == max_iter) {
-      MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-      MSMG_CUDA_TRY(cudaStreamSynchronize(s));
-      if (hsc.done) break;
+  const int64_t vc_launches = 4 + 4 * (int64_t)(c->nL - 2) + 1;
+  int64_t launches = 3 + (use_x0 ? 2 : 1) + vc_launches;
+  const bool graph = !(flags & MSMG_FLAG_NO_GRAPH) && build_iteration_graph(c) == 1;
+  if (graph) {
+    // two iterations per graph launch (the p buffers alternate); kernels are
+    // no-ops once the device flag is set, so the count stays exact
+    for (int it = 0; it < max_iter; it += 2) {
+      launches += 2 * (1 + vc_launches);
+      MSMG_CUDA_TRY(cudaGraphLaunch(c->iter_graph, s));
+      if ((it & 7) == 6 || it + 2 >= max_iter) {
+        MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+        MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hsc.done) break;
+      }
+    }
+  } else {
+    for (int it = 0; it < max_iter; ++it) {
+      launches += 1 + vc_launches;
+      pcg_step_pmatvec(c, sc, s);
+      double* t = B.pcur; B.pcur = B.pnext; B.pnext = t;
+      pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, sc, s);
+      if ((it & 3) == 3 || it + 1 == max_iter) {
+        MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+        MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hsc.done) break;
+      }
     }
   }
   MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
@@ -206,6 +251,7 @@ static int pcg_one(msmg_ctx* c, double rtol, int max_iter, bool use_x0, cudaStre
     info->rel_residual = hsc.bb > 0 ? std::sqrt(hsc.rr / hsc.bb) : 0.0;
     info->true_rel_residual = hsc.bb > 0 ? std::sqrt(hres[1] / hsc.bb) : 0.0;
     info->rhs_mean = hsc.mean;
+    info->kernel_launches = launches + 4;
   }
   if (hsc.done == 2) return MSMG_ERR_BREAKDOWN;
   if (hsc.done != 1) return MSMG_NOT_CONVERGED;
@@ -230,7 +276,8 @@ int pcg_solve(msmg_ctx* c, const double* rhs, double* x, double rtol, int max_it
     launch_nat_to_blk(c, rhs, B.b, s);
     if (x0) launch_nat_to_blk(c, x, B.x, s);
   }
-  int st = pcg_one(c, rtol, max_iter, x0, s, info);
+  int st = pcg_one(c, rtol, max_iter, x0, flags, s, info);
+  if (info) info->kernel_launches += (x0 ? 2 : 1) + 1;   // permutations in and out
   if (host) {
     launch_blk_to_nat(c, B.x, B.q, s);
     MSMG_CUDA_TRY(cudaMemcpyAsync(x, B.q, n * sizeof(double), cudaMemcpyDeviceToHost, s));
