@@ -173,6 +173,26 @@ size_t msmg_dot_scratch_bytes(int64_t n);
 int msmg_dot(const double* a, const double* b, int64_t n, void* scratch, double* result_host, msmg_stream stream);
 
 /*
+ * msmg_dot without any device allocation, for callers that cannot allocate device
+ * memory: code that must stay within a fixed device-memory budget after start-up,
+ * host callbacks or plugins that own no allocator, or latency-critical loops where
+ * cudaMalloc's implicit device synchronisation is not acceptable.  The paper has no
+ * counterpart: this is a library convenience around the PCG reduction kernel.
+ *   a, b         device, n doubles each; n <= MSMG_DOT_NOALLOC_MAX_N, larger n returns
+ *                MSMG_ERR_INVALID_ARG (the fixed scratch holds one partial sum per 1024
+ *                elements)
+ *   result_host  host; the call synchronises the stream
+ * Scratch: a fixed array of (MSMG_DOT_NOALLOC_MAX_N / 1024 + 32) doubles (about 128 KiB)
+ * in this library's device memory, which every GPU that loads the library holds until
+ * the process exits.  The first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (concurrent streams or threads)
+ * race and give wrong results.
+ */
+#define MSMG_DOT_NOALLOC_MAX_N 16777216
+int msmg_dot_noalloc(const double* a, const double* b, int64_t n, double* result_host, msmg_stream stream);
+
+/*
  * Level data in the layouts of the paper's matrices (for parity checks).
  * level l = 1 .. n_levels-1.  Elements of E_l are in lexicographic order (x fastest) of
  * the element grid; the dofs of a level-l local problem are its child elements in

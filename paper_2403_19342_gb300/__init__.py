@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_status_string": (C.c_char_p, [I]),
         "msmg_probe_alu_peaks": (I, [C.POINTER(D), C.POINTER(D), P]),
         "msmg_time_kernels": (I, [P, I, C.POINTER(D), I, P]),
+        "msmg_dot_noalloc": (I, [P, P, I64, C.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -106,7 +107,7 @@ def exported_symbols():
     return ["msmg_workspace_size", "msmg_setup", "msmg_solve", "msmg_apply_A", "msmg_apply_precond",
             "msmg_dot_scratch_bytes", "msmg_dot", "msmg_export_basis", "msmg_import_bases",
             "msmg_export_operator", "msmg_export_faces", "msmg_get_setup_info", "msmg_destroy",
-            "msmg_status_string", "msmg_probe_alu_peaks", "msmg_time_kernels"]
+            "msmg_status_string", "msmg_probe_alu_peaks", "msmg_time_kernels", "msmg_dot_noalloc"]
 
 
 def _check(status: int) -> int:
@@ -225,6 +226,18 @@ def msmg_dot(a: torch.Tensor, b: torch.Tensor, scratch: torch.Tensor | None = No
     out = C.c_double(0.0)
     _check(lib.msmg_dot(_ptr(a, torch.float64), _ptr(b, torch.float64), n, _ptr(scratch), C.byref(out),
                         _stream(stream)))
+    return out.value
+
+
+DOT_NOALLOC_MAX_N = 16777216
+
+
+def msmg_dot_noalloc(a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
+    """msmg_dot without a scratch buffer: the library's fixed device array holds the
+    partial sums (for callers that cannot allocate device memory; see include/msmg.h)."""
+    out = C.c_double(0.0)
+    _check(load_library().msmg_dot_noalloc(_ptr(a, torch.float64), _ptr(b, torch.float64), a.numel(),
+                                           C.byref(out), _stream(stream)))
     return out.value
 
 
