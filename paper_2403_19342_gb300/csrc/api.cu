@@ -19,6 +19,7 @@ int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
 int time_kernels(msmg_ctx* c, int reps, double* acc, cudaStream_t s);
 void apply_vcycle_fp64_out(msmg_ctx* c, cudaStream_t s);
 void prepare_fine_kernels(msmg_ctx* c);
+void prepare_coarse_kernels(msmg_ctx* c);
 
 struct LevelShape {
   int g[kMaxLevels + 1][3];    // element grid of E_l, l = 1 .. nL-1
@@ -129,6 +130,7 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   f.T = ar.take<double>(3 * n);
   f.S = ar.take<double>(n);
   f.invd = ar.take<double>(n);
+  f.D = ar.take<double>(n);
   f.Phi = ar.take<double>(f.m * f.L * f.nb);
   f.lam = ar.take<double>(f.m * f.L);
   if (mixed) {
@@ -164,12 +166,12 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   B.q = ar.take<double>(n);
   B.vu[1] = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
   B.rv = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
-  B.zv = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
   for (int l = 2; l <= nL; ++l) {
     B.vf[l] = ar.take<double>(c->lev[l].n);
     B.vu[l] = ar.take<double>(c->lev[l].n);
     B.vw[l] = ar.take<double>(c->lev[l].n);
   }
+  B.ec32 = mixed ? ar.take<float>(c->lev[2].n) : nullptr;
   B.sc = ar.take<PcgScalars>(c->max_rhs);
   B.n_rhs = c->max_rhs;
   return 0;
@@ -243,6 +245,7 @@ static int build_from_bases(msmg_ctx* c, bool given, cudaStream_t s) {
   if (st) return st;
   launch_mixed_copies(c, s);
   prepare_fine_kernels(c);
+  prepare_coarse_kernels(c);
   return 0;
 }
 
@@ -440,6 +443,7 @@ int msmg_import_bases(msmg_ctx* c, const double* const* bases, msmg_stream strea
   if (st) return st;
   launch_mixed_copies(c, s);
   prepare_fine_kernels(c);
+  prepare_coarse_kernels(c);
   return check_flags(c, s);
 }
 

@@ -156,7 +156,7 @@ __global__ void k_faces(const KT* __restrict__ kappa, int comps, int nx, int ny,
 // d_c = a_cc - sum_{j < c, j ~ c in element} T^2 / d_j, a_cc = sum of the six face
 // coefficients.  Writes 1/d.  flags[1] <- 1 on a non-positive pivot.
 __global__ void k_pivots(const double* __restrict__ T, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
-                         double* __restrict__ invd, int* flags) {
+                         double* __restrict__ invd, double* __restrict__ D, int* flags) {
   extern __shared__ double smem[];
   const Slot s = make_slot(g, m);
   double* t0 = smem + (size_t)s.eloc * (3 * g.P + g.nb);
@@ -182,7 +182,10 @@ __global__ void k_pivots(const double* __restrict__ T, int64_t n, Geo g, int64_t
     }
     __syncthreads();
   }
-  if (s.valid) invd[s.e * g.nb + s.p] = 1.0 / d[s.p];
+  if (s.valid) {
+    invd[s.e * g.nb + s.p] = 1.0 / d[s.p];
+    D[s.e * g.nb + s.p] = diag;
+  }
 }
 
 // natural <-> block-major permutations
@@ -244,16 +247,18 @@ __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, c
 // ============================================================== V-cycle, fine level
 
 // Prolongation: u_c += sum_k Phi[e][k][c] ec[e][k]  (Algorithm 1, R_c^T e_c).
-template <typename V, typename BT>
-__global__ void k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L, const double* __restrict__ ec,
-                          int64_t n, int nb, const PcgScalars* sc) {
+// The coarse correction arrives in the V-cycle precision (EC), so the FP64
+// pipe is not touched per cell in the mixed form.
+template <typename V, typename BT, typename EC>
+__global__ void k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L, const EC* __restrict__ ec, int64_t n,
+                          int nb, const PcgScalars* sc) {
   if (sc && sc->done) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e = i / nb;
   const int p = (int)(i % nb);
   V acc = (V)0;
-  for (int k = 0; k < L; ++k) acc += (V)Phi[(e * L + k) * nb + p] * (V)ec[e * L + k];
+  for (int k = 0; k < L; ++k) acc += (V)__ldg(Phi + (e * L + k) * nb + p) * (V)__ldg(ec + e * L + k);
   u[i] += acc;
 }
 
@@ -284,7 +289,7 @@ void launch_pivots(msmg_ctx* c, cudaStream_t s) {
   const size_t sm = (size_t)g.epc * (3 * g.P + g.nb) * sizeof(double);
   cudaFuncSetAttribute(k_pivots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_pivots<<<fine_grid(c, g), fine_threads(g), sm, s>>>(c->fine.T, c->n, g, c->fine.m, c->fine.nbr, c->fine.invd,
-                                                         c->flags);
+                                                         c->fine.D, c->flags);
 }
 
 void launch_nat_to_blk(msmg_ctx* c, const double* in, double* out, cudaStream_t s) {
@@ -313,13 +318,14 @@ void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s) {
                                                                 c->red, nullptr);
 }
 
-// Prolongation on the fine level (Algorithm 1: u += R_1^T e_c).
+// Prolongation on the fine level (Algorithm 1: u += R_1^T e_c); the coarse
+// correction is in the V-cycle precision.
 template <typename V, typename BT>
-void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const double* ec, PcgScalars* sc, cudaStream_t s) {
-  k_prolong<V, BT><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>((V*)c->sb.vu[1], Phi, c->fine.L, ec, c->n,
-                                                                  c->fine.nb, sc);
+void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const V* ec, PcgScalars* sc, cudaStream_t s) {
+  const unsigned grid = (unsigned)((c->n + 255) / 256);
+  k_prolong<V, BT, V><<<grid, 256, 0, s>>>((V*)c->sb.vu[1], Phi, c->fine.L, ec, c->n, c->fine.nb, sc);
 }
-template void launch_prolong_fine<float, float>(msmg_ctx*, const float*, const double*, PcgScalars*, cudaStream_t);
+template void launch_prolong_fine<float, float>(msmg_ctx*, const float*, const float*, PcgScalars*, cudaStream_t);
 template void launch_prolong_fine<double, double>(msmg_ctx*, const double*, const double*, PcgScalars*, cudaStream_t);
 
 // ---- kernel timing (roofline figures)
@@ -390,11 +396,13 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 }
 void launch_mixed_copies(msmg_ctx* c, cudaStream_t s) {
   if (c->opts.precision != MSMG_MIXED) return;
+  auto cvt = [&](const double* a, float* b, int64_t cnt) {
+    if (cnt > 0) k_to_f32<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(a, b, cnt);
+  };
   const int64_t n = c->n;
-  k_to_f32<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->fine.T, c->fine.T32, 3 * n);
-  k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->fine.invd, c->fine.invd32, n);
-  const int64_t np = c->fine.m * c->fine.L * c->fine.nb;
-  k_to_f32<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(c->fine.Phi, c->fine.Phi32, np);
+  cvt(c->fine.T, c->fine.T32, 3 * n);
+  cvt(c->fine.invd, c->fine.invd32, n);
+  cvt(c->fine.Phi, c->fine.Phi32, c->fine.m * c->fine.L * c->fine.nb);
 }
 
 }  // namespace msmg

@@ -1,12 +1,17 @@
 // Fine-level PCG iteration kernels, one warp per element.
 //
-// Each element of E_1 (bx x by x bz cells) is handled by one warp: its data
-// is one contiguous chunk of every block-major array, loaded with coalesced
-// lane-strided accesses into a padded shared-memory tile together with the
-// one-cell halo from the face-adjacent elements.  The incomplete-Cholesky
+// Each element of E_1 (bx x by x bz cells) is handled by one warp.  Its data is
+// one contiguous chunk of every block-major array; the warp stages what it
+// reuses (the iterate u with its one-cell face halo, the face coefficients T,
+// the inverse IC(0) pivots) in shared memory with asynchronous copies, all in
+// flight at once, then works out of shared memory.  The incomplete-Cholesky
 // solves of the block-Jacobi smoother (Section 5) sweep the element in
-// wavefronts lx + ly + lz = const; the lanes own the x-lines (ly, lz) of the
-// element, so consecutive wavefronts only need a warp-level barrier.
+// wavefronts lx + ly + lz = const; the lanes own the x-lines (ly, lz), so
+// consecutive wavefronts only need a warp-level barrier.
+//
+// The element shape is a template parameter: 8^3 and 4^3 elements are compiled
+// with constant geometry (index arithmetic folds to shifts, loops unroll);
+// other shapes use the same code with runtime geometry.
 //
 // One PCG iteration on the fine level is five kernels:
 //   k_pmatvec  p = z + beta p_old (cells and halo), q = A p, reduce p.q -> alpha
@@ -20,12 +25,18 @@
 
 namespace msmg {
 
-struct WGeo {
+// compile-time element geometry
+template <int BX, int BY, int BZ>
+struct GeoC {
+  static constexpr int bx = BX, by = BY, bz = BZ, nb = BX * BY * BZ, nlines = BY * BZ;
+  static constexpr int P = (BX + 2) * (BY + 2) * (BZ + 2);
+};
+// runtime element geometry
+struct GeoR {
   int bx, by, bz, nb, nlines, P;
 };
-
-static inline WGeo make_wgeo(int bx, int by, int bz) {
-  WGeo g;
+static inline GeoR make_geor(int bx, int by, int bz) {
+  GeoR g;
   g.bx = bx; g.by = by; g.bz = bz; g.nb = bx * by * bz; g.nlines = by * bz;
   g.P = (bx + 2) * (by + 2) * (bz + 2);
   return g;
@@ -33,44 +44,9 @@ static inline WGeo make_wgeo(int bx, int by, int bz) {
 
 constexpr int kWarpsPerCta = 4;
 
-__device__ __forceinline__ int wpad(const WGeo& g, int lx, int ly, int lz) {
+template <typename G>
+__device__ __forceinline__ int wpad(const G& g, int lx, int ly, int lz) {
   return (lx + 1) + (g.bx + 2) * ((ly + 1) + (g.by + 2) * (lz + 1));
-}
-__device__ __forceinline__ int wpad_cell(const WGeo& g, int c) {
-  const int lx = c % g.bx, t = c / g.bx;
-  return wpad(g, lx, t % g.by, t / g.by);
-}
-
-// Interior of element e of X into a padded tile (lane-strided, coalesced).
-template <typename Src, typename Dst>
-__device__ __forceinline__ void w_load_interior(Dst* tile, const Src* __restrict__ X, int64_t e, const WGeo& g,
-                                                int lane) {
-  const Src* src = X + e * g.nb;
-  for (int c = lane; c < g.nb; c += 32) tile[wpad_cell(g, c)] = (Dst)src[c];
-}
-
-// Face halo of element e: faces selected by mask (bit f: -x,+x,-y,+y,-z,+z);
-// zero outside the domain.  Optional per-cell transform for the halo value.
-template <typename Src, typename Dst>
-__device__ __forceinline__ void w_load_halo(Dst* tile, const Src* __restrict__ X, int64_t e, const int* __restrict__ nbr,
-                                            const WGeo& g, int lane, int mask) {
-  const int F0 = g.by * g.bz, F1 = g.bx * g.bz, F2 = g.bx * g.by;
-  for (int f = 0; f < 6; ++f) {
-    if (!((mask >> f) & 1)) continue;
-    const int ne = nbr[e * 6 + f];
-    const int d = f >> 1;
-    const bool plus = f & 1;
-    const int F = d == 0 ? F0 : (d == 1 ? F1 : F2);
-    for (int h = lane; h < F; h += 32) {
-      int dx, dy, dz, sx, sy, sz;
-      if (d == 0) { const int u = h % g.by, v = h / g.by; dy = sy = u; dz = sz = v; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
-      else if (d == 1) { const int u = h % g.bx, v = h / g.bx; dx = sx = u; dz = sz = v; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
-      else { const int u = h % g.bx, v = h / g.bx; dx = sx = u; dy = sy = v; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
-      Dst val = (Dst)0;
-      if (ne >= 0) val = (Dst)X[(int64_t)ne * g.nb + sx + g.bx * (sy + g.by * sz)];
-      tile[wpad(g, dx, dy, dz)] = val;
-    }
-  }
 }
 
 // Element context: base offset and the six neighbour element bases (-1: none).
@@ -79,108 +55,216 @@ struct WElem {
   int64_t nb6[6];
 };
 
-__device__ __forceinline__ WElem w_elem(int64_t e, const int* __restrict__ nbr, const WGeo& g) {
+template <typename G>
+__device__ __forceinline__ WElem w_elem(int64_t e, const int* __restrict__ nbr, const G& g) {
   WElem E;
   E.base = e * g.nb;
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
-    const int ne = nbr[e * 6 + f];
+    const int ne = __ldg(nbr + e * 6 + f);
     E.nb6[f] = ne >= 0 ? (int64_t)ne * g.nb : -1;
   }
   return E;
 }
 
-// Coefficient of the -d face of local cell (lx, ly, lz): in-element, or from the
-// -d neighbour element, or zero on the domain boundary.  T is read through L1.
-template <typename V>
-__device__ __forceinline__ V w_Tminus(const V* __restrict__ Td, const WElem& E, const WGeo& g, int d, int c, int lc) {
-  const int st = d == 0 ? 1 : (d == 1 ? g.bx : g.bx * g.by);
-  const int bd = d == 0 ? g.bx : (d == 1 ? g.by : g.bz);
-  if (lc > 0) return __ldg(Td + E.base + c - st);
-  const int64_t nb = E.nb6[2 * d];
-  return nb >= 0 ? __ldg(Td + nb + c + (bd - 1) * st) : (V)0;
+// ------------------------------------------------------------------ staging
+// Asynchronous global -> shared copies: every copy of an element's working set
+// is in flight at once, so the element pays one memory latency before its
+// wavefronts run out of shared memory.
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_elem(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// one element's chunk of an array; 16-byte copies when the chunk allows it
+template <typename V, typename G>
+__device__ __forceinline__ void w_cp_array(V* dst, const V* __restrict__ src, const G& g, int lane) {
+  if ((g.nb * (int)sizeof(V)) % 16 == 0) {
+    constexpr int per = 16 / sizeof(V);
+#pragma unroll
+    for (int i = 0; i < (g.nb / per + 31) / 32; ++i) {
+      const int k = lane + 32 * i;
+      if (k < g.nb / per) cp_async_16(dst + k * per, src + k * per);
+    }
+  } else {
+    for (int i = lane; i < g.nb; i += 32) cp_async_elem(dst + i, src + i);
+  }
 }
 
-// (A u)_c: u from the padded tile, coefficients from global memory (L1).
+// element interior into the padded tile
+template <typename V, typename G>
+__device__ __forceinline__ void w_cp_padded(V* tile, const V* __restrict__ src, const G& g, int lane) {
+#pragma unroll
+  for (int i = 0; i < (g.nb + 31) / 32; ++i) {
+    const int c = lane + 32 * i;
+    if (c < g.nb) {
+      const int lx = c % g.bx, t = c / g.bx;
+      cp_async_elem(tile + wpad(g, lx, t % g.by, t / g.by), src + c);
+    }
+  }
+}
+
+// face halo f of X into the padded tile (zero on the domain boundary)
+template <typename V, typename G>
+__device__ __forceinline__ void w_cp_face(V* tile, const V* __restrict__ X, const WElem& E, const G& g, int lane,
+                                          int f) {
+  const int d = f >> 1;
+  const bool plus = f & 1;
+  const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
+  const int64_t nb = E.nb6[f];
+  for (int h = lane; h < F; h += 32) {
+    int dx, dy, dz, sx, sy, sz;
+    if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
+    else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
+    else { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dy = sy = vv; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
+    V* dst = tile + wpad(g, dx, dy, dz);
+    if (nb >= 0) cp_async_elem(dst, X + nb + sx + g.bx * (sy + g.by * sz));
+    else *dst = (V)0;
+  }
+}
+
+template <typename V, typename G>
+__device__ __forceinline__ void w_cp_halo(V* tile, const V* __restrict__ X, const WElem& E, const G& g, int lane) {
+#pragma unroll
+  for (int f = 0; f < 6; ++f) w_cp_face(tile, X, E, g, lane, f);
+}
+
+// coefficients of the element's -d boundary faces (held by the -d neighbour)
+template <typename V, typename G>
+__device__ __forceinline__ void w_cp_tminus(V* tm0, V* tm1, V* tm2, const V* __restrict__ T, int64_t n,
+                                            const WElem& E, const G& g, int lane) {
+  for (int h = lane; h < g.by * g.bz; h += 32) {          // (ly, lz) = h, source lx = bx - 1
+    const int64_t nb = E.nb6[0];
+    if (nb >= 0) cp_async_elem(tm0 + h, T + nb + (g.bx - 1) + g.bx * h);
+    else tm0[h] = (V)0;
+  }
+  for (int h = lane; h < g.bx * g.bz; h += 32) {          // (lx, lz), source ly = by - 1
+    const int64_t nb = E.nb6[2];
+    const int lx = h % g.bx, lz = h / g.bx;
+    if (nb >= 0) cp_async_elem(tm1 + h, T + n + nb + lx + g.bx * ((g.by - 1) + g.by * lz));
+    else tm1[h] = (V)0;
+  }
+  for (int h = lane; h < g.bx * g.by; h += 32) {          // (lx, ly), source lz = bz - 1
+    const int64_t nb = E.nb6[4];
+    if (nb >= 0) cp_async_elem(tm2 + h, T + 2 * n + nb + h + g.bx * g.by * (g.bz - 1));
+    else tm2[h] = (V)0;
+  }
+}
+
+// per-warp shared-memory carve of the staged working set
 template <typename V>
-__device__ __forceinline__ V w_apply_A(const V* ut, const V* __restrict__ T, int64_t n, const WElem& E, const WGeo& g,
-                                       int c) {
+struct WStage {
+  V *ut, *t0, *t1, *t2, *tm0, *tm1, *tm2, *dinv, *y;
+};
+__host__ __device__ constexpr int r4(int x) { return (x + 3) / 4 * 4; }
+template <typename G>
+__host__ __device__ inline int wstage_elems(const G& g) {
+  return r4(g.P) + 5 * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
+}
+template <typename V, typename G>
+__device__ __forceinline__ WStage<V> w_stage(unsigned char* base, const G& g, int warp) {
+  V* p = reinterpret_cast<V*>(base) + (size_t)warp * wstage_elems(g);
+  WStage<V> s;
+  s.ut = p; p += r4(g.P);
+  s.t0 = p; p += r4(g.nb);
+  s.t1 = p; p += r4(g.nb);
+  s.t2 = p; p += r4(g.nb);
+  s.dinv = p; p += r4(g.nb);
+  s.y = p; p += r4(g.nb);
+  s.tm0 = p; p += r4(g.by * g.bz);
+  s.tm1 = p; p += r4(g.bx * g.bz);
+  s.tm2 = p;
+  return s;
+}
+
+template <typename V, typename G>
+__device__ __forceinline__ void w_stage_T(const WStage<V>& s, const V* __restrict__ T, const V* __restrict__ invd,
+                                          int64_t n, const WElem& E, const G& g, int lane, bool with_dinv) {
+  w_cp_array(s.t0, T + E.base, g, lane);
+  w_cp_array(s.t1, T + n + E.base, g, lane);
+  w_cp_array(s.t2, T + 2 * n + E.base, g, lane);
+  if (with_dinv) w_cp_array(s.dinv, invd + E.base, g, lane);
+  w_cp_tminus(s.tm0, s.tm1, s.tm2, T, n, E, g, lane);
+}
+
+// (A u)_c from the staged tiles
+template <typename V, typename G>
+__device__ __forceinline__ V w_apply_A_s(const WStage<V>& s, const G& g, int c) {
   const int lx = c % g.bx, t = c / g.bx, ly = t % g.by, lz = t / g.by;
   const int pc = wpad(g, lx, ly, lz);
   const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
+  const V* ut = s.ut;
   const V uc = ut[pc];
-  const V tx = __ldg(T + E.base + c), ty = __ldg(T + n + E.base + c), tz = __ldg(T + 2 * n + E.base + c);
-  const V mx = w_Tminus(T, E, g, 0, c, lx), my = w_Tminus(T + n, E, g, 1, c, ly), mz = w_Tminus(T + 2 * n, E, g, 2, c, lz);
-  V acc = tx * (uc - ut[pc + 1]) + mx * (uc - ut[pc - 1]);
-  acc += ty * (uc - ut[pc + sy]) + my * (uc - ut[pc - sy]);
-  acc += tz * (uc - ut[pc + sz]) + mz * (uc - ut[pc - sz]);
+  const V mx = lx > 0 ? s.t0[c - 1] : s.tm0[ly + g.by * lz];
+  const V my = ly > 0 ? s.t1[c - g.bx] : s.tm1[lx + g.bx * lz];
+  const V mz = lz > 0 ? s.t2[c - g.bx * g.by] : s.tm2[lx + g.bx * ly];
+  V acc = s.t0[c] * (uc - ut[pc + 1]) + mx * (uc - ut[pc - 1]);
+  acc += s.t1[c] * (uc - ut[pc + sy]) + my * (uc - ut[pc - sy]);
+  acc += s.t2[c] * (uc - ut[pc + sz]) + mz * (uc - ut[pc - sz]);
   return acc;
 }
 
-// y <- M^{-1} y on the element, M = (D~ + L) D~^{-1} (D~ + L^T): forward then
-// backward wavefronts; lanes own x-lines; y indexed by the element-local cell.
-template <typename V>
-__device__ __forceinline__ void w_ic0(V* y, const V* __restrict__ T, const V* __restrict__ invd, int64_t n,
-                                      const WElem& E, const WGeo& g, int lane) {
+// y <- M^{-1} y from the staged tiles, M = (D~ + L) D~^{-1} (D~ + L^T):
+// forward then backward wavefronts lx + ly + lz = w; lane l owns the lines
+// l, l + 32, ... (line = ly + by * lz).
+template <typename V, typename G>
+__device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane) {
   const int smax = g.bx + g.by + g.bz - 3;
   const int bxy = g.bx * g.by;
-  const V* T0 = T + E.base;
-  const V* T1 = T + n + E.base;
-  const V* T2 = T + 2 * n + E.base;
-  const V* D = invd + E.base;
+  V* y = s.y;
   for (int w = 0; w <= smax; ++w) {
-    for (int l = lane; l < g.nlines; l += 32) {
+#pragma unroll
+    for (int i = 0; i < (g.nlines + 31) / 32; ++i) {
+      const int l = lane + 32 * i;
+      if (l >= g.nlines) continue;
       const int ly = l % g.by, lz = l / g.by;
       const int lx = w - ly - lz;
       if (lx < 0 || lx >= g.bx) continue;
       const int c = lx + g.bx * ly + bxy * lz;
       V acc = y[c];
-      if (lx > 0) acc += __ldg(T0 + c - 1) * y[c - 1];
-      if (ly > 0) acc += __ldg(T1 + c - g.bx) * y[c - g.bx];
-      if (lz > 0) acc += __ldg(T2 + c - bxy) * y[c - bxy];
-      y[c] = acc * __ldg(D + c);
+      if (lx > 0) acc += s.t0[c - 1] * y[c - 1];
+      if (ly > 0) acc += s.t1[c - g.bx] * y[c - g.bx];
+      if (lz > 0) acc += s.t2[c - bxy] * y[c - bxy];
+      y[c] = acc * s.dinv[c];
     }
     __syncwarp();
   }
   for (int w = smax; w >= 0; --w) {
-    for (int l = lane; l < g.nlines; l += 32) {
+#pragma unroll
+    for (int i = 0; i < (g.nlines + 31) / 32; ++i) {
+      const int l = lane + 32 * i;
+      if (l >= g.nlines) continue;
       const int ly = l % g.by, lz = l / g.by;
       const int lx = w - ly - lz;
       if (lx < 0 || lx >= g.bx) continue;
       const int c = lx + g.bx * ly + bxy * lz;
       V acc = (V)0;
-      if (lx < g.bx - 1) acc += __ldg(T0 + c) * y[c + 1];
-      if (ly < g.by - 1) acc += __ldg(T1 + c) * y[c + g.bx];
-      if (lz < g.bz - 1) acc += __ldg(T2 + c) * y[c + bxy];
-      y[c] += __ldg(D + c) * acc;
+      if (lx < g.bx - 1) acc += s.t0[c] * y[c + 1];
+      if (ly < g.by - 1) acc += s.t1[c] * y[c + g.bx];
+      if (lz < g.bz - 1) acc += s.t2[c] * y[c + bxy];
+      y[c] += s.dinv[c] * acc;
     }
     __syncwarp();
   }
 }
 
-template <typename V>
-struct WTiles {
-  V *ut, *y;
-};
-
-// per warp: padded u tile (P) and the wavefront vector (nb)
-template <typename V>
-__device__ __forceinline__ WTiles<V> w_carve(unsigned char* base, const WGeo& g, int warp) {
-  V* p = reinterpret_cast<V*>(base) + (size_t)warp * (g.P + g.nb);
-  WTiles<V> t;
-  t.ut = p;
-  t.y = p + g.P;
-  return t;
-}
-
 // ------------------------------------------------------------------ k_pre
 // update != 0: x += alpha p, r -= alpha q, rr = r.r (convergence bookkeeping);
 // then f = r (in V precision, also written to rv) and u = M^{-1} f.
-template <typename V>
+template <typename V, typename G>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ x, double* __restrict__ r,
                                                            const double* __restrict__ p, const double* __restrict__ q,
                                                            const V* __restrict__ T, const V* __restrict__ invd,
-                                                           V* __restrict__ rv, V* __restrict__ u, int64_t n, WGeo g,
+                                                           V* __restrict__ rv, V* __restrict__ u, int64_t n, G g,
                                                            int64_t m, const int* __restrict__ nbr, int update,
                                                            RedSlot red, PcgScalars* sc) {
   if (sc && sc->done) return;
@@ -188,27 +272,51 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
   const bool act = e < m;
-  const WTiles<V> s = w_carve<V>(smem, g, warp);
+  const WStage<V> s = w_stage<V>(smem, g, warp);
   double acc = 0.0;
   if (act) {
-    const double alpha = update ? sc->alpha : 0.0;
     const WElem E = w_elem(e, nbr, g);
+    w_stage_T(s, T, invd, n, E, g, lane, true);
+    const double alpha = update ? sc->alpha : 0.0;
     const int64_t base = E.base;
-    for (int c = lane; c < g.nb; c += 32) {
-      double rc = r[base + c];
-      if (update) {
-        x[base + c] += alpha * p[base + c];
-        rc -= alpha * q[base + c];
-        r[base + c] = rc;
-        acc += rc * rc;
+    // batches of 8 cells per lane: all loads of a batch are issued before use
+    constexpr int kB = 8;
+    const int ncl = (g.nb + 31) / 32;
+    for (int b0 = 0; b0 < ncl; b0 += kB) {
+      double rr[kB], qq[kB], xx[kB], pp[kB];
+#pragma unroll
+      for (int i = 0; i < kB; ++i) {
+        const int c = lane + 32 * (b0 + i);
+        const bool in = b0 + i < ncl && c < g.nb;
+        rr[i] = in ? r[base + c] : 0.0;
+        qq[i] = (in && update) ? q[base + c] : 0.0;
+        xx[i] = (in && update) ? x[base + c] : 0.0;
+        pp[i] = (in && update) ? p[base + c] : 0.0;
       }
-      const V fv = (V)rc;
-      s.y[c] = fv;
-      rv[base + c] = fv;
+#pragma unroll
+      for (int i = 0; i < kB; ++i) {
+        const int c = lane + 32 * (b0 + i);
+        if (!(b0 + i < ncl && c < g.nb)) continue;
+        double rc = rr[i];
+        if (update) {
+          x[base + c] = fma(alpha, pp[i], xx[i]);
+          rc = fma(-alpha, qq[i], rc);
+          r[base + c] = rc;
+          acc = fma(rc, rc, acc);
+        }
+        const V fv = (V)rc;
+        s.y[c] = fv;
+        rv[base + c] = fv;
+      }
     }
+    cp_async_wait_all();
     __syncwarp();
-    w_ic0(s.y, T, invd, n, E, g, lane);
-    for (int c = lane; c < g.nb; c += 32) u[base + c] = s.y[c];
+    w_ic0_s(s, g, lane);
+#pragma unroll 4
+    for (int i = 0; i < (g.nb + 31) / 32; ++i) {
+      const int c = lane + 32 * i;
+      if (c < g.nb) u[base + c] = s.y[c];
+    }
   }
   if (update) {
     double v[1] = {acc};
@@ -223,67 +331,140 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
 }
 
 // ------------------------------------------------------------------ k_restrict
-template <typename V, typename BT>
+// Residual in registers (each lane's cells), then one warp reduction per local
+// eigenvector; every global load is issued before the first use.
+template <typename V, typename BT, typename G>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) k_restrict(const V* __restrict__ f, const V* __restrict__ u,
                                                                 const V* __restrict__ T, const BT* __restrict__ Phi,
-                                                                int L, double* __restrict__ rc, int64_t n, WGeo g,
+                                                                int L, double* __restrict__ rc, int64_t n, G g,
                                                                 int64_t m, const int* __restrict__ nbr,
                                                                 const PcgScalars* sc) {
   if (sc && sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int kC = 16;                                   // cells per lane held in registers
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
   if (e >= m) return;
-  const WTiles<V> s = w_carve<V>(smem, g, warp);
+  const WStage<V> s = w_stage<V>(smem, g, warp);
   const WElem E = w_elem(e, nbr, g);
-  w_load_interior(s.ut, u, e, g, lane);
-  w_load_halo(s.ut, u, e, nbr, g, lane, 0x3f);
-  __syncwarp();
-  const int64_t base = E.base;
-  for (int c = lane; c < g.nb; c += 32) s.y[c] = f[base + c] - w_apply_A(s.ut, T, n, E, g, c);
-  __syncwarp();
-  // accumulate in the V-cycle precision (FP32 in the mixed form: the FP64 pipe of
-  // this part is 1/64 of its FP32 rate)
-  for (int k = 0; k < L; ++k) {
-    const BT* ph = Phi + (e * L + k) * g.nb;
-    V acc = (V)0;
-    for (int c = lane; c < g.nb; c += 32) acc += (V)ph[c] * s.y[c];
-    acc = warp_sum_t(acc);
-    if (lane == 0) rc[e * L + k] = (double)acc;
+  w_cp_padded(s.ut, u + E.base, g, lane);
+  w_cp_halo(s.ut, u, E, g, lane);
+  w_stage_T(s, T, (const V*)nullptr, n, E, g, lane, false);
+  const int ncl = (g.nb + 31) / 32;
+  if (ncl <= kC) {
+    V w[kC];
+#pragma unroll
+    for (int i = 0; i < kC; ++i) {
+      const int c = lane + 32 * i;
+      w[i] = (i < ncl && c < g.nb) ? __ldg(f + E.base + c) : (V)0;
+    }
+    cp_async_wait_all();
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kC; ++i) {
+      const int c = lane + 32 * i;
+      if (i < ncl && c < g.nb) w[i] -= w_apply_A_s(s, g, c);
+    }
+    // accumulate in the V-cycle precision (FP32 in the mixed form: the FP64 pipe
+    // runs at 1/64 of the FP32 rate)
+    for (int k = 0; k < L; ++k) {
+      const BT* ph = Phi + (e * L + k) * g.nb;
+      V acc = (V)0;
+#pragma unroll
+      for (int i = 0; i < kC; ++i) {
+        const int c = lane + 32 * i;
+        if (i < ncl && c < g.nb) acc += (V)__ldg(ph + c) * w[i];
+      }
+      acc = warp_sum_t(acc);
+      if (lane == 0) rc[e * L + k] = (double)acc;
+    }
+  } else {
+    cp_async_wait_all();
+    __syncwarp();
+    for (int c = lane; c < g.nb; c += 32) s.y[c] = __ldg(f + E.base + c) - w_apply_A_s(s, g, c);
+    __syncwarp();
+    for (int k = 0; k < L; ++k) {
+      const BT* ph = Phi + (e * L + k) * g.nb;
+      V acc = (V)0;
+      for (int c = lane; c < g.nb; c += 32) acc += (V)__ldg(ph + c) * s.y[c];
+      acc = warp_sum_t(acc);
+      if (lane == 0) rc[e * L + k] = (double)acc;
+    }
   }
 }
 
 // ------------------------------------------------------------------ k_post
-// z = u + M^{-1} (f - A u); reductions: r.z (FP64 r) and z.q (flexible beta).
-template <typename V>
+// z = u + M^{-1} (f - A u), written in FP64; reductions: r.z and z.q (flexible
+// beta).  f, r and q are loaded into registers before the wavefronts start.
+template <typename V, typename G>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict__ f, const double* __restrict__ r,
                                                             const V* __restrict__ u, const V* __restrict__ T,
-                                                            const V* __restrict__ invd, V* __restrict__ z,
-                                                            const double* __restrict__ qv, int64_t n, WGeo g,
+                                                            const V* __restrict__ invd, double* __restrict__ z,
+                                                            const double* __restrict__ qv, int64_t n, G g,
                                                             int64_t m, const int* __restrict__ nbr, RedSlot red,
                                                             PcgScalars* sc) {
   if (sc && sc->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int kC = 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
   const bool act = e < m;
-  const WTiles<V> s = w_carve<V>(smem, g, warp);
+  const WStage<V> s = w_stage<V>(smem, g, warp);
+  const int ncl = (g.nb + 31) / 32;
   double v[2] = {0.0, 0.0};
-  if (act) {
+  if (act && ncl <= kC) {
     const WElem E = w_elem(e, nbr, g);
     const int64_t base = E.base;
-    w_load_interior(s.ut, u, e, g, lane);
-    w_load_halo(s.ut, u, e, nbr, g, lane, 0x3f);
+    w_cp_padded(s.ut, u + base, g, lane);
+    w_cp_halo(s.ut, u, E, g, lane);
+    w_stage_T(s, T, invd, n, E, g, lane, true);
+    V fr[kC];
+    double rr[kC], qq[kC];
+#pragma unroll
+    for (int i = 0; i < kC; ++i) {
+      const int c = lane + 32 * i;
+      const bool in = i < ncl && c < g.nb;
+      fr[i] = in ? __ldg(f + base + c) : (V)0;
+      rr[i] = (in && sc) ? __ldg(r + base + c) : 0.0;
+      qq[i] = (in && qv) ? __ldg(qv + base + c) : 0.0;
+    }
+    cp_async_wait_all();
     __syncwarp();
-    for (int c = lane; c < g.nb; c += 32) s.y[c] = f[base + c] - w_apply_A(s.ut, T, n, E, g, c);
+#pragma unroll
+    for (int i = 0; i < kC; ++i) {
+      const int c = lane + 32 * i;
+      if (i < ncl && c < g.nb) s.y[c] = fr[i] - w_apply_A_s(s, g, c);
+    }
     __syncwarp();
-    w_ic0(s.y, T, invd, n, E, g, lane);
+    w_ic0_s(s, g, lane);
+#pragma unroll
+    for (int i = 0; i < kC; ++i) {
+      const int c = lane + 32 * i;
+      if (!(i < ncl && c < g.nb)) continue;
+      const int lx = c % g.bx, t = c / g.bx;
+      const double zc = (double)(s.ut[wpad(g, lx, t % g.by, t / g.by)] + s.y[c]);
+      z[base + c] = zc;
+      v[0] = fma(rr[i], zc, v[0]);
+      v[1] = fma(zc, qq[i], v[1]);
+    }
+  } else if (act) {
+    const WElem E = w_elem(e, nbr, g);
+    const int64_t base = E.base;
+    w_cp_padded(s.ut, u + base, g, lane);
+    w_cp_halo(s.ut, u, E, g, lane);
+    w_stage_T(s, T, invd, n, E, g, lane, true);
+    cp_async_wait_all();
+    __syncwarp();
+    for (int c = lane; c < g.nb; c += 32) s.y[c] = __ldg(f + base + c) - w_apply_A_s(s, g, c);
+    __syncwarp();
+    w_ic0_s(s, g, lane);
     for (int c = lane; c < g.nb; c += 32) {
-      const V zc = s.ut[wpad_cell(g, c)] + s.y[c];
+      const int lx = c % g.bx, t = c / g.bx;
+      const double zc = (double)(s.ut[wpad(g, lx, t % g.by, t / g.by)] + s.y[c]);
       z[base + c] = zc;
       if (sc) {
-        v[0] += r[base + c] * (double)zc;
-        if (qv) v[1] += (double)zc * qv[base + c];
+        v[0] = fma(r[base + c], zc, v[0]);
+        if (qv) v[1] = fma(zc, qv[base + c], v[1]);
       }
     }
   }
@@ -300,10 +481,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
 
 // ------------------------------------------------------------------ k_pmatvec
 // p = z + beta p_old on the element and its halo, q = A p (FP64), reduce p.q.
-template <typename V>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const V* __restrict__ z, const double* __restrict__ pold,
+template <typename G>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __restrict__ z, const double* __restrict__ pold,
                                                                double* __restrict__ pnew, double* __restrict__ q,
-                                                               const double* __restrict__ T, int64_t n, WGeo g,
+                                                               const double* __restrict__ T,
+                                                               const double* __restrict__ Dg, int64_t n, G g,
                                                                int64_t m, const int* __restrict__ nbr, RedSlot red,
                                                                PcgScalars* sc) {
   if (sc->done) return;
@@ -311,45 +493,66 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const V* __restri
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
   const bool act = e < m;
-  const WTiles<double> s = w_carve<double>(smem, g, warp);
+  double* ut = reinterpret_cast<double*>(smem) + (size_t)warp * r4(g.P);
   double acc = 0.0;
   if (act) {
     const double beta = sc->beta;
-    const int64_t base = e * g.nb;
-    // p tile: interior and halo, p = z + beta pold
-    for (int c = lane; c < g.nb; c += 32) {
-      const double pv = (double)z[base + c] + beta * pold[base + c];
-      s.ut[wpad_cell(g, c)] = pv;
+    const WElem E = w_elem(e, nbr, g);
+    const int64_t base = E.base;
+#pragma unroll 4
+    for (int i = 0; i < (g.nb + 31) / 32; ++i) {
+      const int c = lane + 32 * i;
+      if (c >= g.nb) continue;
+      const double pv = fma(beta, pold[base + c], z[base + c]);
+      const int lx = c % g.bx, t = c / g.bx;
+      ut[wpad(g, lx, t % g.by, t / g.by)] = pv;
       pnew[base + c] = pv;
     }
-    {
-      const int F0 = g.by * g.bz, F1 = g.bx * g.bz, F2 = g.bx * g.by;
-      for (int f = 0; f < 6; ++f) {
-        const int ne = nbr[e * 6 + f];
-        const int d = f >> 1;
-        const bool plus = f & 1;
-        const int F = d == 0 ? F0 : (d == 1 ? F1 : F2);
-        for (int h = lane; h < F; h += 32) {
-          int dx, dy, dz, sx, sy, sz;
-          if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
-          else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
-          else { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dy = sy = vv; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
-          double val = 0.0;
-          if (ne >= 0) {
-            const int64_t src = (int64_t)ne * g.nb + sx + g.bx * (sy + g.by * sz);
-            val = (double)z[src] + beta * pold[src];
-          }
-          s.ut[wpad(g, dx, dy, dz)] = val;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1;
+      const bool plus = f & 1;
+      const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
+      const int64_t nb = E.nb6[f];
+      for (int h = lane; h < F; h += 32) {
+        int dx, dy, dz, sx, sy, sz;
+        if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
+        else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
+        else { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dy = sy = vv; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
+        double val = 0.0;
+        if (nb >= 0) {
+          const int64_t src = nb + sx + g.bx * (sy + g.by * sz);
+          val = fma(beta, pold[src], z[src]);
         }
+        ut[wpad(g, dx, dy, dz)] = val;
       }
     }
     __syncwarp();
-    const WElem E = w_elem(e, nbr, g);
-    for (int c = lane; c < g.nb; c += 32) {
-      const int pc = wpad_cell(g, c);
-      const double a = w_apply_A(s.ut, T, n, E, g, c);
+    const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
+#pragma unroll 2
+    for (int i = 0; i < (g.nb + 31) / 32; ++i) {
+      const int c = lane + 32 * i;
+      if (c >= g.nb) continue;
+      const int lx = c % g.bx, t = c / g.bx, ly = t % g.by, lz = t / g.by;
+      const int pc = wpad(g, lx, ly, lz);
+      const double pcv = ut[pc];
+      // -d face coefficients: in-element, or held by the -d neighbour
+      const double mx = lx > 0 ? __ldg(T + base + c - 1)
+                                : (E.nb6[0] >= 0 ? __ldg(T + E.nb6[0] + c + g.bx - 1) : 0.0);
+      const double my = ly > 0 ? __ldg(T + n + base + c - g.bx)
+                                : (E.nb6[2] >= 0 ? __ldg(T + n + E.nb6[2] + c + g.bx * (g.by - 1)) : 0.0);
+      const double mz = lz > 0 ? __ldg(T + 2 * n + base + c - g.bx * g.by)
+                                : (E.nb6[4] >= 0 ? __ldg(T + 2 * n + E.nb6[4] + c + g.bx * g.by * (g.bz - 1)) : 0.0);
+      // (A p)_c = D_c p_c - sum_f T_f p_nb: one multiply and six FMAs in FP64
+      double a = __ldg(Dg + base + c) * pcv;
+      a = fma(-__ldg(T + base + c), ut[pc + 1], a);
+      a = fma(-mx, ut[pc - 1], a);
+      a = fma(-__ldg(T + n + base + c), ut[pc + sy], a);
+      a = fma(-my, ut[pc - sy], a);
+      a = fma(-__ldg(T + 2 * n + base + c), ut[pc + sz], a);
+      a = fma(-mz, ut[pc - sz], a);
       q[base + c] = a;
-      acc += a * s.ut[pc];
+      acc = fma(a, pcv, acc);
     }
   }
   double v[1] = {acc};
@@ -360,13 +563,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const V* __restri
   });
 }
 
-// z (V) -> FP64
-template <typename V>
-__global__ void k_widen(const V* __restrict__ a, double* __restrict__ b, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (double)a[i];
-}
-
 // ------------------------------------------------------------------ host side
 template <typename V, typename BT>
 struct FineOps {
@@ -375,134 +571,128 @@ struct FineOps {
   const BT* Phi;
 };
 
-static inline size_t wsmem(const WGeo& g, size_t vsize) {
-  return (size_t)kWarpsPerCta * (g.P + g.nb) * vsize;
+template <typename G>
+static inline size_t wsmem(const G& g, size_t vsize) {
+  return (size_t)kWarpsPerCta * wstage_elems(g) * vsize;
+}
+template <typename G>
+static inline size_t wsmem_p(const G& g) {
+  return (size_t)kWarpsPerCta * r4(g.P) * sizeof(double);
+}
+
+// run f(geometry) with the compile-time geometry of the element when available
+template <typename F>
+static void with_geo(const msmg_ctx* c, F&& f) {
+  const int bx = c->fine.bx, by = c->fine.by, bz = c->fine.bz;
+  if (bx == 8 && by == 8 && bz == 8) f(GeoC<8, 8, 8>{});
+  else if (bx == 4 && by == 4 && bz == 4) f(GeoC<4, 4, 4>{});
+  else f(make_geor(bx, by, bz));
+}
+
+template <typename V, typename BT, typename G>
+static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* sc, cudaStream_t s, const G& g) {
+  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
+  SolveBuffers& B = c->sb;
+  k_pre<V, G><<<grid, kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv,
+                                                                    (V*)B.vu[1], c->n, g, c->fine.m, c->fine.nbr,
+                                                                    update, c->red, sc);
+}
+
+template <typename V, typename BT, typename G>
+static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cudaStream_t s, const G& g) {
+  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
+  SolveBuffers& B = c->sb;
+  k_restrict<V, BT, G><<<grid, kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+      (const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L, (double*)B.vf[2], c->n, g, c->fine.m, c->fine.nbr, sc);
+}
+
+template <typename V, typename BT, typename G>
+static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const double* qv, PcgScalars* sc, cudaStream_t s,
+                   const G& g) {
+  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
+  SolveBuffers& B = c->sb;
+  k_post<V, G><<<grid, kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>((const V*)B.rv, B.r, (const V*)B.vu[1], o.T,
+                                                                     o.invd, B.z, qv, c->n, g, c->fine.m,
+                                                                     c->fine.nbr, c->red, sc);
+}
+
+template <typename G>
+static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s, const G& g) {
+  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
+  SolveBuffers& B = c->sb;
+  k_pmatvec<G><<<grid, kWarpsPerCta * 32, wsmem_p(g), s>>>(B.z, B.pcur, B.pnext, B.q, c->fine.T,
+                                                              c->fine.D, c->n, g, c->fine.m, c->fine.nbr, c->red, sc);
 }
 
 template <typename V, typename BT>
-static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* sc, cudaStream_t s) {
-  const WGeo g = make_wgeo(c->fine.bx, c->fine.by, c->fine.bz);
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
-  const size_t sm = wsmem(g, sizeof(V));
-  SolveBuffers& B = c->sb;
-  k_pre<V><<<grid, kWarpsPerCta * 32, sm, s>>>(B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv, (V*)B.vu[1], c->n, g,
-                                               c->fine.m, c->fine.nbr, update, c->red, sc);
-}
-
-template <typename V, typename BT>
-static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cudaStream_t s) {
-  const WGeo g = make_wgeo(c->fine.bx, c->fine.by, c->fine.bz);
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
-  const size_t sm = wsmem(g, sizeof(V));
-  SolveBuffers& B = c->sb;
-  k_restrict<V, BT><<<grid, kWarpsPerCta * 32, sm, s>>>((const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L,
-                                                        (double*)B.vf[2], c->n, g, c->fine.m, c->fine.nbr, sc);
-}
-
-template <typename V, typename BT>
-static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const double* qv, PcgScalars* sc, cudaStream_t s) {
-  const WGeo g = make_wgeo(c->fine.bx, c->fine.by, c->fine.bz);
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
-  const size_t sm = wsmem(g, sizeof(V));
-  SolveBuffers& B = c->sb;
-  k_post<V><<<grid, kWarpsPerCta * 32, sm, s>>>((const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, (V*)B.zv, qv,
-                                                c->n, g, c->fine.m, c->fine.nbr, c->red, sc);
-}
-
-template <typename V>
-static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s) {
-  const WGeo g = make_wgeo(c->fine.bx, c->fine.by, c->fine.bz);
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
-  const size_t sm = wsmem(g, sizeof(double));
-  SolveBuffers& B = c->sb;
-  k_pmatvec<V><<<grid, kWarpsPerCta * 32, sm, s>>>((const V*)B.zv, B.pcur, B.pnext, B.q, c->fine.T, c->n, g,
-                                                   c->fine.m, c->fine.nbr, c->red, sc);
-}
-
-template <typename V, typename BT>
-void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const double* ec, PcgScalars* sc, cudaStream_t s);
+void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const V* ec, PcgScalars* sc, cudaStream_t s);
 
 // Shared-memory limits of the fine-level kernels, set once per context (never
 // during stream capture).
-template <typename V, typename BT>
-static void prepare_t(msmg_ctx* c) {
-  const WGeo g = make_wgeo(c->fine.bx, c->fine.by, c->fine.bz);
-  const int smv = (int)wsmem(g, sizeof(V)), smd = (int)wsmem(g, sizeof(double));
-  cudaFuncSetAttribute(k_pre<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
-  cudaFuncSetAttribute(k_restrict<V, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
-  cudaFuncSetAttribute(k_post<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
-  cudaFuncSetAttribute(k_pmatvec<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
+template <typename V, typename BT, typename G>
+static void prepare_t(const G& g) {
+  const int smv = (int)wsmem(g, sizeof(V)), smd = (int)wsmem_p(g);
+  cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+  cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+  cudaFuncSetAttribute(k_post<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+  cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
 }
 
 void prepare_fine_kernels(msmg_ctx* c) {
-  if (c->opts.precision == MSMG_MIXED) prepare_t<float, float>(c);
-  else prepare_t<double, double>(c);
+  with_geo(c, [&](auto g) {
+    if (c->opts.precision == MSMG_MIXED) prepare_t<float, float>(g);
+    else prepare_t<double, double>(g);
+  });
 }
 
-const double* coarse_cycle(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t s);
+const void* coarse_cycle(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t s);
 
-// Fine-level V-cycle on the residual held in B.r (FP64); result in B.zv (V).
+// Fine-level V-cycle on the residual held in B.r (FP64); result in B.z (FP64).
 // update != 0 first performs the PCG update of x and r with the current alpha.
+// With ev != nullptr, events ev[0..5] bracket the pieces (kernel timing).
 template <typename V, typename BT>
 static void vcycle_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, const double* qv, PcgScalars* sc,
-                     cudaStream_t s) {
-  pre_t<V, BT>(c, o, update, sc, s);
-  restrict_t<V, BT>(c, o, sc, s);
-  const double* ec = coarse_cycle(c, 2, sc, s);
-  launch_prolong_fine<V, BT>(c, o.Phi, ec, sc, s);
-  post_t<V, BT>(c, o, qv, sc, s);
+                     cudaStream_t s, cudaEvent_t* ev) {
+  with_geo(c, [&](auto g) {
+    if (ev) cudaEventRecord(ev[0], s);
+    pre_t<V, BT>(c, o, update, sc, s, g);
+    if (ev) cudaEventRecord(ev[1], s);
+    restrict_t<V, BT>(c, o, sc, s, g);
+    if (ev) cudaEventRecord(ev[2], s);
+    const V* ec = (const V*)coarse_cycle(c, 2, sc, s);
+    if (ev) cudaEventRecord(ev[3], s);
+    launch_prolong_fine<V, BT>(c, o.Phi, ec, sc, s);
+    if (ev) cudaEventRecord(ev[4], s);
+    post_t<V, BT>(c, o, qv, sc, s, g);
+    if (ev) cudaEventRecord(ev[5], s);
+  });
 }
 
-void pcg_step_vcycle(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s) {
+static void pcg_step_vcycle_ev(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s,
+                               cudaEvent_t* ev) {
   if (c->opts.precision == MSMG_MIXED) {
     FineOps<float, float> o{c->fine.T32, c->fine.invd32, c->fine.Phi32};
-    vcycle_t<float, float>(c, o, update, qv, sc, s);
+    vcycle_t<float, float>(c, o, update, qv, sc, s, ev);
   } else {
     FineOps<double, double> o{c->fine.T, c->fine.invd, c->fine.Phi};
-    vcycle_t<double, double>(c, o, update, qv, sc, s);
+    vcycle_t<double, double>(c, o, update, qv, sc, s, ev);
   }
 }
 
-template <typename V, typename BT>
-static void vcycle_timed_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, const double* qv, PcgScalars* sc,
-                           cudaStream_t s, cudaEvent_t* ev) {
-  cudaEventRecord(ev[0], s);
-  pre_t<V, BT>(c, o, update, sc, s);
-  cudaEventRecord(ev[1], s);
-  restrict_t<V, BT>(c, o, sc, s);
-  cudaEventRecord(ev[2], s);
-  const double* ec = coarse_cycle(c, 2, sc, s);
-  cudaEventRecord(ev[3], s);
-  launch_prolong_fine<V, BT>(c, o.Phi, ec, sc, s);
-  cudaEventRecord(ev[4], s);
-  post_t<V, BT>(c, o, qv, sc, s);
-  cudaEventRecord(ev[5], s);
+void pcg_step_vcycle(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s) {
+  pcg_step_vcycle_ev(c, update, qv, sc, s, nullptr);
 }
 
 void pcg_step_vcycle_timed(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s,
                            cudaEvent_t* ev) {
-  if (c->opts.precision == MSMG_MIXED) {
-    FineOps<float, float> o{c->fine.T32, c->fine.invd32, c->fine.Phi32};
-    vcycle_timed_t<float, float>(c, o, update, qv, sc, s, ev);
-  } else {
-    FineOps<double, double> o{c->fine.T, c->fine.invd, c->fine.Phi};
-    vcycle_timed_t<double, double>(c, o, update, qv, sc, s, ev);
-  }
+  pcg_step_vcycle_ev(c, update, qv, sc, s, ev);
 }
 
 void pcg_step_pmatvec(msmg_ctx* c, PcgScalars* sc, cudaStream_t s) {
-  if (c->opts.precision == MSMG_MIXED) pmatvec_t<float>(c, sc, s);
-  else pmatvec_t<double>(c, sc, s);
+  with_geo(c, [&](auto g) { pmatvec_t(c, sc, s, g); });
 }
 
 // z = P^{-1} r in FP64 (natural order handled by the caller): r in B.r, result in B.z.
-void apply_vcycle_fp64_out(msmg_ctx* c, cudaStream_t s) {
-  pcg_step_vcycle(c, 0, nullptr, nullptr, s);
-  const unsigned g1 = (unsigned)((c->n + 255) / 256);
-  if (c->opts.precision == MSMG_MIXED) k_widen<float><<<g1, 256, 0, s>>>((const float*)c->sb.zv, c->sb.z, c->n);
-  else k_widen<double><<<g1, 256, 0, s>>>((const double*)c->sb.zv, c->sb.z, c->n);
-}
-
-int fine_warp_vcycle_launches(const msmg_ctx* c) { return 4; }
+void apply_vcycle_fp64_out(msmg_ctx* c, cudaStream_t s) { pcg_step_vcycle(c, 0, nullptr, nullptr, s); }
 
 }  // namespace msmg

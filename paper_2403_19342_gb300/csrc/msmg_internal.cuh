@@ -87,6 +87,7 @@ struct FineLevel {
   double* T;                    // [3][n] face coefficients (FP64, block-major)
   double* S;                    // [n] Tr K~
   double* invd;                 // [n] inverse IC(0) pivots
+  double* D;                    // [n] diagonal of A (sum of the six face coefficients)
   double* Phi;                  // [m][L][nb] S-orthonormal basis
   double* lam;                  // [m][L]
   float* T32;                   // mixed-precision copies (nullptr in FP64 mode)
@@ -124,8 +125,9 @@ struct SolveBuffers {
   double *b, *x, *r, *z, *p0, *p1, *q;
   double *pcur, *pnext;         // ping-pong search directions of the current iteration
   void* rv;                     // residual in V-cycle precision
-  void* zv;                     // preconditioned residual in V-cycle precision
-  // V-cycle work on every level: f (right side), u (iterate), w (scratch)
+  float* ec32;                  // FP32 copy of the level-2 correction (mixed form), else nullptr
+  // V-cycle work on every level: f (right side), u (iterate), w (scratch); level 1 in
+  // the V-cycle precision, levels >= 2 in FP64
   void* vf[kMaxLevels];
   void* vu[kMaxLevels];
   void* vw[kMaxLevels];

@@ -77,6 +77,24 @@ __global__ void k_init_x0(double* __restrict__ b, double* __restrict__ r, const 
   });
 }
 
+// residual replacement: r = b - q (q = A x), rr; restart the recurrence
+__global__ void k_restart(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
+                          int64_t n, RedSlot red, PcgScalars* sc) {
+  double v[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - q[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  grid_reduce<1>(v, red, [=] __device__(double* t) {
+    sc->rr = t[0];
+    sc->rz = 0.0;
+    sc->pq = 0.0;
+    sc->beta = 0.0;
+    sc->done = t[0] <= sc->tol2 ? 1 : 0;
+  });
+}
+
 __global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n, const PcgScalars* sc) {
   if (sc && sc->done) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -209,41 +227,63 @@ static int pcg_one(msmg_ctx* c, double rtol, int max_iter, bool use_x0, int flag
   const int64_t vc_launches = 4 + 4 * (int64_t)(c->nL - 2) + 1;
   int64_t launches = 3 + (use_x0 ? 2 : 1) + vc_launches;
   const bool graph = !(flags & MSMG_FLAG_NO_GRAPH) && build_iteration_graph(c) == 1;
-  if (graph) {
-    // two iterations per graph launch (the p buffers alternate); kernels are
-    // no-ops once the device flag is set, so the count stays exact
-    for (int it = 0; it < max_iter; it += 2) {
-      launches += 2 * (1 + vc_launches);
-      MSMG_CUDA_TRY(cudaGraphLaunch(c->iter_graph, s));
-      if ((it & 7) == 6 || it + 2 >= max_iter) {
-        MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-        MSMG_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hsc.done) break;
+  auto iterate = [&](int budget) -> int {
+    if (graph) {
+      // two iterations per graph launch (the p buffers alternate); kernels are
+      // no-ops once the device flag is set, so the count stays exact
+      for (int it = 0; it < budget; it += 2) {
+        launches += 2 * (1 + vc_launches);
+        MSMG_CUDA_TRY(cudaGraphLaunch(c->iter_graph, s));
+        if ((it & 7) == 6 || it + 2 >= budget) {
+          MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+          MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+          if (hsc.done) break;
+        }
+      }
+    } else {
+      for (int it = 0; it < budget; ++it) {
+        launches += 1 + vc_launches;
+        pcg_step_pmatvec(c, sc, s);
+        double* t = B.pcur; B.pcur = B.pnext; B.pnext = t;
+        pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, sc, s);
+        if ((it & 3) == 3 || it + 1 == budget) {
+          MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+          MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+          if (hsc.done) break;
+        }
       }
     }
-  } else {
-    for (int it = 0; it < max_iter; ++it) {
-      launches += 1 + vc_launches;
-      pcg_step_pmatvec(c, sc, s);
-      double* t = B.pcur; B.pcur = B.pnext; B.pnext = t;
-      pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, sc, s);
-      if ((it & 3) == 3 || it + 1 == max_iter) {
-        MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-        MSMG_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hsc.done) break;
-      }
-    }
-  }
-  MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-  MSMG_CUDA_TRY(cudaStreamSynchronize(s));
-  // zero-mean solution, true residual
+    MSMG_CUDA_TRY(cudaMemcpyAsync(&hsc, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+  };
+  int st = iterate(max_iter);
+  if (st) return st;
+  // The recurrence residual can drift from b - A x (FP32 V-cycle, flexible beta):
+  // check the true residual in FP64 and, if it is above the tolerance, replace the
+  // residual by it and continue (at most twice).
   double* scal = c->dtmp + 8;
+  double hres[2] = {0.0, 0.0};
+  for (int restart = 0;; ++restart) {
+    launch_matvec(c, B.x, B.q, s);
+    k_resid_norm<<<vg, kVecThreads, 0, s>>>(B.b, B.q, n, c->red, scal + 1);
+    MSMG_CUDA_TRY(cudaMemcpyAsync(hres, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+    launches += 2;
+    if (hsc.done != 1 || hres[1] <= hsc.tol2 || restart == 2 || hsc.iter >= max_iter) break;
+    k_restart<<<vg, kVecThreads, 0, s>>>(B.b, B.q, B.r, n, c->red, sc);
+    MSMG_CUDA_TRY(cudaMemsetAsync(B.p0, 0, n * sizeof(double), s));
+    B.pcur = B.p0;
+    B.pnext = B.p1;
+    pcg_step_vcycle(c, 0, nullptr, sc, s);
+    launches += 1 + vc_launches;
+    st = iterate(max_iter - hsc.iter);
+    if (st) return st;
+  }
+  // zero-mean solution (uniqueness condition, Section 2.1)
   k_sum<<<vg, kVecThreads, 0, s>>>(B.x, n, c->red, scal, 1.0);
   k_sub_scalar<<<vg, kVecThreads, 0, s>>>(B.x, n, scal, 1.0 / (double)n);
-  launch_matvec(c, B.x, B.q, s);
-  k_resid_norm<<<vg, kVecThreads, 0, s>>>(B.b, B.q, n, c->red, scal + 1);
-  double hres[2];
-  MSMG_CUDA_TRY(cudaMemcpyAsync(hres, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  launches += 2;
   MSMG_CUDA_TRY(cudaStreamSynchronize(s));
   if (info) {
     info->iterations = hsc.iter;
@@ -251,7 +291,7 @@ static int pcg_one(msmg_ctx* c, double rtol, int max_iter, bool use_x0, int flag
     info->rel_residual = hsc.bb > 0 ? std::sqrt(hsc.rr / hsc.bb) : 0.0;
     info->true_rel_residual = hsc.bb > 0 ? std::sqrt(hres[1] / hsc.bb) : 0.0;
     info->rhs_mean = hsc.mean;
-    info->kernel_launches = launches + 4;
+    info->kernel_launches = launches;
   }
   if (hsc.done == 2) return MSMG_ERR_BREAKDOWN;
   if (hsc.done != 1) return MSMG_NOT_CONVERGED;
