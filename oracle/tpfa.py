@@ -65,6 +65,26 @@ def interior_face_mask(shape, box) -> np.ndarray:
     return m
 
 
+def apply_A(T: np.ndarray, p: np.ndarray) -> np.ndarray:
+    """q = A p without forming A (Eq. (discrete varia) read face by face): the
+    flux T_e (p_i - p_j) across every internal face e between cells i and j
+    (j the +d neighbour of i) is added to q_i and subtracted from q_j.
+    T as returned by face_transmissibilities, p of shape (nz, ny, nx) or flat."""
+    _, nz, ny, nx = T.shape
+    pp = np.asarray(p, dtype=np.float64).reshape(nz, ny, nx)
+    q = np.zeros_like(pp)
+    fx = T[0][:, :, :-1] * (pp[:, :, :-1] - pp[:, :, 1:])
+    q[:, :, :-1] += fx
+    q[:, :, 1:] -= fx
+    fy = T[1][:, :-1, :] * (pp[:, :-1, :] - pp[:, 1:, :])
+    q[:, :-1, :] += fy
+    q[:, 1:, :] -= fy
+    fz = T[2][:-1, :, :] * (pp[:-1, :, :] - pp[1:, :, :])
+    q[:-1, :, :] += fz
+    q[1:, :, :] -= fz
+    return q.reshape(np.shape(p))
+
+
 def assemble(T: np.ndarray) -> sp.csr_matrix:
     """The symmetric positive semidefinite matrix of Eq. (discrete varia):
     q^T A p = sum over faces e of T_e (p_j - p_i)(q_j - q_i).  Each face with

@@ -101,3 +101,27 @@ def test_face_coefficient_bounds():
     lo = np.minimum(kt[:, :, :-1], kt[:, :, 1:])
     assert np.all(T[0][:, :, :-1] <= 2 * lo * (1 + 1e-15))
     assert np.all(T[0][:, :, :-1] >= lo * (1 - 1e-15))
+
+
+@pytest.mark.parametrize("shape", [(4, 5, 6), (2, 7, 1)])
+def test_matrix_free_apply_closed_form_and_assembled(shape):
+    # the matrix-free form reproduces the closed-form DCT eigenpairs of the homogeneous
+    # operator and the assembled matrix on a heterogeneous orthotropic field
+    nz, ny, nx = shape
+    h = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    T1 = oracle.face_transmissibilities(np.ones(shape), h)
+    iz, iy, ix = np.arange(nz)[:, None, None], np.arange(ny)[None, :, None], np.arange(nx)[None, None, :]
+    for kx, ky, kz in [(1, 0, 0), (0, min(2, ny - 1), 0), (nx - 1, ny - 1, nz - 1)]:
+        v = (np.cos(np.pi * kx * (ix + 0.5) / nx) * np.cos(np.pi * ky * (iy + 0.5) / ny)
+             * np.cos(np.pi * kz * (iz + 0.5) / nz))
+        lam = (nx ** 2 * 2 * (1 - np.cos(np.pi * kx / nx)) + ny ** 2 * 2 * (1 - np.cos(np.pi * ky / ny))
+               + nz ** 2 * 2 * (1 - np.cos(np.pi * kz / nz)))
+        np.testing.assert_allclose(oracle.apply_A(T1, v), lam * v, atol=1e-10 * max(lam, 1.0))
+    rng = np.random.default_rng(11)
+    kap = np.exp(rng.normal(0, 3, size=(3,) + shape))
+    T = oracle.face_transmissibilities(kap, (0.3, 0.2, 0.7))
+    p = rng.standard_normal(shape)
+    q = oracle.apply_A(T, p)
+    ref = oracle.assemble(T) @ p.ravel()
+    np.testing.assert_allclose(q.ravel(), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    assert abs(q.sum()) < 1e-12 * np.abs(q).max()          # A 1 = 0 implies 1^T A p = 0
