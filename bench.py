@@ -11,6 +11,15 @@ seeded; they are resident in HBM when the timed region starts, and L2 is
 flushed (256 MiB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batched [--steps K] [--warmup W]
+
+The default line also carries ``batched_rhs``: the same workload with 16
+zero-mean random right-hand sides solved in one call (one launch sequence for
+all 16, rhs-minor CTA order).  ``--workload batched`` measures the batched
+workload instead: 8 lognormal realisations (sigma_logk 2 + 2i/7, correlation
+length 0.1) on 64^3, 64^3, 96^3, 96^3, 128^3, 128^3, 192^3, 192^3 grids with
+16 random zero-mean right-hand sides each, all solved by one
+msmg_solve_batched call (one stream per problem, CUDA graphs).
 
 With N > 1 (torchrun) every rank solves its own replica of the workload (the
 problem does not shard across the one-GPU machines of this pool): weak scaling,
@@ -43,6 +52,12 @@ N_LEVELS = 4
 N_EIG = [6, 6, 6]
 RATIO = [(2, 2, 2), (2, 2, 2)]
 RTOL = 1e-8
+BATCH_RHS = 16
+C3_GRIDS = [64, 64, 96, 96, 128, 128, 192, 192]   # fields.LOGNORMAL_BATCH_GRIDS
+C3_WORKLOAD = ("8 lognormal realisations (sigma_logk = 2 + 2i/7, i = 0..7, exponential covariance, correlation "
+               "length 0.1, seeds 10..17) on 64^3, 64^3, 96^3, 96^3, 128^3, 128^3, 192^3, 192^3 unit-cube grids, "
+               "16 iid N(0,1) zero-mean right-hand sides each; 8^3 elements, 4 levels (ratio 2), 4 eigenvectors "
+               "per local problem; one msmg_solve_batched call; PCG rtol 1e-8")
 
 
 def field():
@@ -56,18 +71,21 @@ def rhs(shape):
 
 
 # Algorithmic bytes per fine cell and launch of each fine-level kernel of one PCG
-# iteration (halos excluded), by form; L = eigenvectors per element.
-#   pre:      x, r read+write, p, q read (FP64); r copy and u written (V); T (3), 1/d read (V)
-#   restrict: r copy, u, T (3) read (V); basis (L values)
-#   prolong:  u read+write (V); basis (L values)
-#   post:     r copy, u, T (3), 1/d read (V); r read (FP64); q read (FP64, flexible beta only); z write (V)
-#   pmatvec:  z read (V); p_old read, p_new write, q write, T (3) read (FP64)
-def kernel_bytes(form: str, L: int) -> dict:
+# iteration (halos excluded), by form; L = eigenvectors per element, v = bytes of
+# a V-cycle value (4 mixed, 8 FP64).
+#   pre:      x, r read+write, p, q read (FP64); r copy and u written (v); T (3), 1/d read (v)
+#   restrict: r copy, u (v); T (3) (v); basis (L values, v)
+#   prolong:  u read+write (v); basis (L values, v)
+#   post:     r copy, u (v); T (3), 1/d (v); r read (FP64); q read (FP64, flexible beta
+#             only); z written (FP64)
+#   pmatvec:  z, p_old read, p_new, q written (FP64); T (3) and the diagonal D (FP64)
+# With R right-hand sides in one launch the coefficients (T, 1/d, D, basis) are read
+# once for all R: bytes per cell and right-hand side.
+def kernel_bytes(form: str, L: int, R: int = 1) -> dict:
     v = 4 if form == "mixed" else 8
-    b = 4 if form == "mixed" else 8
     flex = 8 if form == "mixed" else 0
-    return {"pre": 48 + 2 * v + 4 * v, "restrict": 2 * v + 3 * v + L * b, "prolong": 2 * v + L * b,
-            "post": 5 * v + 8 + flex + v, "pmatvec": v + 24 + 24}
+    return {"pre": 48 + 2 * v + 4 * v / R, "restrict": 2 * v + (3 * v + L * v) / R, "prolong": 2 * v + L * v / R,
+            "post": 2 * v + 4 * v / R + 8 + flex + 8, "pmatvec": 32 + 32 / R}
 
 
 def load_peaks():
@@ -225,6 +243,41 @@ def run_reference(args, world, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
+def batched_rhs(pkg, S, shape, n, args, world, flush, stream):
+    """The same workload with BATCH_RHS zero-mean random right-hand sides in one
+    msmg_solve call (mixed form)."""
+    import torch
+    import fields
+    F = torch.tensor(fields.rhs_random(shape, BATCH_RHS, seed=2024), device=stream.device)
+    X = torch.zeros_like(F)
+    for _ in range(max(1, args.warmup)):
+        pkg.msmg_solve(S.ctx, F, X, RTOL, 1000, 0)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = []
+    infos = None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, infos = pkg.msmg_solve(S.ctx, F, X, RTOL, 1000, 0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    step = max_over_ranks(world, float(np.mean(ms)))
+    its = [i["iterations"] for i in infos]
+    kt = S.time_kernels(reps=5, n_rhs=BATCH_RHS)
+    kb = kernel_bytes("mixed", N_EIG[0], BATCH_RHS)
+    vc = sum(kb[k] for k in ("pre", "restrict", "prolong", "post")) * n * BATCH_RHS
+    peak, _ = load_peaks()
+    return {"n_rhs": BATCH_RHS, "value": world * n * BATCH_RHS / (step * 1e-3), "unit": "DOF/s",
+            "ms_per_step": step, "iterations_min": min(its), "iterations_max": max(its),
+            "true_rel_residual_max": max(i["true_rel_residual"] for i in infos),
+            "converged": all(i["converged"] for i in infos), "kernel_ms": kt,
+            "vcycle_hbm_frac": vc / (kt["vcycle"] * 1e-3) / 1e9 / peak,
+            "gpu_launches": int(infos[0]["kernel_launches"])}
+
+
 def run_gpu(args, world, rank, local):
     import torch
     import paper_2403_19342_gb300 as pkg
@@ -246,9 +299,10 @@ def run_gpu(args, world, rank, local):
     kernel_times = {}
     sampler = ClockSampler(local)
     launches = 0
+    batched = None
     for form, prec in (("fp64", pkg.FP64), ("mixed", pkg.MIXED)):
         opts = pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec, eig_tol=1e-8)
-        S = pkg.Solver(kappa, opts)
+        S = pkg.Solver(kappa, opts, n_rhs=BATCH_RHS if form == "mixed" else 1)
         info0 = S.info
         for _ in range(args.warmup):
             pkg.msmg_solve(S.ctx, f_dev, x_dev, RTOL, 1000, 0)
@@ -298,6 +352,7 @@ def run_gpu(args, world, rank, local):
             e2e_step = max_over_ranks(world, float(np.mean(e2e_ms)))
             e2e = {"value": world * n / (e2e_step * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": 8 * n,
                    "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_step}
+            batched = batched_rhs(pkg, S, shape, n, args, world, flush, stream)
         S.close()
         del S
     # roofline of the dominant fine-level kernel of the mixed V-cycle
@@ -326,6 +381,7 @@ def run_gpu(args, world, rank, local):
             "forms": forms,
             "vcycle_hbm_frac": {"mixed": vc_frac, "fp64": vc64, "peak_gbs": peak},
             "kernel_ms": kernel_times,
+            "batched_rhs": batched,
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -333,6 +389,88 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rec = oracle_sample(1)
         line["cpu_baseline"] = {k: rec[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args, world, rank, local):
+    """The batched workload: 8 problems of uneven size, 16 right-hand sides each,
+    one msmg_solve_batched call per step (mixed form)."""
+    import torch
+    import fields
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    _build.build()
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    solvers, F, X, Fh, Xh = [], [], [], [], []
+    setup_ms, eig_ms, total = [], [], 0
+    for N, (kappa, f) in zip(C3_GRIDS, fields.lognormal_batch(BATCH_RHS, C3_GRIDS, device="cuda")):
+        opts = pkg.Options(n_levels=4, block=(8, 8, 8), ratio=[(2, 2, 2), (2, 2, 2)], n_eig=[4, 4, 4],
+                           precision=pkg.MIXED, eig_tol=1e-8)
+        S = pkg.Solver(torch.tensor(kappa, device=dev), opts, n_rhs=BATCH_RHS)
+        solvers.append(S)
+        setup_ms.append(S.info["setup_ms"])
+        eig_ms.append(S.info["eig_ms"])
+        F.append(torch.tensor(f, device=dev))
+        X.append(torch.zeros_like(F[-1]))
+        Fh.append(torch.tensor(f).pin_memory())
+        Xh.append(torch.zeros_like(Fh[-1]).pin_memory())
+        total += N ** 3 * BATCH_RHS
+    ctxs = [S.ctx for S in solvers]
+    for _ in range(args.warmup):
+        pkg.msmg_solve_batched(ctxs, F, X, RTOL, 2000, 0)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, infos = [], None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, infos = pkg.msmg_solve_batched(ctxs, F, X, RTOL, 2000, 0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
+    step = max_over_ranks(world, float(np.mean(ms)))
+    # end to end with host buffers (copies inside the call)
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pkg.msmg_solve_batched(ctxs, Fh, Xh, RTOL, 2000, pkg.FLAG_HOST_IO)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_step = max_over_ranks(world, float(np.mean(e2e_ms)))
+    per = []
+    for N, inf in zip(C3_GRIDS, infos):
+        its = [i["iterations"] for i in inf]
+        per.append({"grid": N, "iterations_min": min(its), "iterations_max": max(its),
+                    "true_rel_residual_max": max(i["true_rel_residual"] for i in inf),
+                    "converged": all(i["converged"] for i in inf)})
+    launches = int(sum(inf[0]["kernel_launches"] * ((BATCH_RHS + solvers[j].max_batch_rhs - 1)
+                                                   // solvers[j].max_batch_rhs)
+                       for j, inf in enumerate(infos)))
+    line = {"metric": METRIC, "value": world * total / (step * 1e-3), "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": C3_WORKLOAD, "form": "mixed", "n_rhs_per_problem": BATCH_RHS,
+                       "l2": "flushed before each step (256 MiB write); working set > L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "problems": per, "setup_ms": setup_ms, "eig_ms": eig_ms,
+            "e2e": {"value": world * total / (e2e_step * 1e-3), "unit": "DOF/s",
+                    "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "ms_per_step": e2e_step},
+            "gpu_launches": launches, "clocks": clocks}
+    for S in solvers:
+        S.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -369,6 +507,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="short run for ncu (no timing output)")
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--max-iter", type=int, default=4)
+    ap.add_argument("--workload", default="inclusions", choices=["inclusions", "batched"])
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
@@ -376,7 +515,7 @@ def main():
                                                                    int(os.environ.get("RANK", "0")), 0)
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    rc = run_gpu(args, world, rank, local)
+    rc = (run_batched if args.workload == "batched" else run_gpu)(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -191,3 +191,21 @@ def rhs_random(shape, n_rhs: int, seed: int) -> np.ndarray:
     f = rng.standard_normal((n_rhs,) + tuple(shape))
     f -= f.reshape(n_rhs, -1).mean(axis=1).reshape((n_rhs, 1, 1, 1))
     return f
+
+
+# ------------------------------------------------------------------ batched workload
+LOGNORMAL_BATCH_GRIDS = (64, 64, 96, 96, 128, 128, 192, 192)
+
+
+def lognormal_batch(n_rhs: int = 16, grids=LOGNORMAL_BATCH_GRIDS, device: str = "cpu"):
+    """Inputs of the batched workload, one problem at a time: problem i is a
+    grids[i]^3 unit-cube grid with kappa = exp(sigma_i Y), Y the exponential-
+    covariance Gaussian field (correlation length 0.1, seed 10 + i) and
+    sigma_i = 2 + 2 i / (len(grids) - 1), and ``n_rhs`` iid N(0, 1) zero-mean
+    right-hand sides (seed 100 + i).  Yields (kappa, rhs) with rhs of shape
+    (n_rhs, N, N, N)."""
+    k = len(grids)
+    for i, N in enumerate(grids):
+        sigma = 2.0 + 2.0 * i / max(1, k - 1)
+        kappa = grf_lognormal((N, N, N), seed=10 + i, contrast=None, sigma=sigma, device=device)
+        yield kappa, rhs_random((N, N, N), n_rhs, seed=100 + i)

@@ -71,6 +71,9 @@ typedef struct msmg_ctx msmg_ctx;                /* opaque, owned by the library
                                 /* the copies run on the stream inside the call       */
 #define MSMG_FLAG_NO_GRAPH  4   /* launch the PCG iteration kernel by kernel           */
 
+/* Largest batch width: right-hand sides one context solves in lockstep. */
+#define MSMG_MAX_BATCH_RHS 64
+
 typedef struct {
     int nx, ny, nz;        /* fine cells per direction                     */
     double hx, hy, hz;     /* cell sizes (the paper's unit cube: 1/n)      */
@@ -111,8 +114,10 @@ typedef struct {
 } msmg_solve_info;
 
 /*
- * Workspace bytes needed by msmg_setup for this grid and hierarchy, and for
- * solves of up to n_rhs right-hand sides per call.  Returns
+ * Workspace bytes needed by msmg_setup for this grid and hierarchy with room for
+ * n_rhs right-hand sides solved in lockstep (the batch width; every solve vector
+ * is held n_rhs times, so the size grows linearly with it).  msmg_setup takes the
+ * largest batch width, up to MSMG_MAX_BATCH_RHS, that its workspace holds.  Returns
  * MSMG_ERR_NOT_DIVISIBLE / MSMG_ERR_INVALID_ARG / MSMG_ERR_SINGLE_BLOCK for a
  * hierarchy that cannot be built (block must divide the grid, each ratio
  * must divide the element grid below it, every level below the coarsest must
@@ -147,16 +152,37 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
  * PCG solve of A x = rhs (Eq. (p)) preconditioned by one V-cycle per iteration.
  *   rhs, x     n_rhs x (nx*ny*nz) FP64 values, natural order, one system after another;
  *              device pointers unless MSMG_FLAG_HOST_IO
+ *   n_rhs      any number >= 1: the systems are solved in batches of the context's batch
+ *              width (msmg_max_batch_rhs), each batch in lockstep (one set of launches,
+ *              separate scalars, convergence test and iteration count per system)
  *   rtol       stop when ||b - A x_k||_2 <= rtol ||b||_2 (b = rhs with its mean removed,
  *              the compatibility condition of Section 2.1)
  *   max_iter   iteration cap (MSMG_NOT_CONVERGED when reached)
- *   info       host struct, per system: n_rhs entries (may be NULL)
+ *   info       host array, one entry per system (may be NULL); solve_ms is the device
+ *              time of the system's batch, kernel_launches the batch's launches
  * x is returned with zero mean (Section 2.1).  In MSMG_MIXED the V-cycle runs in FP32
- * and the outer recurrence in FP64 with the flexible (Polak-Ribiere) beta.  Errors:
- * MSMG_ERR_BREAKDOWN, MSMG_ERR_INVALID_ARG (n_rhs above the workspace's).
+ * and the outer recurrence in FP64 with the flexible (Polak-Ribiere) beta.  Returns the
+ * worst status over the systems: MSMG_ERR_BREAKDOWN, MSMG_NOT_CONVERGED, or MSMG_OK.
+ * Blocks the calling thread until the solution is in x.
  */
 int msmg_solve(msmg_ctx* ctx, const double* rhs, double* x, int n_rhs, double rtol, int max_iter,
                int flags, msmg_stream stream, msmg_solve_info* info);
+
+/*
+ * Solves on several contexts at once (independent problems: different grids, fields or
+ * hierarchies).  Context k solves n_rhs[k] systems rhs[k] -> x[k] exactly as msmg_solve
+ * would; the contexts run on streams of their own, forked from and joined back into
+ * stream, and the host advances whichever context's work has completed, so the launches
+ * of small problems overlap.  A context may appear once.  info (may be NULL) has
+ * sum(n_rhs) entries, context after context.  No counterpart in the paper: its
+ * experiments solve one system at a time.
+ */
+int msmg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs, double* const* x,
+                       const int* n_rhs, double rtol, int max_iter, int flags, msmg_stream stream,
+                       msmg_solve_info* info);
+
+/* The context's batch width: right-hand sides one msmg_solve launch sequence carries. */
+int msmg_max_batch_rhs(const msmg_ctx* ctx);
 
 /* q = A p, FP64, natural order (Eq. (discrete varia)). */
 int msmg_apply_A(msmg_ctx* ctx, const double* p, double* q, msmg_stream stream);
@@ -230,14 +256,15 @@ const char* msmg_status_string(int status);
 /*
  * Average device time (ms) per launch of the fine-level kernels of one PCG iteration,
  * measured with CUDA events around each launch on the given stream over reps repetitions on
- * the context's own buffers (fixed synthetic data).  ms_out[0 .. n_out) receives:
+ * the context's own buffers (fixed synthetic data), at batch width n_rhs (1 .. the
+ * context's).  ms_out[0 .. n_out) receives:
  *   [0] PCG update of x and r fused with the pre-smoothing   [1] residual + restriction
  *   [2] prolongation   [3] residual + post-smoothing (with the r.z reduction)
  *   [4] all coarse levels (levels >= 2)   [5] search-direction update fused with q = A p
  *   [6] [0]..[3] and [4] together (one preconditioner application)
  * Used for roofline figures; no effect on results.
  */
-int msmg_time_kernels(msmg_ctx* ctx, int reps, double* ms_out, int n_out, msmg_stream stream);
+int msmg_time_kernels(msmg_ctx* ctx, int n_rhs, int reps, double* ms_out, int n_out, msmg_stream stream);
 
 /* Measured plain-ALU FMA throughput of this GPU (TFLOP/s), for roofline denominators of
  * ALU-bound kernels: a short in-register FMA loop timed with CUDA events. */

@@ -91,7 +91,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_destroy": (None, [P]),
         "msmg_status_string": (C.c_char_p, [I]),
         "msmg_probe_alu_peaks": (I, [C.POINTER(D), C.POINTER(D), P]),
-        "msmg_time_kernels": (I, [P, I, C.POINTER(D), I, P]),
+        "msmg_time_kernels": (I, [P, I, I, C.POINTER(D), I, P]),
+        "msmg_solve_batched": (I, [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), C.POINTER(I), D, I, I, P,
+                                   C.POINTER(msmg_solve_info)]),
+        "msmg_max_batch_rhs": (I, [P]),
         "msmg_dot_noalloc": (I, [P, P, I64, C.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -107,7 +110,8 @@ def exported_symbols():
     return ["msmg_workspace_size", "msmg_setup", "msmg_solve", "msmg_apply_A", "msmg_apply_precond",
             "msmg_dot_scratch_bytes", "msmg_dot", "msmg_export_basis", "msmg_import_bases",
             "msmg_export_operator", "msmg_export_faces", "msmg_get_setup_info", "msmg_destroy",
-            "msmg_status_string", "msmg_probe_alu_peaks", "msmg_time_kernels", "msmg_dot_noalloc"]
+            "msmg_status_string", "msmg_probe_alu_peaks", "msmg_time_kernels", "msmg_dot_noalloc",
+            "msmg_solve_batched", "msmg_max_batch_rhs"]
 
 
 def _check(status: int) -> int:
@@ -204,10 +208,39 @@ def msmg_solve(ctx: int, rhs: torch.Tensor, x: torch.Tensor, rtol: float, max_it
     st = load_library().msmg_solve(ctx, _ptr(rhs, torch.float64, cuda=not host), _ptr(x, torch.float64, cuda=not host),
                                    n_rhs, rtol, max_iter, flags, _stream(stream), infos)
     _check(st)
-    return st, [dict(iterations=i.iterations, converged=bool(i.converged), rel_residual=i.rel_residual,
-                     true_rel_residual=i.true_rel_residual, rhs_mean=i.rhs_mean, solve_ms=i.solve_ms,
-                     kernel_launches=i.kernel_launches)
-                for i in infos]
+    return st, [_info_dict(i) for i in infos]
+
+
+def _info_dict(i) -> dict:
+    return dict(iterations=i.iterations, converged=bool(i.converged), rel_residual=i.rel_residual,
+                true_rel_residual=i.true_rel_residual, rhs_mean=i.rhs_mean, solve_ms=i.solve_ms,
+                kernel_launches=i.kernel_launches)
+
+
+def msmg_solve_batched(ctxs: list, rhs: list, x: list, rtol: float, max_iter: int, flags: int = 0,
+                       stream=None) -> tuple[int, list]:
+    """Solve on several contexts at once; rhs[k] / x[k] hold context k's systems
+    ([n_rhs, nz, ny, nx] or [nz, ny, nx]).  Returns the worst status and one list of
+    info dicts per context."""
+    host = bool(flags & FLAG_HOST_IO)
+    k = len(ctxs)
+    counts = [(r.shape[0] if r.dim() == 4 else 1) for r in rhs]
+    infos = (msmg_solve_info * max(1, sum(counts)))()
+    ca = (C.c_void_p * k)(*ctxs)
+    ra = (C.c_void_p * k)(*[_ptr(r, torch.float64, cuda=not host) for r in rhs])
+    xa = (C.c_void_p * k)(*[_ptr(v, torch.float64, cuda=not host) for v in x])
+    na = (C.c_int * k)(*counts)
+    st = load_library().msmg_solve_batched(ca, k, ra, xa, na, rtol, max_iter, flags, _stream(stream), infos)
+    _check(st)
+    out, o = [], 0
+    for cnt in counts:
+        out.append([_info_dict(infos[o + j]) for j in range(cnt)])
+        o += cnt
+    return st, out
+
+
+def msmg_max_batch_rhs(ctx: int) -> int:
+    return load_library().msmg_max_batch_rhs(ctx)
 
 
 def msmg_apply_A(ctx: int, p: torch.Tensor, q: torch.Tensor, stream=None) -> None:
@@ -274,9 +307,9 @@ def msmg_destroy(ctx: int) -> None:
     load_library().msmg_destroy(ctx)
 
 
-def msmg_time_kernels(ctx: int, reps: int = 20, stream=None) -> list:
+def msmg_time_kernels(ctx: int, reps: int = 20, stream=None, n_rhs: int = 1) -> list:
     out = (C.c_double * 7)()
-    _check(load_library().msmg_time_kernels(ctx, reps, out, 7, _stream(stream)))
+    _check(load_library().msmg_time_kernels(ctx, n_rhs, reps, out, 7, _stream(stream)))
     return list(out)
 
 
@@ -371,8 +404,12 @@ class Solver:
         msmg_export_operator(self.ctx, level, out, self.stream)
         return out
 
-    def time_kernels(self, reps: int = 20) -> dict:
-        v = msmg_time_kernels(self.ctx, reps, self.stream)
+    @property
+    def max_batch_rhs(self) -> int:
+        return msmg_max_batch_rhs(self.ctx)
+
+    def time_kernels(self, reps: int = 20, n_rhs: int = 1) -> dict:
+        v = msmg_time_kernels(self.ctx, reps, self.stream, n_rhs)
         keys = ["pre", "restrict", "prolong", "post", "coarse_levels", "pmatvec", "vcycle"]
         return dict(zip(keys, v))
 

@@ -11,12 +11,14 @@ namespace msmg {
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
-void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s);
 void launch_mixed_copies(msmg_ctx* c, cudaStream_t s);
 void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s);
 int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s);
 int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
-int time_kernels(msmg_ctx* c, int reps, double* acc, cudaStream_t s);
+int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s);
+int pcg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs, double* const* x,
+                      const int* n_rhs, double rtol, int max_iter, int flags, cudaStream_t s,
+                      msmg_solve_info* info);
 void apply_vcycle_fp64_out(msmg_ctx* c, cudaStream_t s);
 void prepare_fine_kernels(msmg_ctx* c);
 void prepare_coarse_kernels(msmg_ctx* c);
@@ -118,12 +120,14 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   // common
   c->flags = ar.take<int>(16);
   c->dtmp = ar.take<double>(16 + nc * nc + 3 * nc + 64);
-  // every reducing kernel launches at most one CTA per element, or 1216 CTAs for
-  // the grid-stride vector kernels
+  // every reducing kernel launches at most one CTA per element and right-hand
+  // side, or 1216 CTAs per right-hand side for the grid-stride vector kernels
   int64_t maxgrid = f.m;
   if (maxgrid < 152 * 8) maxgrid = 152 * 8;
-  c->red.partials = ar.take<double>((size_t)maxgrid * kRedWidth);
-  c->red.counter = ar.take<unsigned>(4);
+  const int R = c->max_rhs;
+  c->red.stride = maxgrid * kRedWidth;
+  c->red.partials = ar.take<double>((size_t)c->red.stride * R);
+  c->red.counter = ar.take<unsigned>(R);
   // fine level
   f.lex_of_hid = ar.take<int>(f.m);
   f.nbr = ar.take<int>(f.m * 6);
@@ -156,24 +160,29 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
     }
   }
   // solve buffers
+  // solve buffers: R copies of every vector, right-hand side r at offset r * n
   SolveBuffers& B = c->sb;
-  B.b = ar.take<double>(n);
-  B.x = ar.take<double>(n);
-  B.r = ar.take<double>(n);
-  B.z = ar.take<double>(n);
-  B.p0 = ar.take<double>(n);
-  B.p1 = ar.take<double>(n);
-  B.q = ar.take<double>(n);
-  B.vu[1] = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
-  B.rv = mixed ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n);
+  const int64_t nR = n * R;
+  B.b = ar.take<double>(nR);
+  B.x = ar.take<double>(nR);
+  B.r = ar.take<double>(nR);
+  B.z = ar.take<double>(nR);
+  B.p0 = ar.take<double>(nR);
+  B.p1 = ar.take<double>(nR);
+  B.q = ar.take<double>(nR);
+  B.vu[1] = mixed ? (void*)ar.take<float>(nR) : (void*)ar.take<double>(nR);
+  B.rv = mixed ? (void*)ar.take<float>(nR) : (void*)ar.take<double>(nR);
   for (int l = 2; l <= nL; ++l) {
-    B.vf[l] = ar.take<double>(c->lev[l].n);
-    B.vu[l] = ar.take<double>(c->lev[l].n);
-    B.vw[l] = ar.take<double>(c->lev[l].n);
+    B.vf[l] = ar.take<double>(c->lev[l].n * R);
+    B.vu[l] = ar.take<double>(c->lev[l].n * R);
+    B.vw[l] = ar.take<double>(c->lev[l].n * R);
   }
-  B.ec32 = mixed ? ar.take<float>(c->lev[2].n) : nullptr;
-  B.sc = ar.take<PcgScalars>(c->max_rhs);
-  B.n_rhs = c->max_rhs;
+  B.ec32 = mixed ? ar.take<float>(c->lev[2].n * R) : nullptr;
+  B.sc = ar.take<PcgScalars>(R);
+  B.dres = ar.take<double>(2 * R);
+  B.dmask = ar.take<int>(R);
+  B.n_rhs = R;
+  B.R = 1;
   return 0;
 }
 
@@ -286,19 +295,35 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   Arena ar;
   ar.base = static_cast<char*>(workspace);
   ar.cap = workspace_bytes;
-  // the largest n_rhs that fits
+  // the largest batch width that fits (the workspace grows linearly with it)
   int n_rhs = 1;
-  for (int k = 2; k <= 4096; k *= 2) {
-    size_t b = 0;
-    msmg_workspace_size(grid, opts, k, &b);
-    if (b <= workspace_bytes) n_rhs = k; else break;
+  {
+    size_t b1 = 0, b2 = 0;
+    msmg_workspace_size(grid, opts, 1, &b1);
+    msmg_workspace_size(grid, opts, 2, &b2);
+    const size_t per = b2 > b1 ? b2 - b1 : 1;
+    size_t k = 1 + (workspace_bytes - b1) / per;
+    if (k > MSMG_MAX_BATCH_RHS) k = MSMG_MAX_BATCH_RHS;
+    n_rhs = (int)k;
+    for (;;) {
+      size_t b = 0;
+      msmg_workspace_size(grid, opts, n_rhs, &b);
+      if (b <= workspace_bytes || n_rhs == 1) break;
+      --n_rhs;
+    }
   }
   plan_and_carve(grid, opts, n_rhs, ar, c);
   c->ws_bytes = workspace_bytes;
   cudaGetDevice(&c->device);
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
+  for (int k = 0; k < 3; ++k) cudaEventCreateWithFlags(&c->poll_evs[k], cudaEventDisableTiming);
   *out = c;
+  // pinned host mirrors of the PCG scalars (latest + two in-flight chunks),
+  // residual norms and restart mask
+  MSMG_CUDA_TRY(cudaMallocHost(&c->hsc, (size_t)3 * n_rhs * sizeof(PcgScalars)));
+  MSMG_CUDA_TRY(cudaMallocHost(&c->hres, (size_t)2 * n_rhs * sizeof(double)));
+  MSMG_CUDA_TRY(cudaMallocHost(&c->hmask, (size_t)n_rhs * sizeof(int)));
   cudaEventRecord(c->ev0, s);
   LevelShape sh;
   shapes(grid, opts, sh);
@@ -316,7 +341,7 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   MSMG_CUDA_TRY(cudaStreamSynchronize(s));   // host tables go out of scope
   MSMG_CUDA_TRY(cudaMemsetAsync(c->flags, 0, 16 * sizeof(int), s));
   MSMG_CUDA_TRY(cudaMemsetAsync(c->dtmp, 0, 16 * sizeof(double), s));
-  MSMG_CUDA_TRY(cudaMemsetAsync(c->red.counter, 0, 4 * sizeof(unsigned), s));
+  MSMG_CUDA_TRY(cudaMemsetAsync(c->red.counter, 0, (size_t)c->max_rhs * sizeof(unsigned), s));
   launch_faces(c, kappa, kappa_components, kappa_dtype, s);
   {
     // stop before any eigensolve when the permeability is not positive and finite
@@ -357,28 +382,42 @@ int msmg_solve(msmg_ctx* c, const double* rhs, double* x, int n_rhs, double rtol
                msmg_stream stream, msmg_solve_info* info) {
   if (!c || !rhs || !x || n_rhs < 1 || max_iter < 0 || !(rtol >= 0)) return MSMG_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int worst = 0;
-  for (int i = 0; i < n_rhs; ++i) {
-    cudaEventRecord(c->ev0, s);
-    msmg_solve_info loc{};
-    int st = pcg_solve(c, rhs + (int64_t)i * c->n, x + (int64_t)i * c->n, rtol, max_iter, flags, s, &loc);
-    cudaEventRecord(c->ev1, s);
-    cudaEventSynchronize(c->ev1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    loc.solve_ms = ms;
-    if (info) info[i] = loc;
-    if (st < 0) return st;
-    if (st > worst) worst = st;
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
-  return worst;
+  if (info)
+    for (int i = 0; i < n_rhs; ++i) info[i] = msmg_solve_info{};
+  const int st = pcg_solve(c, rhs, x, n_rhs, rtol, max_iter, flags, s, info);
+  if (st < 0) return st;
+  cudaError_t e = cudaGetLastError();   // a NotReady left by an event poll is not an error
+  if (e != cudaSuccess && e != cudaErrorNotReady) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
+  return st;
 }
+
+int msmg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs, double* const* x,
+                       const int* n_rhs, double rtol, int max_iter, int flags, msmg_stream stream,
+                       msmg_solve_info* info) {
+  if (!ctxs || n_ctx < 1 || !rhs || !x || !n_rhs || max_iter < 0 || !(rtol >= 0)) return MSMG_ERR_INVALID_ARG;
+  int64_t total = 0;
+  for (int k = 0; k < n_ctx; ++k) {
+    if (!ctxs[k] || !rhs[k] || !x[k] || n_rhs[k] < 0) return MSMG_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return MSMG_ERR_INVALID_ARG;   // one solve per context at a time
+    total += n_rhs[k];
+  }
+  if (info)
+    for (int64_t i = 0; i < total; ++i) info[i] = msmg_solve_info{};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int st = pcg_solve_batched(ctxs, n_ctx, rhs, x, n_rhs, rtol, max_iter, flags, s, info);
+  if (st < 0) return st;
+  cudaError_t e = cudaGetLastError();   // a NotReady left by an event poll is not an error
+  if (e != cudaSuccess && e != cudaErrorNotReady) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
+  return st;
+}
+
+int msmg_max_batch_rhs(const msmg_ctx* c) { return c ? c->max_rhs : 0; }
 
 int msmg_apply_A(msmg_ctx* c, const double* p, double* q, msmg_stream stream) {
   if (!c || !p || !q) return MSMG_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  c->sb.R = 1;
   launch_nat_to_blk(c, p, c->sb.p0, s);
   launch_matvec(c, c->sb.p0, c->sb.q, s);
   launch_blk_to_nat(c, c->sb.q, q, s);
@@ -389,6 +428,7 @@ int msmg_apply_A(msmg_ctx* c, const double* p, double* q, msmg_stream stream) {
 int msmg_apply_precond(msmg_ctx* c, const double* r, double* z, msmg_stream stream) {
   if (!c || !r || !z) return MSMG_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  c->sb.R = 1;
   launch_nat_to_blk(c, r, c->sb.r, s);
   apply_vcycle_fp64_out(c, s);
   launch_blk_to_nat(c, c->sb.z, z, s);
@@ -471,15 +511,21 @@ void msmg_destroy(msmg_ctx* c) {
   if (!c) return;
   if (c->graph_state == 1) cudaGraphExecDestroy(c->iter_graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->run_stream) cudaStreamDestroy(c->run_stream);
   cudaEventDestroy(c->ev0);
   cudaEventDestroy(c->ev1);
+  for (int k = 0; k < 3; ++k)
+    if (c->poll_evs[k]) cudaEventDestroy(c->poll_evs[k]);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->hres) cudaFreeHost(c->hres);
+  if (c->hmask) cudaFreeHost(c->hmask);
   delete c;
 }
 
-int msmg_time_kernels(msmg_ctx* c, int reps, double* ms_out, int n_out, msmg_stream stream) {
-  if (!c || !ms_out || reps < 1 || n_out < 1) return MSMG_ERR_INVALID_ARG;
+int msmg_time_kernels(msmg_ctx* c, int n_rhs, int reps, double* ms_out, int n_out, msmg_stream stream) {
+  if (!c || !ms_out || reps < 1 || n_out < 1 || n_rhs < 1 || n_rhs > c->max_rhs) return MSMG_ERR_INVALID_ARG;
   double acc[7];
-  int st = time_kernels(c, reps, acc, reinterpret_cast<cudaStream_t>(stream));
+  int st = time_kernels(c, n_rhs, reps, acc, reinterpret_cast<cudaStream_t>(stream));
   if (st) return st;
   for (int i = 0; i < n_out && i < 7; ++i) ms_out[i] = acc[i];
   return 0;

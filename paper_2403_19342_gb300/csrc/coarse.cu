@@ -11,9 +11,11 @@
 // smoother is block Jacobi over the parents (elements of E_l): one dense
 // nP x nP inverse per parent, nP = children * L, applied as a GEMV.
 //
-// One CTA per parent.  The parent's smoother inverse is staged in shared memory
-// with asynchronous copies (all in flight at once); the per-row stencil loops
-// are unrolled for the common block sizes L (template parameter, 0 = runtime).
+// One CTA per parent and right-hand side (R right-hand sides in lockstep,
+// level-l vectors stored n_l apart; CTA b handles parent b / R of right-hand
+// side b % R).  The parent's smoother inverse is staged in shared memory with
+// asynchronous copies (all in flight at once); the per-row stencil loops are
+// unrolled for the common block sizes L (template parameter, 0 = runtime).
 #include "msmg_internal.cuh"
 #include "reduce.cuh"
 #include <type_traits>
@@ -120,11 +122,15 @@ __device__ __forceinline__ S smem_gemv_col(const S* M, const S* x, int nP, int t
 // Pre-smoothing from zero on level l: u_P = Minv_P f_P.
 template <typename S>
 __global__ void k_coarse_smooth_first(CoarseLevel lv, LevelData<S> D, const S* __restrict__ f, S* __restrict__ u,
-                                      const PcgScalars* sc) {
+                                      const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
+  f += (int64_t)bi.r * lv.n;
+  u += (int64_t)bi.r * lv.n;
   extern __shared__ __align__(16) unsigned char smraw[];
   S* sm = reinterpret_cast<S*>(smraw);
-  const int64_t P = blockIdx.x;
+  const int64_t P = bi.blk;
   const int nP = lv.nP;
   S* Mi = sm;                      // [nP][nP]
   S* fs = sm + (size_t)nP * nP;
@@ -139,11 +145,16 @@ __global__ void k_coarse_smooth_first(CoarseLevel lv, LevelData<S> D, const S* _
 // Residual and restriction to level l+1: fn[P][j] = sum_i Psi[P][j][i] (f - A_l u)_i.
 template <int LT, typename S>
 __global__ void k_coarse_resid_restrict(CoarseLevel lv, LevelData<S> D, const S* __restrict__ f,
-                                        const S* __restrict__ u, S* __restrict__ fn, const PcgScalars* sc) {
+                                        const S* __restrict__ u, S* __restrict__ fn, const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
+  f += (int64_t)bi.r * lv.n;
+  u += (int64_t)bi.r * lv.n;
+  fn += (int64_t)bi.r * lv.mP * lv.Lnext;
   extern __shared__ __align__(16) unsigned char smraw[];
   S* sm = reinterpret_cast<S*>(smraw);
-  const int64_t P = blockIdx.x;
+  const int64_t P = bi.blk;
   const int nP = lv.nP, Ln = lv.Lnext;
   const int nw = (blockDim.x + 31) >> 5;
   S* ps = sm;                            // [Ln][nP]
@@ -170,9 +181,13 @@ __global__ void k_coarse_resid_restrict(CoarseLevel lv, LevelData<S> D, const S*
 // Prolongation: u_P += Psi_P^T e_P.
 template <typename S>
 __global__ void k_coarse_prolong(CoarseLevel lv, LevelData<S> D, S* __restrict__ u, const S* __restrict__ e,
-                                 const PcgScalars* sc) {
+                                 const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
-  const int64_t P = blockIdx.x;
+  u += (int64_t)bi.r * lv.n;
+  e += (int64_t)bi.r * lv.mP * lv.Lnext;
+  const int64_t P = bi.blk;
   const int t = threadIdx.x;
   if (t >= lv.nP) return;
   const S* ps = D.Psi + (size_t)P * lv.Lnext * lv.nP;
@@ -186,11 +201,18 @@ __global__ void k_coarse_prolong(CoarseLevel lv, LevelData<S> D, S* __restrict__
 template <int LT, typename S>
 __global__ void k_coarse_resid_smooth(CoarseLevel lv, LevelData<S> D, const S* __restrict__ f,
                                       const S* __restrict__ u, S* __restrict__ out, float* __restrict__ out32,
-                                      const PcgScalars* sc) {
+                                      const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
+  {
+    const int64_t off = (int64_t)bi.r * lv.n;
+    f += off; u += off; out += off;
+    if (out32) out32 += off;
+  }
   extern __shared__ __align__(16) unsigned char smraw[];
   S* sm = reinterpret_cast<S*>(smraw);
-  const int64_t P = blockIdx.x;
+  const int64_t P = bi.blk;
   const int nP = lv.nP;
   S* Mi = sm;
   S* rs = sm + (size_t)nP * nP;
@@ -209,10 +231,15 @@ __global__ void k_coarse_resid_smooth(CoarseLevel lv, LevelData<S> D, const S* _
 // Coarsest level: u = A^dagger f, dense symmetric GEMV, one warp per row.
 template <typename S>
 __global__ void k_dense_gemv(const double* __restrict__ A, const S* __restrict__ x, S* __restrict__ y,
-                             float* __restrict__ y32, int64_t n, const PcgScalars* sc) {
+                             float* __restrict__ y32, int64_t n, const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
+  x += (int64_t)bi.r * n;
+  y += (int64_t)bi.r * n;
+  if (y32) y32 += (int64_t)bi.r * n;
   const int lane = threadIdx.x & 31;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t row = ((int64_t)bi.blk * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
   const double* a = A + row * n;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -286,24 +313,25 @@ static const S* coarse_cycle_t(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t 
   S* f = (S*)c->sb.vf[l];
   S* u = (S*)c->sb.vu[l];
   S* w = (S*)c->sb.vw[l];
+  const int R = c->sb.R;
   if (l == c->nL) {
-    const unsigned grid = (unsigned)((lv.n * 32 + 255) / 256);
-    k_dense_gemv<S><<<grid, 256, 0, s>>>(lv.pinv, f, u, l == 2 ? c->sb.ec32 : nullptr, lv.n, sc);
+    const unsigned grid = (unsigned)((lv.n * 32 + 255) / 256 * R);
+    k_dense_gemv<S><<<grid, 256, 0, s>>>(lv.pinv, f, u, l == 2 ? c->sb.ec32 : nullptr, lv.n, sc, R);
     return u;
   }
   const LevelData<S> D = level_data<S>(lv);
   S* fn = (S*)c->sb.vf[l + 1];
   const unsigned thr = coarse_threads(lv);
-  k_coarse_smooth_first<S><<<(unsigned)lv.mP, thr, smem_smooth<S>(lv), s>>>(lv, D, f, u, sc);
+  const unsigned grid = (unsigned)(lv.mP * R);
+  k_coarse_smooth_first<S><<<grid, thr, smem_smooth<S>(lv), s>>>(lv, D, f, u, sc, R);
   with_L(lv.L, [&](auto LC) {
-    k_coarse_resid_restrict<decltype(LC)::value, S><<<(unsigned)lv.mP, thr, smem_restrict<S>(lv), s>>>(lv, D, f, u,
-                                                                                                       fn, sc);
+    k_coarse_resid_restrict<decltype(LC)::value, S><<<grid, thr, smem_restrict<S>(lv), s>>>(lv, D, f, u, fn, sc, R);
   });
   const S* e = coarse_cycle_t<S>(c, l + 1, sc, s);
-  k_coarse_prolong<S><<<(unsigned)lv.mP, thr, 0, s>>>(lv, D, u, e, sc);
+  k_coarse_prolong<S><<<grid, thr, 0, s>>>(lv, D, u, e, sc, R);
   with_L(lv.L, [&](auto LC) {
-    k_coarse_resid_smooth<decltype(LC)::value, S><<<(unsigned)lv.mP, thr, smem_smooth<S>(lv), s>>>(
-        lv, D, f, u, w, l == 2 ? c->sb.ec32 : nullptr, sc);
+    k_coarse_resid_smooth<decltype(LC)::value, S><<<grid, thr, smem_smooth<S>(lv), s>>>(
+        lv, D, f, u, w, l == 2 ? c->sb.ec32 : nullptr, sc, R);
   });
   return w;
 }

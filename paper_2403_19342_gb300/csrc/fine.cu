@@ -40,11 +40,11 @@ struct Slot {
   bool valid;
 };
 
-__device__ __forceinline__ Slot make_slot(const Geo& g, int64_t m) {
+__device__ __forceinline__ Slot make_slot(const Geo& g, int64_t m, unsigned blk) {
   Slot s;
   s.eloc = threadIdx.x / g.nb;
   s.p = threadIdx.x % g.nb;
-  s.e = (int64_t)blockIdx.x * g.epc + s.eloc;
+  s.e = (int64_t)blk * g.epc + s.eloc;
   s.valid = (s.eloc < g.epc) && (s.e < m);
   s.lx = s.p % g.bx;
   int t = s.p / g.bx;
@@ -158,7 +158,7 @@ __global__ void k_faces(const KT* __restrict__ kappa, int comps, int nx, int ny,
 __global__ void k_pivots(const double* __restrict__ T, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
                          double* __restrict__ invd, double* __restrict__ D, int* flags) {
   extern __shared__ double smem[];
-  const Slot s = make_slot(g, m);
+  const Slot s = make_slot(g, m, blockIdx.x);
   double* t0 = smem + (size_t)s.eloc * (3 * g.P + g.nb);
   double* t1 = t0 + g.P;
   double* t2 = t1 + g.P;
@@ -213,13 +213,18 @@ __global__ void k_perm(const Tin* __restrict__ in, Tout* __restrict__ out, int64
 
 // ============================================================== stencil
 
-// q = A p (FP64).  With Reduce, also p.q and the PCG step length (finaliser).
+// q = A p (FP64) for R right-hand sides stored n apart.  With Reduce, also p.q
+// and the PCG step length (finaliser).
 template <bool Reduce>
 __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, const double* __restrict__ T, int64_t n,
-                         Geo g, int64_t m, const int* __restrict__ nbr, RedSlot red, PcgScalars* sc) {
+                         Geo g, int64_t m, const int* __restrict__ nbr, RedSlot red, PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (Reduce) sc += bi.r;
   if (Reduce && sc->done) return;
+  p += (int64_t)bi.r * n;
+  q += (int64_t)bi.r * n;
   extern __shared__ double smem[];
-  const Slot s = make_slot(g, m);
+  const Slot s = make_slot(g, m, bi.blk);
   double* pt = smem + (size_t)s.eloc * 4 * g.P;
   double* t0 = pt + g.P;
   double* t1 = t0 + g.P;
@@ -236,7 +241,7 @@ __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, c
     v[0] = a * pt[pad(g, s.lx, s.ly, s.lz)];
   }
   if (Reduce) {
-    grid_reduce<1>(v, red, [=] __device__(double* t) {
+    grid_reduce_r<1>(v, red, bi, [=] __device__(double* t) {
       sc->pq = t[0];
       if (!(t[0] > 0.0) || !isfinite(t[0])) { sc->done = 2; sc->alpha = 0.0; }
       else sc->alpha = sc->rz / t[0];
@@ -251,9 +256,13 @@ __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, c
 // pipe is not touched per cell in the mixed form.
 template <typename V, typename BT, typename EC>
 __global__ void k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L, const EC* __restrict__ ec, int64_t n,
-                          int nb, const PcgScalars* sc) {
+                          int64_t nc, int nb, const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  u += (int64_t)bi.r * n;
+  ec += (int64_t)bi.r * nc;
+  const int64_t i = (int64_t)bi.blk * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e = i / nb;
   const int p = (int)(i % nb);
@@ -310,20 +319,21 @@ void launch_faces_to_nat(msmg_ctx* c, double* out, cudaStream_t s) {
       c->fine.T, out, c->n, g, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->grid.nx, c->grid.ny, 3);
 }
 
-void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s) {
+void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s, int R) {
   const Geo g = fine_geo(c);
   const size_t sm = (size_t)g.epc * 4 * g.P * sizeof(double);
   cudaFuncSetAttribute(k_matvec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_matvec<false><<<fine_grid(c, g), fine_threads(g), sm, s>>>(p, q, c->fine.T, c->n, g, c->fine.m, c->fine.nbr,
-                                                                c->red, nullptr);
+  k_matvec<false><<<fine_grid(c, g) * R, fine_threads(g), sm, s>>>(p, q, c->fine.T, c->n, g, c->fine.m, c->fine.nbr,
+                                                                    c->red, nullptr, R);
 }
 
 // Prolongation on the fine level (Algorithm 1: u += R_1^T e_c); the coarse
 // correction is in the V-cycle precision.
 template <typename V, typename BT>
 void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const V* ec, PcgScalars* sc, cudaStream_t s) {
-  const unsigned grid = (unsigned)((c->n + 255) / 256);
-  k_prolong<V, BT, V><<<grid, 256, 0, s>>>((V*)c->sb.vu[1], Phi, c->fine.L, ec, c->n, c->fine.nb, sc);
+  const unsigned grid = (unsigned)((c->n + 255) / 256 * c->sb.R);
+  k_prolong<V, BT, V><<<grid, 256, 0, s>>>((V*)c->sb.vu[1], Phi, c->fine.L, ec, c->n, c->lev[2].n, c->fine.nb, sc,
+                                           c->sb.R);
 }
 template void launch_prolong_fine<float, float>(msmg_ctx*, const float*, const float*, PcgScalars*, cudaStream_t);
 template void launch_prolong_fine<double, double>(msmg_ctx*, const double*, const double*, PcgScalars*, cudaStream_t);
@@ -333,7 +343,9 @@ __global__ void k_fill_pattern(double* __restrict__ v, int64_t n, double phase) 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = sin(0.001 * (double)i + phase) + 0.25 * cos(0.0173 * (double)i);
 }
-__global__ void k_reset_scalars(PcgScalars* sc) {
+__global__ void k_reset_scalars(PcgScalars* scs, int R) {
+  if ((int)threadIdx.x >= R) return;
+  PcgScalars* sc = scs + threadIdx.x;
   sc->done = 0;
   sc->iter = 1;
   sc->max_iter = 1 << 30;
@@ -349,10 +361,13 @@ void pcg_step_vcycle_timed(msmg_ctx* c, int update, const double* qv, PcgScalars
                            cudaEvent_t* ev);
 void pcg_step_pmatvec(msmg_ctx* c, PcgScalars* sc, cudaStream_t s);
 
-// Per-kernel device times of one PCG iteration's fine-level work (events on s).
-int time_kernels(msmg_ctx* c, int reps, double* acc, cudaStream_t s) {
+// Per-kernel device times of one PCG iteration's fine-level work (events on s),
+// for a batch of R right-hand sides.
+int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s) {
   SolveBuffers& B = c->sb;
-  const int64_t n = c->n;
+  if (R < 1 || R > B.n_rhs) return MSMG_ERR_INVALID_ARG;
+  B.R = R;
+  const int64_t n = c->n * R;
   const unsigned g1 = (unsigned)((n + 255) / 256);
   k_fill_pattern<<<g1, 256, 0, s>>>(B.r, n, 0.3);
   k_fill_pattern<<<g1, 256, 0, s>>>(B.p0, n, 1.1);
@@ -365,9 +380,9 @@ int time_kernels(msmg_ctx* c, int reps, double* acc, cudaStream_t s) {
   for (int i = 0; i < 7; ++i) acc[i] = 0.0;
   const bool flexible = c->opts.precision == MSMG_MIXED;
   for (int r = 0; r < reps; ++r) {
-    k_reset_scalars<<<1, 1, 0, s>>>(B.sc);
+    k_reset_scalars<<<1, 32 * ((R + 31) / 32), 0, s>>>(B.sc, R);
     pcg_step_vcycle_timed(c, 1, flexible ? B.q : nullptr, B.sc, s, ev);   // ev[0..5]
-    k_reset_scalars<<<1, 1, 0, s>>>(B.sc);
+    k_reset_scalars<<<1, 32 * ((R + 31) / 32), 0, s>>>(B.sc, R);
     cudaEventRecord(ev[6], s);
     pcg_step_pmatvec(c, B.sc, s);
     cudaEventRecord(ev[7], s);

@@ -20,6 +20,11 @@
 //   k_restrict r_c = Phi^T (r - A u) per element (Algorithm 1, restriction)
 //   k_prolong  u += Phi e_c (Algorithm 1, prolongation)   [fine.cu]
 //   k_post     z = u + M^{-T} (r - A u), reduce r.z (and z.q for the flexible beta)
+//
+// Every kernel also runs R right-hand sides in lockstep (vectors stored n
+// apart, one PcgScalars record and one reduction slice each): CTA b handles
+// element group b / R of right-hand side b % R, so an element's coefficients
+// are read from HBM once per launch and from L2 by the other R - 1 CTAs.
 #include "msmg_internal.cuh"
 #include "reduce.cuh"
 
@@ -266,11 +271,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
                                                            const V* __restrict__ T, const V* __restrict__ invd,
                                                            V* __restrict__ rv, V* __restrict__ u, int64_t n, G g,
                                                            int64_t m, const int* __restrict__ nbr, int update,
-                                                           RedSlot red, PcgScalars* sc) {
+                                                           RedSlot red, PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
+  {
+    const int64_t off = (int64_t)bi.r * n;
+    x += off; r += off; p += off; q += off; rv += off; u += off;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
   const bool act = e < m;
   const WStage<V> s = w_stage<V>(smem, g, warp);
   double acc = 0.0;
@@ -320,7 +331,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
   }
   if (update) {
     double v[1] = {acc};
-    grid_reduce<1>(v, red, [=] __device__(double* t) {
+    grid_reduce_r<1>(v, red, bi, [=] __device__(double* t) {
       sc->rr = t[0];
       sc->iter += 1;
       if (!isfinite(t[0])) sc->done = 2;
@@ -336,14 +347,19 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
 template <typename V, typename BT, typename G>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) k_restrict(const V* __restrict__ f, const V* __restrict__ u,
                                                                 const V* __restrict__ T, const BT* __restrict__ Phi,
-                                                                int L, double* __restrict__ rc, int64_t n, G g,
-                                                                int64_t m, const int* __restrict__ nbr,
-                                                                const PcgScalars* sc) {
+                                                                int L, double* __restrict__ rc, int64_t nc, int64_t n,
+                                                                G g, int64_t m, const int* __restrict__ nbr,
+                                                                const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
+  f += (int64_t)bi.r * n;
+  u += (int64_t)bi.r * n;
+  rc += (int64_t)bi.r * nc;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kC = 16;                                   // cells per lane held in registers
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
   if (e >= m) return;
   const WStage<V> s = w_stage<V>(smem, g, warp);
   const WElem E = w_elem(e, nbr, g);
@@ -402,12 +418,19 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
                                                             const V* __restrict__ invd, double* __restrict__ z,
                                                             const double* __restrict__ qv, int64_t n, G g,
                                                             int64_t m, const int* __restrict__ nbr, RedSlot red,
-                                                            PcgScalars* sc) {
+                                                            PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
   if (sc && sc->done) return;
+  {
+    const int64_t off = (int64_t)bi.r * n;
+    f += off; r += off; u += off; z += off;
+    if (qv) qv += off;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kC = 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
   const bool act = e < m;
   const WStage<V> s = w_stage<V>(smem, g, warp);
   const int ncl = (g.nb + 31) / 32;
@@ -469,7 +492,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
     }
   }
   if (sc) {
-    grid_reduce<2>(v, red, [=] __device__(double* t) {
+    grid_reduce_r<2>(v, red, bi, [=] __device__(double* t) {
       sc->rz_old = sc->rz;
       sc->rz = t[0];
       if (sc->flexible) sc->beta = sc->rz_old != 0.0 ? -sc->alpha * t[1] / sc->rz_old : 0.0;
@@ -487,11 +510,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __r
                                                                const double* __restrict__ T,
                                                                const double* __restrict__ Dg, int64_t n, G g,
                                                                int64_t m, const int* __restrict__ nbr, RedSlot red,
-                                                               PcgScalars* sc) {
+                                                               PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  sc += bi.r;
   if (sc->done) return;
+  {
+    const int64_t off = (int64_t)bi.r * n;
+    z += off; pold += off; pnew += off; q += off;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
   const bool act = e < m;
   double* ut = reinterpret_cast<double*>(smem) + (size_t)warp * r4(g.P);
   double acc = 0.0;
@@ -556,7 +585,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __r
     }
   }
   double v[1] = {acc};
-  grid_reduce<1>(v, red, [=] __device__(double* t) {
+  grid_reduce_r<1>(v, red, bi, [=] __device__(double* t) {
     sc->pq = t[0];
     if (!(t[0] > 0.0) || !isfinite(t[0])) { sc->done = 2; sc->alpha = 0.0; }
     else sc->alpha = sc->rz / t[0];
@@ -589,39 +618,41 @@ static void with_geo(const msmg_ctx* c, F&& f) {
   else f(make_geor(bx, by, bz));
 }
 
+// CTAs of a batched fine-level launch: element groups x right-hand sides
+static inline unsigned fine_wgrid(const msmg_ctx* c) {
+  return (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta * c->sb.R);
+}
+
 template <typename V, typename BT, typename G>
 static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* sc, cudaStream_t s, const G& g) {
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
   SolveBuffers& B = c->sb;
-  k_pre<V, G><<<grid, kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv,
-                                                                    (V*)B.vu[1], c->n, g, c->fine.m, c->fine.nbr,
-                                                                    update, c->red, sc);
+  k_pre<V, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+      B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv, (V*)B.vu[1], c->n, g, c->fine.m, c->fine.nbr, update, c->red, sc,
+      B.R);
 }
 
 template <typename V, typename BT, typename G>
 static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cudaStream_t s, const G& g) {
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
   SolveBuffers& B = c->sb;
-  k_restrict<V, BT, G><<<grid, kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
-      (const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L, (double*)B.vf[2], c->n, g, c->fine.m, c->fine.nbr, sc);
+  k_restrict<V, BT, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+      (const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
+      c->fine.nbr, sc, B.R);
 }
 
 template <typename V, typename BT, typename G>
 static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const double* qv, PcgScalars* sc, cudaStream_t s,
                    const G& g) {
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
   SolveBuffers& B = c->sb;
-  k_post<V, G><<<grid, kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>((const V*)B.rv, B.r, (const V*)B.vu[1], o.T,
-                                                                     o.invd, B.z, qv, c->n, g, c->fine.m,
-                                                                     c->fine.nbr, c->red, sc);
+  k_post<V, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>((const V*)B.rv, B.r, (const V*)B.vu[1],
+                                                                             o.T, o.invd, B.z, qv, c->n, g, c->fine.m,
+                                                                             c->fine.nbr, c->red, sc, B.R);
 }
 
 template <typename G>
 static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s, const G& g) {
-  const unsigned grid = (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta);
   SolveBuffers& B = c->sb;
-  k_pmatvec<G><<<grid, kWarpsPerCta * 32, wsmem_p(g), s>>>(B.z, B.pcur, B.pnext, B.q, c->fine.T,
-                                                              c->fine.D, c->n, g, c->fine.m, c->fine.nbr, c->red, sc);
+  k_pmatvec<G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem_p(g), s>>>(B.z, B.pcur, B.pnext, B.q, c->fine.T, c->fine.D,
+                                                                      c->n, g, c->fine.m, c->fine.nbr, c->red, sc, B.R);
 }
 
 template <typename V, typename BT>

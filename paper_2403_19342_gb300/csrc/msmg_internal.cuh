@@ -68,11 +68,40 @@ struct PcgScalars {
 
 // A deterministic grid reduction slot: per-CTA partials, a ticket counter and
 // a result.  The last CTA to finish sums the partials in index order.
+//
+// A batched launch (R right-hand sides in lockstep) reduces each right-hand
+// side separately: slice r of the partials starts at r * stride and uses
+// counter[r].
 struct RedSlot {
-  double* partials;     // [max CTAs of a reducing launch][kRedWidth]
-  unsigned* counter;    // zero between uses
+  double* partials;     // [R][max CTAs of a reducing launch per rhs][kRedWidth]
+  unsigned* counter;    // [R], zero between uses
+  int64_t stride;       // doubles per right-hand-side slice of partials
 };
 constexpr int kRedWidth = 4;   // up to 4 simultaneous sums per reduction
+
+// Batched launches order their CTAs right-hand-side minor: CTA b works on block
+// b / R of the data of right-hand side b % R, so the R CTAs that share an
+// element's coefficients run next to each other and the coefficients are read
+// from HBM once and from L2 R - 1 times.
+struct BatchIdx {
+  int r;              // right-hand side
+  unsigned blk;       // block index within the right-hand side
+  unsigned nblk;      // blocks per right-hand side
+};
+__device__ __forceinline__ BatchIdx batch_idx(int R) {
+  BatchIdx b;
+  b.r = (int)(blockIdx.x % (unsigned)R);
+  b.blk = blockIdx.x / (unsigned)R;
+  b.nblk = gridDim.x / (unsigned)R;
+  return b;
+}
+__host__ __device__ __forceinline__ RedSlot red_for(const RedSlot& red, int r) {
+  RedSlot o;
+  o.partials = red.partials + (int64_t)r * red.stride;
+  o.counter = red.counter + r;
+  o.stride = red.stride;
+  return o;
+}
 
 // ---------------------------------------------------------------- levels
 struct FineLevel {
@@ -132,7 +161,10 @@ struct SolveBuffers {
   void* vu[kMaxLevels];
   void* vw[kMaxLevels];
   PcgScalars* sc;               // [n_rhs]
-  int n_rhs;
+  int n_rhs;                    // capacity: every vector above holds n_rhs copies
+  int R;                        // right-hand sides of the batch in flight (<= n_rhs)
+  double* dres;                 // [n_rhs][2] true-residual norms, mean sums
+  int* dmask;                   // [n_rhs] restart mask
 };
 
 }  // namespace msmg
@@ -157,6 +189,12 @@ struct msmg_ctx {
   cudaStream_t cap_stream;                      // private stream for graph capture
   cudaGraphExec_t iter_graph;                   // two captured PCG iterations
   int graph_state;                              // 0 not built, 1 ready, -1 capture failed
+  int graph_R;                                  // batch width the graph was captured for
+  msmg::PcgScalars* hsc;                        // pinned host mirror of sb.sc [max_rhs]
+  double* hres;                                 // pinned host mirror of sb.dres [max_rhs][2]
+  int* hmask;                                   // pinned host restart mask [max_rhs]
+  cudaEvent_t poll_evs[3];                      // PCG polls: two in-flight chunks, exit checks
+  cudaStream_t run_stream;                      // per-context stream of batched solves
 };
 
 namespace msmg {
@@ -170,8 +208,8 @@ void launch_pivots(msmg_ctx* c, cudaStream_t s);
 void launch_nat_to_blk(msmg_ctx* c, const double* in, double* out, cudaStream_t s);
 void launch_blk_to_nat(msmg_ctx* c, const double* in, double* out, cudaStream_t s);
 void launch_faces_to_nat(msmg_ctx* c, double* out, cudaStream_t s);
-// q = A p (FP64, block-major).  If dot_out != nullptr also p.q into it.
-void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s);
+// q = A p (FP64, block-major) for R right-hand sides stored n apart.
+void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s, int R = 1);
 
 // ---------------------------------------------------------------- setup
 int launch_level1_eigen(msmg_ctx* c, cudaStream_t s);
@@ -182,7 +220,7 @@ void launch_basis_export(msmg_ctx* c, int level, double* basis, double* lam, boo
 void launch_operator_export(msmg_ctx* c, int level, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- solve
-int pcg_solve(msmg_ctx* c, const double* rhs_nat, double* x_nat, double rtol, int max_iter, int flags,
+int pcg_solve(msmg_ctx* c, const double* rhs_nat, double* x_nat, int n_rhs, double rtol, int max_iter, int flags,
               cudaStream_t s, msmg_solve_info* info);
 double dot_host(msmg_ctx* c, const double* a, const double* b, int64_t n, cudaStream_t s);
 

@@ -31,19 +31,21 @@ __device__ __forceinline__ void block_sum(double (&v)[W], double* sh /* W * 32 *
   __syncthreads();
 }
 
-// Grid-wide deterministic reduction; ``fin(totals)`` runs once, in thread 0 of
-// the last CTA.  Every CTA of the grid must call this exactly once.
+// Grid-wide deterministic reduction over the nblk CTAs that share ``red``
+// (CTA index blk among them); ``fin(totals)`` runs once, in thread 0 of the
+// last of them.  Every one of those CTAs must call this exactly once.
 template <int W, typename Fin>
-__device__ __forceinline__ void grid_reduce(double (&v)[W], const RedSlot& red, Fin fin) {
+__device__ __forceinline__ void grid_reduce_b(double (&v)[W], const RedSlot& red, unsigned blk, unsigned nblk,
+                                              Fin fin) {
   __shared__ double sh[W * 32];
   __shared__ int am_last;
   block_sum<W>(v, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) red.partials[(size_t)blockIdx.x * W + w] = v[w];
+    for (int w = 0; w < W; ++w) red.partials[(size_t)blk * W + w] = v[w];
     __threadfence();
     unsigned t = atomicAdd(red.counter, 1u);
-    am_last = (t == gridDim.x - 1);
+    am_last = (t == nblk - 1);
   }
   __syncthreads();
   if (!am_last) return;
@@ -51,7 +53,7 @@ __device__ __forceinline__ void grid_reduce(double (&v)[W], const RedSlot& red, 
   double acc[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) acc[w] = 0.0;
-  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+  for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) {
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] += __ldcg(&red.partials[(size_t)i * W + w]);
   }
@@ -61,6 +63,18 @@ __device__ __forceinline__ void grid_reduce(double (&v)[W], const RedSlot& red, 
     *red.counter = 0u;
     __threadfence();
   }
+}
+
+// The same over the whole grid of a launch.
+template <int W, typename Fin>
+__device__ __forceinline__ void grid_reduce(double (&v)[W], const RedSlot& red, Fin fin) {
+  grid_reduce_b<W>(v, red, blockIdx.x, gridDim.x, fin);
+}
+
+// Batched form: right-hand side bi.r reduces over its own CTAs into its slice.
+template <int W, typename Fin>
+__device__ __forceinline__ void grid_reduce_r(double (&v)[W], const RedSlot& red, const BatchIdx& bi, Fin fin) {
+  grid_reduce_b<W>(v, red_for(red, bi.r), bi.blk, bi.nblk, fin);
 }
 
 }  // namespace msmg
