@@ -12,6 +12,7 @@ flushed (256 MiB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batched [--steps K] [--warmup W]
+  python bench.py --workload layered [--steps K] [--warmup W]
 
 The default line also carries ``batched_rhs``: the same workload with 16
 zero-mean random right-hand sides solved in one call (one launch sequence for
@@ -20,6 +21,11 @@ workload instead: 8 lognormal realisations (sigma_logk 2 + 2i/7, correlation
 length 0.1) on 64^3, 64^3, 96^3, 96^3, 128^3, 128^3, 192^3, 192^3 grids with
 16 random zero-mean right-hand sides each, all solved by one
 msmg_solve_batched call (one stream per problem, CUDA graphs).
+``--workload layered`` measures the learned warm start: a 512^3 layered field
+with sinuous channels (85 layers, contrast 1e6-1e8, seed 100), 8^3 elements,
+6 levels, 6 eigenvectors per local problem; the network is trained first on
+eigenpairs the library computes for held-out 128^3 fields of the same kind
+(seeds 101-110); set-up is timed cold and warm-started, then the mixed solve.
 
 With N > 1 (torchrun) every rank solves its own replica of the workload (the
 problem does not shard across the one-GPU machines of this pool): weak scaling,
@@ -75,17 +81,17 @@ def rhs(shape):
 # a V-cycle value (4 mixed, 8 FP64).
 #   pre:      x, r read+write, p, q read (FP64); r copy and u written (v); T (3), 1/d read (v)
 #   restrict: r copy, u (v); T (3) (v); basis (L values, v)
-#   prolong:  u read+write (v); basis (L values, v)
-#   post:     r copy, u (v); T (3), 1/d (v); r read (FP64); q read (FP64, flexible beta
-#             only); z written (FP64)
+#   post:     r copy, u (v); T (3), 1/d (v); basis (L values, v: the prolongation
+#             runs inside it); r read (FP64); q read (FP64, flexible beta only);
+#             z written (FP64)
 #   pmatvec:  z, p_old read, p_new, q written (FP64); T (3) and the diagonal D (FP64)
 # With R right-hand sides in one launch the coefficients (T, 1/d, D, basis) are read
 # once for all R: bytes per cell and right-hand side.
 def kernel_bytes(form: str, L: int, R: int = 1) -> dict:
     v = 4 if form == "mixed" else 8
     flex = 8 if form == "mixed" else 0
-    return {"pre": 48 + 2 * v + 4 * v / R, "restrict": 2 * v + (3 * v + L * v) / R, "prolong": 2 * v + L * v / R,
-            "post": 2 * v + 4 * v / R + 8 + flex + 8, "pmatvec": 32 + 32 / R}
+    return {"pre": 48 + 2 * v + 4 * v / R, "restrict": 2 * v + (3 * v + L * v) / R, "prolong": 0.0,
+            "post": 2 * v + (4 * v + L * v) / R + 8 + flex + 8, "pmatvec": 32 + 32 / R}
 
 
 def load_peaks():
@@ -268,7 +274,7 @@ def batched_rhs(pkg, S, shape, n, args, world, flush, stream):
     its = [i["iterations"] for i in infos]
     kt = S.time_kernels(reps=5, n_rhs=BATCH_RHS)
     kb = kernel_bytes("mixed", N_EIG[0], BATCH_RHS)
-    vc = sum(kb[k] for k in ("pre", "restrict", "prolong", "post")) * n * BATCH_RHS
+    vc = sum(kb[k] for k in ("pre", "restrict", "post")) * n * BATCH_RHS
     peak, _ = load_peaks()
     return {"n_rhs": BATCH_RHS, "value": world * n * BATCH_RHS / (step * 1e-3), "unit": "DOF/s",
             "ms_per_step": step, "iterations_min": min(its), "iterations_max": max(its),
@@ -301,7 +307,8 @@ def run_gpu(args, world, rank, local):
     launches = 0
     batched = None
     for form, prec in (("fp64", pkg.FP64), ("mixed", pkg.MIXED)):
-        opts = pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec, eig_tol=1e-8)
+        opts = pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec, eig_tol=1e-8,
+                           autotune=True)
         S = pkg.Solver(kappa, opts, n_rhs=BATCH_RHS if form == "mixed" else 1)
         info0 = S.info
         for _ in range(args.warmup):
@@ -329,6 +336,7 @@ def run_gpu(args, world, rank, local):
         if form == "mixed":
             launches = int(sum(i["kernel_launches"] for i in infos))
         forms[form] = {"value": world * n / (ms_step * 1e-3), "unit": "DOF/s", "ms_per_step": ms_step,
+                       "tuning": info0["tuning"],
                        "iterations": inf["iterations"], "true_rel_residual": inf["true_rel_residual"],
                        "converged": bool(inf["converged"]), "setup_ms": info0["setup_ms"],
                        "eig_ms": info0["eig_ms"], "eig_residual_max": info0["eig_residual_max"],
@@ -360,14 +368,14 @@ def run_gpu(args, world, rank, local):
     L = N_EIG[0]
     kb = kernel_bytes("mixed", L)
     kt = kernel_times["mixed"]
-    fine = {k: kt[k] for k in ("pre", "restrict", "prolong", "post", "pmatvec")}
+    fine = {k: kt[k] for k in ("pre", "restrict", "post", "pmatvec")}
     dom = max(fine, key=fine.get)
     achieved = kb[dom] * n / (kt[dom] * 1e-3) / 1e9
     traffic = traffic_record(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": kb[dom] * n, "avg_launch_ms": kt[dom]}
-    vc_keys = ("pre", "restrict", "prolong", "post")
+    vc_keys = ("pre", "restrict", "post")
     vc_bytes = sum(kb[k] for k in vc_keys) * n
     vc_frac = vc_bytes / (kt["vcycle"] * 1e-3) / 1e9 / peak
     vc64 = sum(kernel_bytes("fp64", L)[k] for k in vc_keys) * n / (kernel_times["fp64"]["vcycle"] * 1e-3) / 1e9 / peak
@@ -411,7 +419,7 @@ def run_batched(args, world, rank, local):
     setup_ms, eig_ms, total = [], [], 0
     for N, (kappa, f) in zip(C3_GRIDS, fields.lognormal_batch(BATCH_RHS, C3_GRIDS, device="cuda")):
         opts = pkg.Options(n_levels=4, block=(8, 8, 8), ratio=[(2, 2, 2), (2, 2, 2)], n_eig=[4, 4, 4],
-                           precision=pkg.MIXED, eig_tol=1e-8)
+                           precision=pkg.MIXED, eig_tol=1e-8, autotune=True)
         S = pkg.Solver(torch.tensor(kappa, device=dev), opts, n_rhs=BATCH_RHS)
         solvers.append(S)
         setup_ms.append(S.info["setup_ms"])
@@ -476,6 +484,102 @@ def run_batched(args, world, rank, local):
     return 0
 
 
+LAYERED_N = 512
+LAYERED_WORKLOAD = ("512^3 layered field: 85 z-layers of laterally upsampled 60x220 lognormal lattices, sinuous "
+                    "binary channels in 50 layers, contrast U(1e6, 1e8) (seed 100); corner source/sink; 8^3 "
+                    "elements, 6 levels (ratio 2), 6 eigenvectors per local problem; PCG rtol 1e-8; learned "
+                    "warm start trained on 128^3 fields of the same kind (seeds 101-110)")
+
+
+def train_warm_start(pkg, torch, fields, L, n_fields=10, N=128, steps=6000, hidden=(1024, 1024)):
+    """Train the warm-start network on eigenpairs the library computes for held-out
+    fields; returns (net, record)."""
+    opts = dict(n_levels=4, block=(8, 8, 8), ratio=[(2, 2, 2)] * 2, n_eig=[L] * 3, precision=pkg.MIXED,
+                eig_tol=1e-8)
+    t0 = time.perf_counter()
+    xs, ys = [], []
+    for seed in range(101, 101 + n_fields):
+        S = pkg.Solver(torch.tensor(fields.layered_channels((N, N, N), seed=seed), device="cuda"),
+                       pkg.Options(**opts))
+        x, y = S.learning_data()
+        xs.append(x)
+        ys.append(y.reshape(y.shape[0], -1))
+        S.close()
+    X, Y = torch.cat(xs), torch.cat(ys)
+    t1 = time.perf_counter()
+    net = pkg.WarmStartNet(n_in=512, hidden=hidden, n_vec=L - 1, batch_max=512, seed=7)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    loss = None
+    for step in range(steps):
+        idx = torch.randint(0, X.shape[0], (512,), device="cuda", generator=gen)
+        loss = net.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr=3e-4 if step < 0.7 * steps else 1e-4)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return net, {"samples": int(X.shape[0]), "eigenpairs": int(X.shape[0]) * (L - 1), "steps": steps,
+                 "hidden": list(hidden), "final_batch_loss": loss, "data_s": t1 - t0, "train_s": t2 - t1}
+
+
+def run_layered(args, world, rank, local):
+    import torch
+    import fields
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    _build.build()
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = 6
+    net, train = train_warm_start(pkg, torch, fields, L)
+    kappa = torch.tensor(fields.layered_channels((LAYERED_N,) * 3, seed=100), device=dev)
+    n = LAYERED_N ** 3
+    base = dict(n_levels=6, block=(8, 8, 8), ratio=[(2, 2, 2)] * 4, n_eig=[L] * 5, precision=pkg.MIXED, eig_tol=1e-8,
+                autotune=True)
+    recs = {}
+    solver = None
+    for name, ws in (("cold", None), ("warm", net)):
+        S = pkg.Solver(kappa, pkg.Options(**base, warm_start=ws))
+        i = S.info
+        recs[name] = {"setup_ms": i["setup_ms"], "eig_ms": i["eig_ms"], "eig_iterations_total": i["eig_iterations_total"],
+                      "eig_iterations_max": i["eig_iterations_max"], "eig_residual_max": i["eig_residual_max"],
+                      "warm_started": i["warm_started"]}
+        if name == "warm":
+            solver = S
+        else:
+            S.close()
+            del S
+    f = torch.tensor(rhs((LAYERED_N,) * 3), device=dev)
+    x = torch.zeros_like(f)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pkg.msmg_solve(solver.ctx, f, x, RTOL, 2000, 0)
+    torch.cuda.synchronize()
+    ms, info = [], None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, info = pkg.msmg_solve(solver.ctx, f, x, RTOL, 2000, 0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    step = max_over_ranks(world, float(np.mean(ms)))
+    line = {"metric": METRIC, "value": world * n / (step * 1e-3), "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": LAYERED_WORKLOAD, "form": "mixed, learned warm start",
+                       "l2": "flushed before each step (256 MiB write); working set > L2"},
+            "iterations": info[0]["iterations"], "true_rel_residual": info[0]["true_rel_residual"],
+            "setup": recs, "training": train,
+            "setup_speedup": recs["cold"]["setup_ms"] / recs["warm"]["setup_ms"],
+            "gpu_launches": int(info[0]["kernel_launches"])}
+    solver.close()
+    net.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile(args):
     """Short run for ncu: set-up of the default workload, then one solve capped at
     ``--max-iter`` PCG iterations in the chosen form."""
@@ -507,7 +611,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="short run for ncu (no timing output)")
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--max-iter", type=int, default=4)
-    ap.add_argument("--workload", default="inclusions", choices=["inclusions", "batched"])
+    ap.add_argument("--workload", default="inclusions", choices=["inclusions", "batched", "layered"])
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
@@ -515,7 +619,8 @@ def main():
                                                                    int(os.environ.get("RANK", "0")), 0)
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    rc = (run_batched if args.workload == "batched" else run_gpu)(args, world, rank, local)
+    run = {"batched": run_batched, "layered": run_layered}.get(args.workload, run_gpu)
+    rc = run(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

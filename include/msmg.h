@@ -39,6 +39,7 @@ extern "C" {
 
 typedef struct CUstream_st* msmg_stream;        /* same handle as cudaStream_t */
 typedef struct msmg_ctx msmg_ctx;                /* opaque, owned by the library */
+typedef struct msmg_net msmg_net;                /* opaque: learned warm-start network */
 
 #define MSMG_MAX_LEVELS 8
 
@@ -90,6 +91,12 @@ typedef struct {
     int precision;                     /* MSMG_FP64 or MSMG_MIXED                                    */
     double eig_tol;                    /* local eigen-residual tolerance (see msmg_setup)            */
     int eig_max_iter;                  /* cap on subspace iterations per element (0: default 200)    */
+    int autotune;                      /* 1: msmg_setup times the V-cycle variants (msmg_autotune)   */
+                                       /* for batch width 1 and the context's widest batch           */
+    const msmg_net* warm_start;        /* NULL: cold start; else a network whose n_in equals the     */
+                                       /* level-1 element's cells and n_vec equals n_eig[0] - 1:     */
+                                       /* its guesses seed the level-1 subspace iteration (elements  */
+                                       /* of more than 96 cells), which still runs to eig_tol        */
 } msmg_options;
 
 typedef struct {
@@ -99,6 +106,14 @@ typedef struct {
     double setup_ms;                   /* device time of msmg_setup                      */
     double eig_ms;                     /* of which level-1 eigensolves                   */
     int eig_iterations_max;            /* subspace iterations of the slowest element     */
+    int64_t eig_iterations_total;      /* subspace iterations summed over the elements   */
+    int warm_started;                  /* 1 when the learned warm start seeded level 1   */
+    int tuning[4];                     /* V-cycle variants in use, for batch width 1 and  */
+                                       /* wider: [0], [1] fine prolongation inside the    */
+                                       /* post-smoothing kernel (1) or apart (0); [2], [3] */
+                                       /* coarse cycle: a launch per step (0), the small  */
+                                       /* levels as one cluster launch (1), every coarse  */
+                                       /* level as one cooperative grid launch (2)        */
     double eig_residual_max;           /* largest final eigen-residual (level 1)         */
     int64_t workspace_bytes;
 } msmg_setup_info;
@@ -184,6 +199,25 @@ int msmg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rh
 /* The context's batch width: right-hand sides one msmg_solve launch sequence carries. */
 int msmg_max_batch_rhs(const msmg_ctx* ctx);
 
+/*
+ * Autotuner: times the V-cycle variants at batch width n_rhs (1 .. msmg_max_batch_rhs) with
+ * CUDA events over reps repetitions on the context's buffers and keeps the fastest for
+ * that width class (width 1, or wider).  The variants -- fine prolongation fused into the
+ * post-smoothing kernel or a kernel of its own; the coarse cycle as a launch per step, its
+ * small levels and the coarsest solve as one thread-block-cluster launch (when the
+ * hierarchy has such a tail: at most 256 parents on its first level, at most 1536
+ * coarsest unknowns), or every coarse level as one cooperative launch over the whole GPU
+ * (at most 4096 coarsest unknowns) -- give the same bits: only the time moves.  Overwrites the solve buffers; call between
+ * solves.  msmg_setup runs it when options.autotune is set; the choice is reported in
+ * msmg_setup_info.tuning.
+ */
+int msmg_autotune(msmg_ctx* ctx, int n_rhs, int reps, msmg_stream stream);
+
+/* Apply a tuning found earlier (for instance a saved msmg_setup_info.tuning): four
+ * values in the order and ranges of msmg_setup_info.tuning.  MSMG_ERR_UNSUPPORTED if a
+ * fused coarse form is asked for that the hierarchy or the GPU does not allow. */
+int msmg_set_tuning(msmg_ctx* ctx, const int* tuning);
+
 /* q = A p, FP64, natural order (Eq. (discrete varia)). */
 int msmg_apply_A(msmg_ctx* ctx, const double* p, double* q, msmg_stream stream);
 
@@ -254,12 +288,76 @@ void msmg_destroy(msmg_ctx* ctx);
 const char* msmg_status_string(int status);
 
 /*
+ * ------------------------------------------------------------ learned warm start
+ * A multilayer perceptron n_in -> hidden[0] -> hidden[1] -> n_vec * n_in (ReLU after
+ * the two hidden layers), its output o_k scaled cell by cell by w_c = sqrt(S_c / sum S)
+ * (recovered from the input: S_c is proportional to exp(8 x_c)), maps a level-1
+ * element's standardised log-permeability patch
+ * x[c] = clamp(log S_c - mean log S, -20, 20) / 8 (S = Tr K~ of Eq. (spepb); for an
+ * isotropic kappa, log S is log kappa plus a constant) to guesses for the element's
+ * eigenvectors 1 .. n_vec in the symmetric form y = S^{1/2} phi, ||y||_2 = 1 (vector 0,
+ * the constant, is known).  Not part of the paper: it only seeds the subspace iteration
+ * of msmg_setup (options.warm_start), which still runs to eig_tol, so the
+ * preconditioner does not depend on it.
+ *
+ * Weights: FP32 masters and BF16 copies that every product reads; FP32 activations and
+ * accumulation.  Parameter layout (one FP32 array of msmg_net_param_count values):
+ * W_l row-major [fan_in][fan_out] at w_off[l], b_l at b_off[l] (msmg_net_param_offsets).
+ * Loss per sample and vector (sign-invariant): ||p||^2 + ||t||^2 - 2 |p . t|, averaged
+ * over samples and vectors.  Training: Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * masters.  All kernels are deterministic.
+ */
+typedef struct {
+    int n_in;              /* cells per level-1 element                              */
+    int hidden[2];         /* hidden layer widths                                    */
+    int n_vec;             /* eigenvector guesses per element (n_eig[0] - 1)         */
+    int batch_max;         /* rows per pass (activations are sized for it)           */
+} msmg_net_desc;
+
+/* Device bytes for a network of this shape (0 for an invalid description). */
+size_t msmg_net_workspace_size(const msmg_net_desc* desc);
+
+/* Create a network in the caller's device workspace (256-byte aligned, >=
+ * msmg_net_workspace_size); weights uniform in +-sqrt(6 / fan_in) (last layer a quarter
+ * of that) from a counter-based hash of seed and index (splitmix64), biases zero. */
+int msmg_net_create(const msmg_net_desc* desc, void* workspace, size_t workspace_bytes, uint64_t seed,
+                    msmg_stream stream, msmg_net** out);
+void msmg_net_destroy(msmg_net* net);
+int64_t msmg_net_param_count(const msmg_net* net);
+int msmg_net_param_offsets(const msmg_net* net, int64_t* w_off, int64_t* b_off);   /* 3 + 3 values */
+
+/* Copy the FP32 master parameters out (device array of msmg_net_param_count floats) or
+ * in (the BF16 copies are refreshed). */
+int msmg_net_get_params(const msmg_net* net, float* params, msmg_stream stream);
+int msmg_net_set_params(msmg_net* net, const float* params, msmg_stream stream);
+
+/* y[b] = network(x[b]) for b < batch (device, row-major [batch][n_in] -> [batch][n_vec * n_in]). */
+int msmg_net_forward(msmg_net* net, const float* x, float* y, int batch, msmg_stream stream);
+
+/* Loss of a batch (<= batch_max) and its gradient with respect to every parameter
+ * (device array of msmg_net_param_count floats, may be NULL); loss_host may be NULL. */
+int msmg_net_gradients(msmg_net* net, const float* x, const float* target, int batch, float* grad,
+                       float* loss_host, msmg_stream stream);
+
+/* One Adam step on a batch (<= batch_max) with learning rate lr; the batch loss before
+ * the step goes to *loss_host (may be NULL). */
+int msmg_net_train_step(msmg_net* net, const float* x, const float* target, int batch, float lr,
+                        float* loss_host, msmg_stream stream);
+
+/* Training pairs of a set-up context (level-1 elements of more than one eigenvector):
+ * x [m][nb] network inputs and y [m][n_eig[0] - 1][nb] the computed eigenvectors 1 ..
+ * n_eig[0]-1 in the symmetric form; elements in lexicographic order (x fastest), as in
+ * msmg_export_basis. */
+int msmg_learning_data(msmg_ctx* ctx, float* x, float* y, msmg_stream stream);
+
+/*
  * Average device time (ms) per launch of the fine-level kernels of one PCG iteration,
  * measured with CUDA events around each launch on the given stream over reps repetitions on
  * the context's own buffers (fixed synthetic data), at batch width n_rhs (1 .. the
  * context's).  ms_out[0 .. n_out) receives:
  *   [0] PCG update of x and r fused with the pre-smoothing   [1] residual + restriction
- *   [2] prolongation   [3] residual + post-smoothing (with the r.z reduction)
+ *   [2] 0 (the prolongation runs inside [3])
+ *   [3] prolongation + residual + post-smoothing (with the r.z reduction)
  *   [4] all coarse levels (levels >= 2)   [5] search-direction update fused with q = A p
  *   [6] [0]..[3] and [4] together (one preconditioner application)
  * Used for roofline figures; no effect on results.

@@ -23,6 +23,9 @@ reordering beyond what the definition states:
                     the coarsest Moore-Penrose pseudo-inverse.
 * ``solver``     -- the V-cycle (Algorithm 1, generalised recursively to any
                     number of levels) and preconditioned conjugate gradients.
+* ``learned``    -- the learned warm start of the level-1 eigensolves (not a
+                    step of the paper): network forward, sign-invariant loss,
+                    back-propagation and the Adam step.
 
 Pins (tests marked ``not gpu``) tie each function to closed forms, to values
 the paper prints, to library routines on special cases and to brute force.

@@ -47,13 +47,19 @@ class msmg_grid(C.Structure):
 class msmg_options(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("block", C.c_int * 3), ("ratio", (C.c_int * 3) * MAX_LEVELS),
                 ("n_eig", C.c_int * MAX_LEVELS), ("nu", C.c_int * MAX_LEVELS), ("precision", C.c_int),
-                ("eig_tol", C.c_double), ("eig_max_iter", C.c_int)]
+                ("eig_tol", C.c_double), ("eig_max_iter", C.c_int), ("autotune", C.c_int),
+                ("warm_start", C.c_void_p)]
 
 
 class msmg_setup_info(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("dims", C.c_int64 * MAX_LEVELS), ("elements", C.c_int64 * MAX_LEVELS),
                 ("setup_ms", C.c_double), ("eig_ms", C.c_double), ("eig_iterations_max", C.c_int),
+                ("eig_iterations_total", C.c_int64), ("warm_started", C.c_int), ("tuning", C.c_int * 4),
                 ("eig_residual_max", C.c_double), ("workspace_bytes", C.c_int64)]
+
+
+class msmg_net_desc(C.Structure):
+    _fields_ = [("n_in", C.c_int), ("hidden", C.c_int * 2), ("n_vec", C.c_int), ("batch_max", C.c_int)]
 
 
 class msmg_solve_info(C.Structure):
@@ -95,6 +101,19 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_solve_batched": (I, [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), C.POINTER(I), D, I, I, P,
                                    C.POINTER(msmg_solve_info)]),
         "msmg_max_batch_rhs": (I, [P]),
+        "msmg_autotune": (I, [P, I, I, P]),
+        "msmg_set_tuning": (I, [P, C.POINTER(I)]),
+        "msmg_net_workspace_size": (S, [C.POINTER(msmg_net_desc)]),
+        "msmg_net_create": (I, [C.POINTER(msmg_net_desc), P, S, C.c_uint64, P, C.POINTER(P)]),
+        "msmg_net_destroy": (None, [P]),
+        "msmg_net_param_count": (I64, [P]),
+        "msmg_net_param_offsets": (I, [P, C.POINTER(I64), C.POINTER(I64)]),
+        "msmg_net_get_params": (I, [P, P, P]),
+        "msmg_net_set_params": (I, [P, P, P]),
+        "msmg_net_forward": (I, [P, P, P, I, P]),
+        "msmg_net_gradients": (I, [P, P, P, I, P, C.POINTER(C.c_float), P]),
+        "msmg_net_train_step": (I, [P, P, P, I, C.c_float, C.POINTER(C.c_float), P]),
+        "msmg_learning_data": (I, [P, P, P, P]),
         "msmg_dot_noalloc": (I, [P, P, I64, C.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -111,7 +130,11 @@ def exported_symbols():
             "msmg_dot_scratch_bytes", "msmg_dot", "msmg_export_basis", "msmg_import_bases",
             "msmg_export_operator", "msmg_export_faces", "msmg_get_setup_info", "msmg_destroy",
             "msmg_status_string", "msmg_probe_alu_peaks", "msmg_time_kernels", "msmg_dot_noalloc",
-            "msmg_solve_batched", "msmg_max_batch_rhs"]
+            "msmg_solve_batched", "msmg_max_batch_rhs", "msmg_autotune", "msmg_set_tuning",
+            "msmg_net_workspace_size", "msmg_net_create",
+            "msmg_net_destroy", "msmg_net_param_count", "msmg_net_param_offsets", "msmg_net_get_params",
+            "msmg_net_set_params", "msmg_net_forward", "msmg_net_gradients", "msmg_net_train_step",
+            "msmg_learning_data"]
 
 
 def _check(status: int) -> int:
@@ -147,6 +170,8 @@ class Options:
     precision: int = FP64
     eig_tol: float = 1e-12
     eig_max_iter: int = 0
+    autotune: bool = False             # time the V-cycle variants at set-up (msmg_autotune)
+    warm_start: object = None          # a WarmStartNet (or its handle) seeds the level-1 eigensolves
 
     def to_c(self) -> msmg_options:
         o = msmg_options()
@@ -164,6 +189,9 @@ class Options:
         o.precision = self.precision
         o.eig_tol = self.eig_tol
         o.eig_max_iter = self.eig_max_iter
+        o.autotune = 1 if self.autotune else 0
+        ws = self.warm_start
+        o.warm_start = (ws.handle if hasattr(ws, "handle") else ws) or None
         return o
 
 
@@ -243,6 +271,15 @@ def msmg_max_batch_rhs(ctx: int) -> int:
     return load_library().msmg_max_batch_rhs(ctx)
 
 
+def msmg_autotune(ctx: int, n_rhs: int = 1, reps: int = 3, stream=None) -> None:
+    _check(load_library().msmg_autotune(ctx, n_rhs, reps, _stream(stream)))
+
+
+def msmg_set_tuning(ctx: int, tuning) -> None:
+    arr = (C.c_int * 4)(*tuning)
+    _check(load_library().msmg_set_tuning(ctx, arr))
+
+
 def msmg_apply_A(ctx: int, p: torch.Tensor, q: torch.Tensor, stream=None) -> None:
     _check(load_library().msmg_apply_A(ctx, _ptr(p, torch.float64), _ptr(q, torch.float64), _stream(stream)))
 
@@ -299,8 +336,10 @@ def msmg_get_setup_info(ctx: int) -> dict:
     _check(load_library().msmg_get_setup_info(ctx, C.byref(i)))
     nL = i.n_levels
     return dict(n_levels=nL, dims=list(i.dims[:nL]), elements=list(i.elements[:nL - 1]), setup_ms=i.setup_ms,
-                eig_ms=i.eig_ms, eig_iterations_max=i.eig_iterations_max, eig_residual_max=i.eig_residual_max,
-                workspace_bytes=i.workspace_bytes)
+                eig_ms=i.eig_ms, eig_iterations_max=i.eig_iterations_max,
+                eig_iterations_total=i.eig_iterations_total, warm_started=bool(i.warm_started),
+                tuning=list(i.tuning),
+                eig_residual_max=i.eig_residual_max, workspace_bytes=i.workspace_bytes)
 
 
 def msmg_destroy(ctx: int) -> None:
@@ -317,6 +356,103 @@ def msmg_probe_alu_peaks(stream=None) -> tuple[float, float]:
     a, b = C.c_double(0), C.c_double(0)
     _check(load_library().msmg_probe_alu_peaks(C.byref(a), C.byref(b), _stream(stream)))
     return a.value, b.value
+
+
+# ----------------------------------------------------------------- learned warm start
+def msmg_net_workspace_size(desc: msmg_net_desc) -> int:
+    return load_library().msmg_net_workspace_size(C.byref(desc))
+
+
+def msmg_net_create(desc: msmg_net_desc, workspace: torch.Tensor, seed: int = 0, stream=None) -> int:
+    h = C.c_void_p(0)
+    _check(load_library().msmg_net_create(C.byref(desc), _ptr(workspace), workspace.numel(), seed, _stream(stream),
+                                          C.byref(h)))
+    return h.value
+
+
+def msmg_net_forward(net: int, x: torch.Tensor, y: torch.Tensor, stream=None) -> None:
+    _check(load_library().msmg_net_forward(net, _ptr(x, torch.float32), _ptr(y, torch.float32), x.shape[0],
+                                           _stream(stream)))
+
+
+def msmg_net_gradients(net: int, x: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,
+                       stream=None) -> float:
+    loss = C.c_float(0)
+    _check(load_library().msmg_net_gradients(net, _ptr(x, torch.float32), _ptr(target, torch.float32), x.shape[0],
+                                             _ptr(grad, torch.float32) if grad is not None else None,
+                                             C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def msmg_net_train_step(net: int, x: torch.Tensor, target: torch.Tensor, lr: float, stream=None) -> float:
+    loss = C.c_float(0)
+    _check(load_library().msmg_net_train_step(net, _ptr(x, torch.float32), _ptr(target, torch.float32), x.shape[0],
+                                              lr, C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def msmg_learning_data(ctx: int, x: torch.Tensor, y: torch.Tensor, stream=None) -> None:
+    _check(load_library().msmg_learning_data(ctx, _ptr(x, torch.float32), _ptr(y, torch.float32), _stream(stream)))
+
+
+class WarmStartNet:
+    """The learned warm start (include/msmg.h): a network in a torch-allocated device
+    workspace.  ``train`` runs Adam steps through the library's kernels."""
+
+    def __init__(self, n_in: int = 512, hidden=(512, 512), n_vec: int = 5, batch_max: int = 1024, seed: int = 0,
+                 stream=None):
+        self.desc = msmg_net_desc()
+        self.desc.n_in, self.desc.n_vec, self.desc.batch_max = n_in, n_vec, batch_max
+        self.desc.hidden[0], self.desc.hidden[1] = hidden
+        nbytes = msmg_net_workspace_size(self.desc)
+        if nbytes == 0:
+            raise MsmgError(-1, "invalid network description")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream
+        self.handle = msmg_net_create(self.desc, self.workspace, seed, stream)
+
+    @property
+    def n_param(self) -> int:
+        return load_library().msmg_net_param_count(self.handle)
+
+    def offsets(self):
+        w = (C.c_int64 * 3)()
+        b = (C.c_int64 * 3)()
+        _check(load_library().msmg_net_param_offsets(self.handle, w, b))
+        return list(w), list(b)
+
+    def get_params(self) -> torch.Tensor:
+        p = torch.empty(self.n_param, dtype=torch.float32, device="cuda")
+        _check(load_library().msmg_net_get_params(self.handle, _ptr(p), _stream(self.stream)))
+        return p
+
+    def set_params(self, p: torch.Tensor) -> None:
+        p = p.to(device="cuda", dtype=torch.float32).contiguous()
+        _check(load_library().msmg_net_set_params(self.handle, _ptr(p), _stream(self.stream)))
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        y = torch.empty((x.shape[0], self.desc.n_vec * self.desc.n_in), dtype=torch.float32, device="cuda")
+        msmg_net_forward(self.handle, x.contiguous(), y, self.stream)
+        return y
+
+    def gradients(self, x: torch.Tensor, target: torch.Tensor):
+        g = torch.empty(self.n_param, dtype=torch.float32, device="cuda")
+        loss = msmg_net_gradients(self.handle, x.contiguous(), target.contiguous(), g, self.stream)
+        return loss, g
+
+    def train_step(self, x: torch.Tensor, target: torch.Tensor, lr: float) -> float:
+        return msmg_net_train_step(self.handle, x.contiguous(), target.contiguous(), lr, self.stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().msmg_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------- convenience
@@ -412,6 +548,16 @@ class Solver:
         v = msmg_time_kernels(self.ctx, reps, self.stream, n_rhs)
         keys = ["pre", "restrict", "prolong", "post", "coarse_levels", "pmatvec", "vcycle"]
         return dict(zip(keys, v))
+
+    def learning_data(self):
+        """(x [m, nb], y [m, L-1, nb]) training pairs of this context's level-1 elements."""
+        m = self.info["elements"][0]
+        nb = self.opts.block[0] * self.opts.block[1] * self.opts.block[2]
+        L = self.opts.n_eig[0]
+        x = torch.empty((m, nb), dtype=torch.float32, device="cuda")
+        y = torch.empty((m, L - 1, nb), dtype=torch.float32, device="cuda")
+        msmg_learning_data(self.ctx, x, y, self.stream)
+        return x, y
 
     def export_faces(self) -> torch.Tensor:
         out = torch.empty((3,) + self.shape, dtype=torch.float64, device="cuda")

@@ -13,7 +13,9 @@ void set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
 void launch_mixed_copies(msmg_ctx* c, cudaStream_t s);
 void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s);
-int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s);
+int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess);
+int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream_t s);
+bool net_matches(const msmg_ctx* c, const msmg_net* net);
 int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
 int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s);
 int pcg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs, double* const* x,
@@ -22,6 +24,7 @@ int pcg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs
 void apply_vcycle_fp64_out(msmg_ctx* c, cudaStream_t s);
 void prepare_fine_kernels(msmg_ctx* c);
 void prepare_coarse_kernels(msmg_ctx* c);
+int coarse_forms(const msmg_ctx* c);
 
 struct LevelShape {
   int g[kMaxLevels + 1][3];    // element grid of E_l, l = 1 .. nL-1
@@ -228,7 +231,7 @@ static void build_tables(const msmg_ctx* c, const LevelShape& sh, std::vector<st
 }
 
 static int check_flags(msmg_ctx* c, cudaStream_t s) {
-  int h[4];
+  int h[8];
   double d[2];
   MSMG_CUDA_TRY(cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, s));
   MSMG_CUDA_TRY(cudaMemcpyAsync(d, c->dtmp, sizeof(d), cudaMemcpyDeviceToHost, s));
@@ -238,7 +241,38 @@ static int check_flags(msmg_ctx* c, cudaStream_t s) {
   if (h[1] || d[1] != 0.0) return MSMG_ERR_NOT_FACTORIZABLE;
   c->info.eig_residual_max = d[0];
   c->info.eig_iterations_max = h[3];
+  c->info.eig_iterations_total = h[4];
   if (h[2]) return MSMG_ERR_EIG_NOT_CONVERGED;
+  return 0;
+}
+
+// Autotuner: time each result-preserving variant of the V-cycle at batch width R
+// (CUDA events over reps repetitions on the context's own buffers) and keep the
+// fastest for that width class.  Variants give the same bits, so the choice
+// moves only the time.  Clobbers the solve buffers (call between solves).
+static int autotune(msmg_ctx* c, int R, int reps, cudaStream_t s) {
+  const int cls = R > 1 ? 1 : 0;
+  double best = 1e300;
+  int bf = c->tune_fused[cls], bt = c->tune_tail[cls];
+  const int forms = coarse_forms(c);
+  for (int tail = 0; tail < 3; ++tail)
+    for (int v = 0; v < 2; ++v) {
+      if (!((forms >> tail) & 1)) continue;
+      c->tune_fused[cls] = v;
+      c->tune_tail[cls] = tail;
+      double acc[7];
+      int st = time_kernels(c, R, reps, acc, s);
+      if (st) return st;
+      if (acc[6] < best) { best = acc[6]; bf = v; bt = tail; }
+    }
+  c->tune_fused[cls] = bf;
+  c->tune_tail[cls] = bt;
+  c->tuned[cls] = 1;
+  // a captured iteration graph holds the previous variant
+  if (c->graph_state == 1) {
+    cudaGraphExecDestroy(c->iter_graph);
+    c->graph_state = 0;
+  }
   return 0;
 }
 
@@ -317,13 +351,18 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   cudaGetDevice(&c->device);
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
+  // untuned defaults: separate prolongation for single solves, fused for batches
+  c->tune_fused[0] = 0;
+  c->tune_fused[1] = 1;
+  c->tune_tail[0] = c->tune_tail[1] = 2;   // the fused coarse cycle, where the hierarchy allows it
   for (int k = 0; k < 3; ++k) cudaEventCreateWithFlags(&c->poll_evs[k], cudaEventDisableTiming);
   *out = c;
   // pinned host mirrors of the PCG scalars (latest + two in-flight chunks),
   // residual norms and restart mask
   MSMG_CUDA_TRY(cudaMallocHost(&c->hsc, (size_t)3 * n_rhs * sizeof(PcgScalars)));
   MSMG_CUDA_TRY(cudaMallocHost(&c->hres, (size_t)2 * n_rhs * sizeof(double)));
-  MSMG_CUDA_TRY(cudaMallocHost(&c->hmask, (size_t)n_rhs * sizeof(int)));
+  MSMG_CUDA_TRY(cudaMallocHost(&c->hmask, (size_t)(n_rhs + 1) * sizeof(int)));
+  c->hmask[n_rhs] = 0;
   cudaEventRecord(c->ev0, s);
   LevelShape sh;
   shapes(grid, opts, sh);
@@ -355,7 +394,23 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   cudaEventCreate(&e_eig0);
   cudaEventCreate(&e_eig1);
   cudaEventRecord(e_eig0, s);
-  st = (c->fine.nb <= 96) ? launch_level1_eigen(c, s) : launch_level1_chfsi(c, s);
+  if (c->fine.nb <= 96) {
+    st = launch_level1_eigen(c, s);
+  } else {
+    // learned warm start: features and guesses in the (still unused) solve
+    // buffers, which span at least 56 n bytes
+    const float* guess = nullptr;
+    const msmg_net* net = opts->warm_start;
+    if (net && net_matches(c, net) && (size_t)4 * c->fine.L * c->n <= (size_t)56 * c->n) {
+      float* x = reinterpret_cast<float*>(c->sb.b);
+      float* g = x + c->n;
+      st = net_guesses(c, net, x, g, s);
+      if (st) return st;
+      guess = g;
+      c->info.warm_started = 1;
+    }
+    st = launch_level1_chfsi(c, s, guess);
+  }
   cudaEventRecord(e_eig1, s);
   if (st) return st;
   st = build_from_bases(c, false, s);
@@ -375,6 +430,15 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   I.setup_ms = ms;
   I.eig_ms = ems;
   I.workspace_bytes = (int64_t)workspace_bytes;
+  if (opts->autotune && fl >= 0) {
+    int st2 = autotune(c, 1, 3, s);
+    if (!st2 && c->max_rhs > 1) st2 = autotune(c, c->max_rhs, 3, s);
+    if (st2) return st2;
+  }
+  for (int k = 0; k < 2; ++k) {
+    I.tuning[k] = c->tune_fused[k];
+    I.tuning[2 + k] = c->tune_tail[k];
+  }
   return fl;
 }
 
@@ -413,6 +477,36 @@ int msmg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rh
 }
 
 int msmg_max_batch_rhs(const msmg_ctx* c) { return c ? c->max_rhs : 0; }
+
+int msmg_set_tuning(msmg_ctx* c, const int* tuning) {
+  if (!c || !tuning) return MSMG_ERR_INVALID_ARG;
+  for (int k = 0; k < 2; ++k)
+    if (tuning[k] != 0 && tuning[k] != 1) return MSMG_ERR_INVALID_ARG;
+  for (int k = 2; k < 4; ++k) {
+    if (tuning[k] < 0 || tuning[k] > 2) return MSMG_ERR_INVALID_ARG;
+    if (!((coarse_forms(c) >> tuning[k]) & 1)) return MSMG_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < 2; ++k) {
+    c->tune_fused[k] = tuning[k];
+    c->tune_tail[k] = tuning[2 + k];
+  }
+  for (int k = 0; k < 4; ++k) c->info.tuning[k] = tuning[k];
+  if (c->graph_state == 1) {
+    cudaGraphExecDestroy(c->iter_graph);
+    c->graph_state = 0;
+  }
+  return 0;
+}
+
+int msmg_autotune(msmg_ctx* c, int n_rhs, int reps, msmg_stream stream) {
+  if (!c || n_rhs < 1 || n_rhs > c->max_rhs || reps < 1) return MSMG_ERR_INVALID_ARG;
+  const int st = autotune(c, n_rhs, reps, reinterpret_cast<cudaStream_t>(stream));
+  for (int k = 0; k < 2; ++k) {
+    c->info.tuning[k] = c->tune_fused[k];
+    c->info.tuning[2 + k] = c->tune_tail[k];
+  }
+  return st;
+}
 
 int msmg_apply_A(msmg_ctx* c, const double* p, double* q, msmg_stream stream) {
   if (!c || !p || !q) return MSMG_ERR_INVALID_ARG;

@@ -17,6 +17,11 @@
 // K x K projected matrix; stop when the L wanted Ritz pairs have residual
 // ||A~ y - theta y||_2 <= tol.  K - L guard vectors keep the convergence rate
 // set by the gap to theta_{K-1}, not by clusters at the L-th eigenvalue.
+//
+// Starting block: the constant S^{1/2} 1 and separable cosine modes ranked by
+// frequency, or, with a learned warm start, the network's guesses for
+// eigenvectors 1 .. L-1 in place of the first cosines (the guard vectors stay
+// cosines).  The stopping test is the same either way.
 #include "msmg_internal.cuh"
 #include "reduce.cuh"
 #include "linalg_small.cuh"
@@ -68,7 +73,8 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c) 
 
 __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__ T, const double* __restrict__ S, int64_t n, int bx, int by,
                                int bz, int64_t m, int L, int K, int mdeg, int max_iter, double tol,
-                               double* __restrict__ Phi, double* __restrict__ lam, double* stats, int* flags) {
+                               const float* __restrict__ guess, double* __restrict__ Phi, double* __restrict__ lam,
+                               double* stats, int* flags) {
   extern __shared__ double sm[];
   const int nb = bx * by * bz, bxy = bx * by;
   double* g = sm;
@@ -155,6 +161,10 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
   const double PI = 3.141592653589793238462643383279502884;
   if (act) {
     for (int q = 0; q < K; ++q) {
+      if (guess && q >= 1 && q < L) {
+        X[q * nb + c] = (double)guess[((size_t)e * (L - 1) + (q - 1)) * nb + c];
+        continue;
+      }
       const double v = cos(PI * modes[3 * q] * (lx + 0.5) / bx) * cos(PI * modes[3 * q + 1] * (ly + 0.5) / by) *
                        cos(PI * modes[3 * q + 2] * (lz + 0.5) / bz);
       X[q * nb + c] = sq * v;
@@ -291,11 +301,12 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
   if (threadIdx.x == 0) {
     atomic_max_pos(&stats[0], rmax);
     atomicMax(&flags[3], it);
+    atomicAdd(&flags[4], it);
     if (!(rmax <= tol)) atomicExch(&flags[2], 1);
   }
 }
 
-int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s) {
+int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess) {
   FineLevel& f = c->fine;
   const int L = f.L;
   int guard = L / 2 > 4 ? L / 2 : 4;
@@ -310,8 +321,8 @@ int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s) {
                         sizeof(double) + (size_t)(kKMax + 2 + kKMax + 3 * kKMax) * sizeof(int) + 64;
   cudaFuncSetAttribute(k_eig_l1_chfsi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const unsigned thr = (unsigned)((f.nb + 31) / 32 * 32);
-  k_eig_l1_chfsi<<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, L, K, 10, max_iter, tol, f.Phi,
-                                                f.lam, c->dtmp, c->flags);
+  k_eig_l1_chfsi<<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, L, K, 10, max_iter, tol, guess,
+                                                f.Phi, f.lam, c->dtmp, c->flags);
   return 0;
 }
 

@@ -249,28 +249,6 @@ __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, c
   }
 }
 
-// ============================================================== V-cycle, fine level
-
-// Prolongation: u_c += sum_k Phi[e][k][c] ec[e][k]  (Algorithm 1, R_c^T e_c).
-// The coarse correction arrives in the V-cycle precision (EC), so the FP64
-// pipe is not touched per cell in the mixed form.
-template <typename V, typename BT, typename EC>
-__global__ void k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L, const EC* __restrict__ ec, int64_t n,
-                          int64_t nc, int nb, const PcgScalars* sc, int R) {
-  const BatchIdx bi = batch_idx(R);
-  if (sc) sc += bi.r;
-  if (sc && sc->done) return;
-  u += (int64_t)bi.r * n;
-  ec += (int64_t)bi.r * nc;
-  const int64_t i = (int64_t)bi.blk * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t e = i / nb;
-  const int p = (int)(i % nb);
-  V acc = (V)0;
-  for (int k = 0; k < L; ++k) acc += (V)__ldg(Phi + (e * L + k) * nb + p) * (V)__ldg(ec + e * L + k);
-  u[i] += acc;
-}
-
 // ============================================================== host launchers
 
 static inline Geo fine_geo(const msmg_ctx* c) { return make_geo(c->fine.bx, c->fine.by, c->fine.bz); }
@@ -326,17 +304,6 @@ void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s, int 
   k_matvec<false><<<fine_grid(c, g) * R, fine_threads(g), sm, s>>>(p, q, c->fine.T, c->n, g, c->fine.m, c->fine.nbr,
                                                                     c->red, nullptr, R);
 }
-
-// Prolongation on the fine level (Algorithm 1: u += R_1^T e_c); the coarse
-// correction is in the V-cycle precision.
-template <typename V, typename BT>
-void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const V* ec, PcgScalars* sc, cudaStream_t s) {
-  const unsigned grid = (unsigned)((c->n + 255) / 256 * c->sb.R);
-  k_prolong<V, BT, V><<<grid, 256, 0, s>>>((V*)c->sb.vu[1], Phi, c->fine.L, ec, c->n, c->lev[2].n, c->fine.nb, sc,
-                                           c->sb.R);
-}
-template void launch_prolong_fine<float, float>(msmg_ctx*, const float*, const float*, PcgScalars*, cudaStream_t);
-template void launch_prolong_fine<double, double>(msmg_ctx*, const double*, const double*, PcgScalars*, cudaStream_t);
 
 // ---- kernel timing (roofline figures)
 __global__ void k_fill_pattern(double* __restrict__ v, int64_t n, double phase) {

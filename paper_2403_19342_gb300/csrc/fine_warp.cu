@@ -13,13 +13,19 @@
 // with constant geometry (index arithmetic folds to shifts, loops unroll);
 // other shapes use the same code with runtime geometry.
 //
-// One PCG iteration on the fine level is five kernels:
+// One PCG iteration on the fine level is four kernels:
 //   k_pmatvec  p = z + beta p_old (cells and halo), q = A p, reduce p.q -> alpha
 //   k_pre      x += alpha p, r -= alpha q, reduce r.r (convergence), and the
 //              pre-smoothing u = M^{-1} r of Algorithm 1 (from u = 0)
 //   k_restrict r_c = Phi^T (r - A u) per element (Algorithm 1, restriction)
-//   k_prolong  u += Phi e_c (Algorithm 1, prolongation)   [fine.cu]
-//   k_post     z = u + M^{-T} (r - A u), reduce r.z (and z.q for the flexible beta)
+//   k_post     prolongation u' = u + Phi e_c (Algorithm 1) applied to the staged
+//              tile (the element's cells and its face halo, the halo with the
+//              neighbours' bases and coarse coordinates), then the
+//              post-smoothing z = u' + M^{-T} (r - A u'); reduces r.z (and z.q
+//              for the flexible beta)
+// or, as two launches, k_prolong (u += Phi e_c, a thread per cell) and k_post
+// without the prolongation.  Both give the same bits; the context's autotuner
+// picks the faster per batch width.
 //
 // Every kernel also runs R right-hand sides in lockstep (vectors stored n
 // apart, one PcgScalars record and one reduction slice each): CTA b handles
@@ -409,16 +415,169 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_restrict(const V* __restr
   }
 }
 
+// ------------------------------------------------------------------ prolongation
+// Coarse correction (Algorithm 1, R_1^T e_c) added to the staged padded tile:
+// the element's own cells and the face halo (cells of the six neighbours, with
+// the neighbours' bases and coordinates).  Each cell's correction is
+// sum_k Phi[ne][k][c] ec[ne][k], accumulated in the V-cycle precision in k
+// order.  All L basis loads of a group of cells are issued before the first
+// product (L <= kProlongLMax; larger L takes the plain loop).
+constexpr int kProlongLMax = 8;
+
+template <typename V, typename BT>
+__device__ __forceinline__ void w_corr_group(V* ut, const BT* __restrict__ ph, const V (&ev)[kProlongLMax], int L,
+                                             int nb, const int (&src)[4], const int (&dst)[4], int cnt) {
+  BT v[4][kProlongLMax];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k)
+      if (j < cnt && k < L) v[j][k] = __ldg(ph + (size_t)k * nb + src[j]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j >= cnt) continue;
+    V acc = (V)0;
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k)
+      if (k < L) acc += (V)v[j][k] * ev[k];
+    ut[dst[j]] += acc;
+  }
+}
+
+template <typename V, typename BT>
+__device__ __forceinline__ V w_coarse_corr(const BT* __restrict__ ph, const V* __restrict__ en, int L, int nb, int c) {
+  V acc = (V)0;
+  for (int k = 0; k < L; ++k) acc += (V)__ldg(ph + (size_t)k * nb + c) * __ldg(en + k);
+  return acc;
+}
+
+template <typename V, typename BT, typename G>
+__device__ __forceinline__ void w_prolong_tile(V* ut, const BT* __restrict__ Phi, const V* __restrict__ ec, int L,
+                                               int64_t e, const WElem& E, const G& g, int lane) {
+  if (L > kProlongLMax) {
+    const V* en = ec + e * L;
+    const BT* ph = Phi + (size_t)e * L * g.nb;
+    for (int c = lane; c < g.nb; c += 32) {
+      const int lx = c % g.bx, t = c / g.bx;
+      ut[wpad(g, lx, t % g.by, t / g.by)] += w_coarse_corr(ph, en, L, g.nb, c);
+    }
+    for (int f = 0; f < 6; ++f) {
+      const int64_t nbase = E.nb6[f];
+      if (nbase < 0) continue;
+      const int64_t ne = nbase / g.nb;
+      const int d = f >> 1;
+      const bool plus = f & 1;
+      const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
+      for (int h = lane; h < F; h += 32) {
+        int dx, dy, dz, sx, sy, sz;
+        if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
+        else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
+        else { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dy = sy = vv; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
+        ut[wpad(g, dx, dy, dz)] += w_coarse_corr(Phi + (size_t)ne * L * g.nb, ec + ne * L, L, g.nb,
+                                                 sx + g.bx * (sy + g.by * sz));
+      }
+    }
+    return;
+  }
+  V ev[kProlongLMax];
+#pragma unroll
+  for (int k = 0; k < kProlongLMax; ++k) ev[k] = k < L ? ec[e * L + k] : (V)0;
+  {
+    const BT* ph = Phi + (size_t)e * L * g.nb;
+    const int ncl = (g.nb + 31) / 32;
+    for (int i0 = 0; i0 < ncl; i0 += 4) {
+      int src[4], dst[4];
+      int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = lane + 32 * (i0 + j);
+        src[j] = c;
+        dst[j] = 0;
+        if (i0 + j < ncl && c < g.nb) {
+          const int lx = c % g.bx, t = c / g.bx;
+          dst[j] = wpad(g, lx, t % g.by, t / g.by);
+          cnt = j + 1;
+        }
+      }
+      w_corr_group(ut, ph, ev, L, g.nb, src, dst, cnt);
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int64_t nbase = E.nb6[f];
+    if (nbase < 0) continue;
+    const int64_t ne = nbase / g.nb;
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k) ev[k] = k < L ? ec[ne * L + k] : (V)0;
+    const BT* pn = Phi + (size_t)ne * L * g.nb;
+    const int d = f >> 1;
+    const bool plus = f & 1;
+    const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
+    for (int h0 = 0; h0 < F; h0 += 4 * 32) {
+      int src[4], dst[4];
+      int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int h = h0 + lane + 32 * j;
+        src[j] = 0;
+        dst[j] = 0;
+        if (h < F) {
+          int dx, dy, dz, sx, sy, sz;
+          if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
+          else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
+          else { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dy = sy = vv; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
+          src[j] = sx + g.bx * (sy + g.by * sz);
+          dst[j] = wpad(g, dx, dy, dz);
+          cnt = j + 1;
+        }
+      }
+      w_corr_group(ut, pn, ev, L, g.nb, src, dst, cnt);
+    }
+  }
+}
+
+// Separate prolongation: u_c += sum_k Phi[e][k][c] ec[e][k], a thread per cell,
+// same accumulation order as the fused form.
+template <typename V, typename BT, typename G>
+__global__ void __launch_bounds__(256) k_prolong(V* __restrict__ u, const BT* __restrict__ Phi, int L,
+                                                 const V* __restrict__ ec, int64_t n, int64_t nc, G g,
+                                                 const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
+  if (sc && sc->done) return;
+  u += (int64_t)bi.r * n;
+  ec += (int64_t)bi.r * nc;
+  const int64_t i = (int64_t)bi.blk * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = i / g.nb;
+  const int c = (int)(i - e * g.nb);
+  const BT* ph = Phi + (size_t)e * L * g.nb + c;
+  V acc = (V)0;
+  if (L <= kProlongLMax) {
+    BT v[kProlongLMax];
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k)
+      if (k < L) v[k] = __ldg(ph + (size_t)k * g.nb);
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k)
+      if (k < L) acc += (V)v[k] * __ldg(ec + e * L + k);
+  } else {
+    for (int k = 0; k < L; ++k) acc += (V)__ldg(ph + (size_t)k * g.nb) * __ldg(ec + e * L + k);
+  }
+  u[i] += acc;
+}
+
 // ------------------------------------------------------------------ k_post
 // z = u + M^{-1} (f - A u), written in FP64; reductions: r.z and z.q (flexible
 // beta).  f, r and q are loaded into registers before the wavefronts start.
-template <typename V, typename G>
+template <typename V, typename BT, typename G, bool FUSE>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict__ f, const double* __restrict__ r,
                                                             const V* __restrict__ u, const V* __restrict__ T,
-                                                            const V* __restrict__ invd, double* __restrict__ z,
-                                                            const double* __restrict__ qv, int64_t n, G g,
-                                                            int64_t m, const int* __restrict__ nbr, RedSlot red,
-                                                            PcgScalars* sc, int R) {
+                                                            const V* __restrict__ invd, const BT* __restrict__ Phi,
+                                                            const V* __restrict__ ec, int L, int64_t nc,
+                                                            double* __restrict__ z, const double* __restrict__ qv,
+                                                            int64_t n, G g, int64_t m, const int* __restrict__ nbr,
+                                                            RedSlot red, PcgScalars* sc, int R) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -426,6 +585,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
     const int64_t off = (int64_t)bi.r * n;
     f += off; r += off; u += off; z += off;
     if (qv) qv += off;
+    ec += (int64_t)bi.r * nc;
   }
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kC = 16;
@@ -441,22 +601,33 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
     w_cp_padded(s.ut, u + base, g, lane);
     w_cp_halo(s.ut, u, E, g, lane);
     w_stage_T(s, T, invd, n, E, g, lane, true);
-    V fr[kC];
+    cp_async_wait_all();
+    __syncwarp();
+    if (FUSE) {
+      w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
+      __syncwarp();
+    }
+    {
+      V fr[kC];
+#pragma unroll
+      for (int i = 0; i < kC; ++i) {
+        const int c = lane + 32 * i;
+        fr[i] = (i < ncl && c < g.nb) ? __ldg(f + base + c) : (V)0;
+      }
+#pragma unroll
+      for (int i = 0; i < kC; ++i) {
+        const int c = lane + 32 * i;
+        if (i < ncl && c < g.nb) s.y[c] = fr[i] - w_apply_A_s(s, g, c);
+      }
+    }
+    // r and q are needed only after the sweeps: their loads overlap them
     double rr[kC], qq[kC];
 #pragma unroll
     for (int i = 0; i < kC; ++i) {
       const int c = lane + 32 * i;
       const bool in = i < ncl && c < g.nb;
-      fr[i] = in ? __ldg(f + base + c) : (V)0;
       rr[i] = (in && sc) ? __ldg(r + base + c) : 0.0;
       qq[i] = (in && qv) ? __ldg(qv + base + c) : 0.0;
-    }
-    cp_async_wait_all();
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < kC; ++i) {
-      const int c = lane + 32 * i;
-      if (i < ncl && c < g.nb) s.y[c] = fr[i] - w_apply_A_s(s, g, c);
     }
     __syncwarp();
     w_ic0_s(s, g, lane);
@@ -478,6 +649,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
     w_stage_T(s, T, invd, n, E, g, lane, true);
     cp_async_wait_all();
     __syncwarp();
+    if (FUSE) {
+      w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
+      __syncwarp();
+    }
     for (int c = lane; c < g.nb; c += 32) s.y[c] = __ldg(f + base + c) - w_apply_A_s(s, g, c);
     __syncwarp();
     w_ic0_s(s, g, lane);
@@ -528,60 +703,102 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __r
     const double beta = sc->beta;
     const WElem E = w_elem(e, nbr, g);
     const int64_t base = E.base;
-#pragma unroll 4
-    for (int i = 0; i < (g.nb + 31) / 32; ++i) {
-      const int c = lane + 32 * i;
-      if (c >= g.nb) continue;
-      const double pv = fma(beta, pold[base + c], z[base + c]);
-      const int lx = c % g.bx, t = c / g.bx;
-      ut[wpad(g, lx, t % g.by, t / g.by)] = pv;
-      pnew[base + c] = pv;
+    constexpr int kC = 16;                       // cells per lane (8^3 elements)
+    const int ncl = (g.nb + 31) / 32;
+    // p on the element: every load issued before the first use
+    for (int i0 = 0; i0 < ncl; i0 += kC) {
+      double zz[kC], po[kC];
+#pragma unroll
+      for (int i = 0; i < kC; ++i) {
+        const int c = lane + 32 * (i0 + i);
+        const bool in = i0 + i < ncl && c < g.nb;
+        zz[i] = in ? __ldg(z + base + c) : 0.0;
+        po[i] = in ? __ldg(pold + base + c) : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < kC; ++i) {
+        const int c = lane + 32 * (i0 + i);
+        if (!(i0 + i < ncl && c < g.nb)) continue;
+        const double pv = fma(beta, po[i], zz[i]);
+        const int lx = c % g.bx, t = c / g.bx;
+        ut[wpad(g, lx, t % g.by, t / g.by)] = pv;
+        pnew[base + c] = pv;
+      }
     }
+    // p on the face halo, recomputed from the neighbours' z and p_old
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1;
       const bool plus = f & 1;
       const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
       const int64_t nb = E.nb6[f];
-      for (int h = lane; h < F; h += 32) {
-        int dx, dy, dz, sx, sy, sz;
-        if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
-        else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
-        else { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dy = sy = vv; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
-        double val = 0.0;
-        if (nb >= 0) {
-          const int64_t src = nb + sx + g.bx * (sy + g.by * sz);
-          val = fma(beta, pold[src], z[src]);
+      for (int h0 = 0; h0 < F; h0 += 64) {
+        double zv[2], pv[2];
+        int dst[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int h = h0 + lane + 32 * j;
+          zv[j] = 0.0;
+          pv[j] = 0.0;
+          dst[j] = -1;
+          if (h < F) {
+            int dx, dy, dz, sx, sy, sz;
+            if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
+            else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
+            else { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dy = sy = vv; dz = plus ? g.bz : -1; sz = plus ? 0 : g.bz - 1; }
+            dst[j] = wpad(g, dx, dy, dz);
+            if (nb >= 0) {
+              const int64_t src = nb + sx + g.bx * (sy + g.by * sz);
+              zv[j] = __ldg(z + src);
+              pv[j] = __ldg(pold + src);
+            }
+          }
         }
-        ut[wpad(g, dx, dy, dz)] = val;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          if (dst[j] >= 0) ut[dst[j]] = nb >= 0 ? fma(beta, pv[j], zv[j]) : 0.0;
       }
     }
     __syncwarp();
     const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
-#pragma unroll 2
-    for (int i = 0; i < (g.nb + 31) / 32; ++i) {
-      const int c = lane + 32 * i;
-      if (c >= g.nb) continue;
-      const int lx = c % g.bx, t = c / g.bx, ly = t % g.by, lz = t / g.by;
-      const int pc = wpad(g, lx, ly, lz);
-      const double pcv = ut[pc];
-      // -d face coefficients: in-element, or held by the -d neighbour
-      const double mx = lx > 0 ? __ldg(T + base + c - 1)
-                                : (E.nb6[0] >= 0 ? __ldg(T + E.nb6[0] + c + g.bx - 1) : 0.0);
-      const double my = ly > 0 ? __ldg(T + n + base + c - g.bx)
-                                : (E.nb6[2] >= 0 ? __ldg(T + n + E.nb6[2] + c + g.bx * (g.by - 1)) : 0.0);
-      const double mz = lz > 0 ? __ldg(T + 2 * n + base + c - g.bx * g.by)
-                                : (E.nb6[4] >= 0 ? __ldg(T + 2 * n + E.nb6[4] + c + g.bx * g.by * (g.bz - 1)) : 0.0);
-      // (A p)_c = D_c p_c - sum_f T_f p_nb: one multiply and six FMAs in FP64
-      double a = __ldg(Dg + base + c) * pcv;
-      a = fma(-__ldg(T + base + c), ut[pc + 1], a);
-      a = fma(-mx, ut[pc - 1], a);
-      a = fma(-__ldg(T + n + base + c), ut[pc + sy], a);
-      a = fma(-my, ut[pc - sy], a);
-      a = fma(-__ldg(T + 2 * n + base + c), ut[pc + sz], a);
-      a = fma(-mz, ut[pc - sz], a);
-      q[base + c] = a;
-      acc = fma(a, pcv, acc);
+    // q = A p: coefficients of a group of 4 cells loaded before the products
+    for (int i0 = 0; i0 < ncl; i0 += 4) {
+      double t0[4], t1[4], t2[4], dg[4], mx[4], my[4], mz[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = lane + 32 * (i0 + j);
+        t0[j] = t1[j] = t2[j] = dg[j] = mx[j] = my[j] = mz[j] = 0.0;
+        if (!(i0 + j < ncl && c < g.nb)) continue;
+        const int lx = c % g.bx, t = c / g.bx, ly = t % g.by, lz = t / g.by;
+        t0[j] = __ldg(T + base + c);
+        t1[j] = __ldg(T + n + base + c);
+        t2[j] = __ldg(T + 2 * n + base + c);
+        dg[j] = __ldg(Dg + base + c);
+        // -d face coefficients: in-element, or held by the -d neighbour
+        mx[j] = lx > 0 ? __ldg(T + base + c - 1) : (E.nb6[0] >= 0 ? __ldg(T + E.nb6[0] + c + g.bx - 1) : 0.0);
+        my[j] = ly > 0 ? __ldg(T + n + base + c - g.bx)
+                       : (E.nb6[2] >= 0 ? __ldg(T + n + E.nb6[2] + c + g.bx * (g.by - 1)) : 0.0);
+        mz[j] = lz > 0 ? __ldg(T + 2 * n + base + c - g.bx * g.by)
+                       : (E.nb6[4] >= 0 ? __ldg(T + 2 * n + E.nb6[4] + c + g.bx * g.by * (g.bz - 1)) : 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = lane + 32 * (i0 + j);
+        if (!(i0 + j < ncl && c < g.nb)) continue;
+        const int lx = c % g.bx, t = c / g.bx, ly = t % g.by, lz = t / g.by;
+        const int pc = wpad(g, lx, ly, lz);
+        const double pcv = ut[pc];
+        // (A p)_c = D_c p_c - sum_f T_f p_nb: one multiply and six FMAs in FP64
+        double a = dg[j] * pcv;
+        a = fma(-t0[j], ut[pc + 1], a);
+        a = fma(-mx[j], ut[pc - 1], a);
+        a = fma(-t1[j], ut[pc + sy], a);
+        a = fma(-my[j], ut[pc - sy], a);
+        a = fma(-t2[j], ut[pc + sz], a);
+        a = fma(-mz[j], ut[pc - sz], a);
+        q[base + c] = a;
+        acc = fma(a, pcv, acc);
+      }
     }
   }
   double v[1] = {acc};
@@ -640,12 +857,25 @@ static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cud
 }
 
 template <typename V, typename BT, typename G>
-static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const double* qv, PcgScalars* sc, cudaStream_t s,
-                   const G& g) {
+static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, const double* qv, PcgScalars* sc,
+                   cudaStream_t s, const G& g, bool fuse) {
   SolveBuffers& B = c->sb;
-  k_post<V, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>((const V*)B.rv, B.r, (const V*)B.vu[1],
-                                                                             o.T, o.invd, B.z, qv, c->n, g, c->fine.m,
-                                                                             c->fine.nbr, c->red, sc, B.R);
+  if (fuse)
+    k_post<V, BT, G, true><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+        (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
+        c->fine.m, c->fine.nbr, c->red, sc, B.R);
+  else
+    k_post<V, BT, G, false><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+        (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
+        c->fine.m, c->fine.nbr, c->red, sc, B.R);
+}
+
+template <typename V, typename BT, typename G>
+static void prolong_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, PcgScalars* sc, cudaStream_t s,
+                      const G& g) {
+  SolveBuffers& B = c->sb;
+  const unsigned grid = (unsigned)((c->n + 255) / 256 * B.R);
+  k_prolong<V, BT, G><<<grid, 256, 0, s>>>((V*)B.vu[1], o.Phi, c->fine.L, ec, c->n, c->lev[2].n, g, sc, B.R);
 }
 
 template <typename G>
@@ -655,8 +885,6 @@ static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s, const G& g) {
                                                                       c->n, g, c->fine.m, c->fine.nbr, c->red, sc, B.R);
 }
 
-template <typename V, typename BT>
-void launch_prolong_fine(msmg_ctx* c, const BT* Phi, const V* ec, PcgScalars* sc, cudaStream_t s);
 
 // Shared-memory limits of the fine-level kernels, set once per context (never
 // during stream capture).
@@ -665,7 +893,8 @@ static void prepare_t(const G& g) {
   const int smv = (int)wsmem(g, sizeof(V)), smd = (int)wsmem_p(g);
   cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
-  cudaFuncSetAttribute(k_post<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+  cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+  cudaFuncSetAttribute(k_post<V, BT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
 }
 
@@ -692,9 +921,11 @@ static void vcycle_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, const dou
     if (ev) cudaEventRecord(ev[2], s);
     const V* ec = (const V*)coarse_cycle(c, 2, sc, s);
     if (ev) cudaEventRecord(ev[3], s);
-    launch_prolong_fine<V, BT>(c, o.Phi, ec, sc, s);
+    // fused: the prolongation is part of k_post and the [3, 4] interval stays empty
+    const bool fuse = c->tune_fused[c->sb.R > 1 ? 1 : 0] != 0;
+    if (!fuse) prolong_t<V, BT>(c, o, ec, sc, s, g);
     if (ev) cudaEventRecord(ev[4], s);
-    post_t<V, BT>(c, o, qv, sc, s, g);
+    post_t<V, BT>(c, o, ec, qv, sc, s, g, fuse);
     if (ev) cudaEventRecord(ev[5], s);
   });
 }

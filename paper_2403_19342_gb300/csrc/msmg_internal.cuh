@@ -195,6 +195,17 @@ struct msmg_ctx {
   int* hmask;                                   // pinned host restart mask [max_rhs]
   cudaEvent_t poll_evs[3];                      // PCG polls: two in-flight chunks, exit checks
   cudaStream_t run_stream;                      // per-context stream of batched solves
+  // autotuned variants (result-preserving), index 0: batch width 1, 1: wider batches
+  int tune_fused[2];                            // prolongation inside k_post (1) or separate (0)
+  int tune_tail[2];                             // coarse cycle: per level (0), cluster tail (1), one grid (2)
+  int tuned[2];                                 // set once measured
+  int tail_l0;                                  // first level of the cluster tail (0: none)
+  int tail_cs;                                  // CTAs per cluster
+  int tail_lt;                                  // compile-time L of the tail levels (0: runtime)
+  size_t tail_smem;
+  int coop_grid;                                // CTAs of the cooperative coarse cycle (0: unavailable)
+  int coop_lt;
+  size_t coop_smem;
 };
 
 namespace msmg {

@@ -1,0 +1,569 @@
+// Learned warm start for the level-1 local eigenproblems (Eq. (spepb)): a
+// multilayer perceptron maps an element's standardised log-permeability patch
+// to guesses for its eigenvectors 1 .. L-1 in the symmetric form
+// y = S^{1/2} phi (eigenvector 0, the constant, is known exactly).  The guesses
+// seed the subspace iteration, which still runs to the same eigen-residual
+// tolerance, so the preconditioner is unchanged; only the set-up time moves.
+//
+// Network: x (n_in) -> relu(x W1 + b1) (h1) -> relu(. W2 + b2) (h2) -> o = . W3 + b3
+// (n_vec * n_in) -> y_k = w * o_k.  The fixed output weighting
+// w_c = sqrt(S_c / sum S), recovered from the input (S_c is proportional to
+// exp(8 x_c)), makes the network predict the eigenvectors phi, which vary
+// slowly across permeability jumps, while its output y = S^{1/2} phi stays in
+// the symmetric form.  Weights are kept as FP32 masters (training, Adam) and
+// BF16 copies that every product reads; activations and accumulation are FP32.
+//
+// Loss per sample and output vector k (sign-invariant: an eigenvector is only
+// defined up to sign):  l = ||p||^2 + ||t||^2 - 2 |p . t|,  the smaller of
+// ||p - t||^2 and ||p + t||^2;  the batch loss is the mean over samples and
+// vectors.
+//
+// All kernels are deterministic (no atomics): a training run is reproducible.
+#include "msmg_internal.cuh"
+#include <cuda_bf16.h>
+#include <new>
+
+struct msmg_net {
+  msmg_net_desc d;
+  int n_out;                    // n_vec * n_in
+  int64_t n_param;              // total parameters
+  // parameter blocks inside one array: W1 [n_in][h1], b1, W2 [h1][h2], b2, W3 [h2][n_out], b3
+  int64_t off_w[3], off_b[3];
+  float* w32;                   // FP32 masters
+  __nv_bfloat16* w16;           // BF16 copies (read by the products)
+  float* grad;                  // gradients, same layout
+  float* adam_m;
+  float* adam_v;
+  float* h1;                    // [batch_max][h1]
+  float* h2;                    // [batch_max][h2]
+  float* out;                   // [batch_max][n_out]
+  float* d_out;                 // [batch_max][n_out]
+  float* d_h2;                  // [batch_max][h2]
+  float* d_h1;                  // [batch_max][h1]
+  float* wgt;                   // [batch_max][n_in] output weighting of the current batch
+  float* loss;                  // [batch_max * n_vec + 32]
+  int64_t step;
+};
+
+namespace msmg {
+
+// ------------------------------------------------------------------ GEMM
+// C[M][N] = op(A)[M][K] op(B)[K][N] (+ bias[N]) (ReLU), FP32 accumulation.
+//   A element (m, k): TA ? A[k * lda + m] : A[m * lda + k]
+//   B element (k, n): TB ? B[n * ldb + k] : B[k * ldb + n]
+// 64 x 64 output tile per CTA of 256 threads, 4 x 4 outputs per thread, K in
+// steps of 16 through shared memory.
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename TAe, typename TBe, bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(256) k_gemm(const TAe* __restrict__ A, int lda, const TBe* __restrict__ B, int ldb,
+                                              float* __restrict__ C, int ldc, const float* __restrict__ bias, int M,
+                                              int N, int K) {
+  __shared__ float As[kBK][kBM + 4];
+  __shared__ float Bs[kBK][kBN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kBK) {
+    // 1024 values of each tile, 4 per thread
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + 256 * q;
+      // A tile: (mm, kk), mm < 64, kk < 16
+      int mm, kk;
+      if (TA) { mm = idx % kBM; kk = idx / kBM; }     // consecutive threads along m (contiguous in A^T layout)
+      else { kk = idx % kBK; mm = idx / kBK; }        // consecutive threads along k
+      const int gm = m0 + mm, gk = k0 + kk;
+      float va = 0.f;
+      if (gm < M && gk < K) va = to_f(TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]);
+      As[kk][mm] = va;
+      // B tile: (kk, nn)
+      int nn;
+      if (TB) { kk = idx % kBK; nn = idx / kBK; }
+      else { nn = idx % kBN; kk = idx / kBN; }
+      const int gn = n0 + nn;
+      const int gk2 = k0 + kk;
+      float vb = 0.f;
+      if (gn < N && gk2 < K) vb = to_f(TB ? B[(int64_t)gn * ldb + gk2] : B[(int64_t)gk2 * ldb + gn]);
+      Bs[kk][nn] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      float v = acc[i][j];
+      if (EPI >= 1) v += bias[gn];
+      if (EPI == 2) v = v > 0.f ? v : 0.f;
+      C[(int64_t)gm * ldc + gn] = v;
+    }
+  }
+}
+
+template <typename TAe, typename TBe, bool TA, bool TB, int EPI>
+static void gemm(const TAe* A, int lda, const TBe* B, int ldb, float* C, int ldc, const float* bias, int M, int N,
+                 int K, cudaStream_t s) {
+  dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
+  k_gemm<TAe, TBe, TA, TB, EPI><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, bias, M, N, K);
+}
+
+// ------------------------------------------------------------------ output weighting
+// w[b][c] = exp(4 (x_c - max x)) / sqrt(sum_c exp(8 (x_c - max x))) = sqrt(S_c / sum S)
+// for x_c = (log S_c - mean) / 8; one CTA per row.
+__global__ void k_out_weight(const float* __restrict__ x, int n_in, float* __restrict__ w) {
+  const int64_t b = blockIdx.x;
+  const float* xr = x + b * n_in;
+  __shared__ float red[32];
+  __shared__ float bc;
+  float mx = -3.0e38f;
+  for (int c = threadIdx.x; c < n_in; c += blockDim.x) mx = fmaxf(mx, xr[c]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = red[0];
+    for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i) m = fmaxf(m, red[i]);
+    bc = m;
+  }
+  __syncthreads();
+  mx = bc;
+  float acc = 0.f;
+  for (int c = threadIdx.x; c < n_in; c += blockDim.x) acc += expf(8.f * (xr[c] - mx));
+  acc = warp_sum_t(acc);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) t += red[i];
+    bc = rsqrtf(t);
+  }
+  __syncthreads();
+  const float inv = bc;
+  for (int c = threadIdx.x; c < n_in; c += blockDim.x) w[b * n_in + c] = expf(4.f * (xr[c] - mx)) * inv;
+}
+
+// y[b][k][c] *= w[b][c]  (forward: y = w o; backward: d o = w d y)
+__global__ void k_apply_weight(float* __restrict__ y, const float* __restrict__ w, int batch, int n_vec, int n_in) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)batch * n_vec * n_in;
+  if (i >= total) return;
+  const int c = (int)(i % n_in);
+  const int64_t b = i / ((int64_t)n_vec * n_in);
+  y[i] *= w[b * n_in + c];
+}
+
+// ------------------------------------------------------------------ elementwise
+// d_h *= (h > 0)   (ReLU derivative from the post-activation value)
+__global__ void k_relu_back(float* __restrict__ dh, const float* __restrict__ h, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !(h[i] > 0.f)) dh[i] = 0.f;
+}
+
+// db[n] = sum_b d[b][n]  (thread per column, rows in order)
+__global__ void k_colsum(const float* __restrict__ d, int rows, int cols, float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= cols) return;
+  float acc = 0.f;
+  for (int b = 0; b < rows; ++b) acc += d[(int64_t)b * cols + n];
+  db[n] = acc;
+}
+
+// Sign-invariant loss and its gradient; one warp per (sample, vector).
+//   loss[b * n_vec + k] = ||p||^2 + ||t||^2 - 2 |p.t|
+//   dp = 2 (p - sign(p.t) t) * scale
+__global__ void k_loss(const float* __restrict__ out, const float* __restrict__ target, int batch, int n_vec, int n_in,
+                       float scale, float* __restrict__ loss, float* __restrict__ d_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= (int64_t)batch * n_vec) return;
+  const float* p = out + w * n_in;
+  const float* t = target + w * n_in;
+  float pt = 0.f, pp = 0.f, tt = 0.f;
+  for (int i = lane; i < n_in; i += 32) {
+    const float a = p[i], b = t[i];
+    pt = fmaf(a, b, pt);
+    pp = fmaf(a, a, pp);
+    tt = fmaf(b, b, tt);
+  }
+  pt = warp_sum_t(pt);
+  pp = warp_sum_t(pp);
+  tt = warp_sum_t(tt);
+  const float sg = pt >= 0.f ? 1.f : -1.f;
+  if (lane == 0) loss[w] = pp + tt - 2.f * fabsf(pt);
+  if (d_out) {
+    float* dp = d_out + w * n_in;
+    for (int i = lane; i < n_in; i += 32) dp[i] = 2.f * scale * (p[i] - sg * t[i]);
+  }
+}
+
+// total = sum of n values, in order, one thread (n is batch * n_vec, small)
+__global__ void k_sum_in_order(const float* __restrict__ v, int n, float* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) acc += v[i];
+  *out = (float)acc;
+}
+
+// Adam (Kingma and Ba, 2015) on the FP32 masters; refresh the BF16 copies.
+__global__ void k_adam(float* __restrict__ w, __nv_bfloat16* __restrict__ w16, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, int64_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  w16[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16(a[i]);
+}
+
+// Deterministic initial weights: uniform(-a, a), a = sqrt(6 / fan_in), from a
+// counter-based hash of (seed, index) (the splitmix64 finaliser); biases zero.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void k_init_uniform(float* __restrict__ w, int64_t n, uint64_t seed, float a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t h = splitmix64(seed ^ splitmix64((uint64_t)i));
+  const float u = (float)((h >> 40) * (1.0 / 16777216.0));   // [0, 1)
+  w[i] = a * (2.f * u - 1.f);
+}
+
+static inline unsigned g256(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// ------------------------------------------------------------------ passes
+// forward for `batch` rows of x; output in net->out
+static void net_forward(msmg_net* t, const float* x, int batch, cudaStream_t s) {
+  const msmg_net_desc& d = t->d;
+  const int h1 = d.hidden[0], h2 = d.hidden[1], no = t->n_out;
+  gemm<float, __nv_bfloat16, false, false, 2>(x, d.n_in, t->w16 + t->off_w[0], h1, t->h1, h1, t->w32 + t->off_b[0],
+                                              batch, h1, d.n_in, s);
+  gemm<float, __nv_bfloat16, false, false, 2>(t->h1, h1, t->w16 + t->off_w[1], h2, t->h2, h2, t->w32 + t->off_b[1],
+                                              batch, h2, h1, s);
+  gemm<float, __nv_bfloat16, false, false, 1>(t->h2, h2, t->w16 + t->off_w[2], no, t->out, no, t->w32 + t->off_b[2],
+                                              batch, no, h2, s);
+  k_out_weight<<<(unsigned)batch, 128, 0, s>>>(x, d.n_in, t->wgt);
+  k_apply_weight<<<g256((int64_t)batch * no), 256, 0, s>>>(t->out, t->wgt, batch, d.n_vec, d.n_in);
+}
+
+// loss and gradients for `batch` rows (forward included); loss total in t->loss[batch * n_vec]
+static void net_backward(msmg_net* t, const float* x, const float* target, int batch, cudaStream_t s) {
+  const msmg_net_desc& d = t->d;
+  const int h1 = d.hidden[0], h2 = d.hidden[1], no = t->n_out;
+  net_forward(t, x, batch, s);
+  const int nl = batch * d.n_vec;
+  const float scale = 1.f / (float)nl;
+  k_loss<<<(unsigned)(((int64_t)nl * 32 + 255) / 256), 256, 0, s>>>(t->out, target, batch, d.n_vec, d.n_in, scale,
+                                                                   t->loss, t->d_out);
+  k_sum_in_order<<<1, 32, 0, s>>>(t->loss, nl, t->loss + nl);
+  k_apply_weight<<<g256((int64_t)batch * no), 256, 0, s>>>(t->d_out, t->wgt, batch, d.n_vec, d.n_in);
+  float* g = t->grad;
+  // layer 3: dW3 = h2^T d_out, db3, d_h2 = d_out W3^T (relu mask)
+  gemm<float, float, true, false, 0>(t->h2, h2, t->d_out, no, g + t->off_w[2], no, nullptr, h2, no, batch, s);
+  k_colsum<<<g256(no), 256, 0, s>>>(t->d_out, batch, no, g + t->off_b[2]);
+  gemm<float, __nv_bfloat16, false, true, 0>(t->d_out, no, t->w16 + t->off_w[2], no, t->d_h2, h2, nullptr, batch, h2,
+                                             no, s);
+  k_relu_back<<<g256((int64_t)batch * h2), 256, 0, s>>>(t->d_h2, t->h2, (int64_t)batch * h2);
+  // layer 2
+  gemm<float, float, true, false, 0>(t->h1, h1, t->d_h2, h2, g + t->off_w[1], h2, nullptr, h1, h2, batch, s);
+  k_colsum<<<g256(h2), 256, 0, s>>>(t->d_h2, batch, h2, g + t->off_b[1]);
+  gemm<float, __nv_bfloat16, false, true, 0>(t->d_h2, h2, t->w16 + t->off_w[1], h2, t->d_h1, h1, nullptr, batch, h1,
+                                             h2, s);
+  k_relu_back<<<g256((int64_t)batch * h1), 256, 0, s>>>(t->d_h1, t->h1, (int64_t)batch * h1);
+  // layer 1
+  gemm<float, float, true, false, 0>(x, d.n_in, t->d_h1, h1, g + t->off_w[0], h1, nullptr, d.n_in, h1, batch, s);
+  k_colsum<<<g256(h1), 256, 0, s>>>(t->d_h1, batch, h1, g + t->off_b[0]);
+}
+
+}  // namespace msmg
+
+using namespace msmg;
+
+static int64_t net_layout(const msmg_net_desc* d, int64_t off_w[3], int64_t off_b[3]) {
+  const int n_out = d->n_vec * d->n_in;
+  const int64_t dims[4] = {d->n_in, d->hidden[0], d->hidden[1], n_out};
+  int64_t o = 0;
+  for (int l = 0; l < 3; ++l) {
+    off_w[l] = o;
+    o += dims[l] * dims[l + 1];
+    o = (o + 63) / 64 * 64;
+    off_b[l] = o;
+    o += dims[l + 1];
+    o = (o + 63) / 64 * 64;
+  }
+  return o;
+}
+
+static bool desc_ok(const msmg_net_desc* d) {
+  return d && d->n_in >= 1 && d->n_in <= 4096 && d->hidden[0] >= 1 && d->hidden[1] >= 1 && d->hidden[0] <= 16384 &&
+         d->hidden[1] <= 16384 && d->n_vec >= 1 && d->n_vec <= 64 && d->batch_max >= 1 && d->batch_max <= 1 << 20;
+}
+
+static int64_t net_carve(const msmg_net_desc* d, Arena& ar, msmg_net* t) {
+  int64_t ow[3], ob[3];
+  const int64_t np = net_layout(d, ow, ob);
+  const int no = d->n_vec * d->n_in;
+  const int64_t B = d->batch_max;
+  float* w32 = ar.take<float>(np);
+  __nv_bfloat16* w16 = ar.take<__nv_bfloat16>(np);
+  float* grad = ar.take<float>(np);
+  float* am = ar.take<float>(np);
+  float* av = ar.take<float>(np);
+  float* h1 = ar.take<float>(B * d->hidden[0]);
+  float* h2 = ar.take<float>(B * d->hidden[1]);
+  float* out = ar.take<float>(B * no);
+  float* dout = ar.take<float>(B * no);
+  float* dh2 = ar.take<float>(B * d->hidden[1]);
+  float* dh1 = ar.take<float>(B * d->hidden[0]);
+  float* loss = ar.take<float>(B * d->n_vec + 32);
+  float* wgt = ar.take<float>(B * d->n_in);
+  if (t) {
+    t->d = *d;
+    t->n_out = no;
+    t->n_param = np;
+    for (int l = 0; l < 3; ++l) { t->off_w[l] = ow[l]; t->off_b[l] = ob[l]; }
+    t->w32 = w32; t->w16 = w16; t->grad = grad; t->adam_m = am; t->adam_v = av;
+    t->h1 = h1; t->h2 = h2; t->out = out; t->d_out = dout; t->d_h2 = dh2; t->d_h1 = dh1; t->loss = loss;
+    t->wgt = wgt;
+    t->step = 0;
+  }
+  return np;
+}
+
+// --------------------------------------------------------------- set-up integration
+namespace msmg {
+
+// x[e][c] = clamp(log S_c - mean_e log S, -20, 20) / 8: the element's
+// log-permeability pattern up to a constant factor (for isotropic kappa,
+// log S = log kappa + const), the scale-free input of the network.
+// Output row: the element itself, or its lexicographic index when lex_of_hid is given.
+__global__ void k_net_features(const double* __restrict__ S, int nb, int64_t m, const int* __restrict__ lex_of_hid,
+                               float* __restrict__ x) {
+  const int64_t e = blockIdx.x;
+  if (e >= m) return;
+  const int64_t row = lex_of_hid ? (int64_t)lex_of_hid[e] : e;
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) acc += log(S[e * nb + c]);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += red[w];
+    red[0] = t / nb;
+  }
+  __syncthreads();
+  const double mean = red[0];
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    double v = log(S[e * nb + c]) - mean;
+    v = v < -20.0 ? -20.0 : (v > 20.0 ? 20.0 : v);
+    x[row * nb + c] = (float)(v / 8.0);
+  }
+}
+
+// y[e][k - 1][c] = sqrt(S_c) Phi[e][k][c], k = 1 .. L-1: the level-1 eigenvectors
+// in the symmetric form (Euclidean-orthonormal), the network's targets.
+__global__ void k_net_targets(const double* __restrict__ S, const double* __restrict__ Phi, int nb, int L, int64_t m,
+                              const int* __restrict__ lex_of_hid, float* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = m * (L - 1) * nb;
+  if (i >= total) return;
+  const int c = (int)(i % nb);
+  const int64_t ek = i / nb;
+  const int k = (int)(ek % (L - 1)) + 1;
+  const int64_t e = ek / (L - 1);
+  const int64_t row = lex_of_hid ? (int64_t)lex_of_hid[e] : e;
+  y[(row * (L - 1) + (k - 1)) * nb + c] = (float)(sqrt(S[e * nb + c]) * Phi[(e * L + k) * nb + c]);
+}
+
+void launch_net_features(msmg_ctx* c, float* x, const int* lex_of_hid, cudaStream_t s) {
+  k_net_features<<<(unsigned)c->fine.m, 128, 0, s>>>(c->fine.S, c->fine.nb, c->fine.m, lex_of_hid, x);
+}
+
+// Guesses for every element, in chunks of the network's batch: g[e][k-1][c].
+int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream_t s) {
+  msmg_net* t = const_cast<msmg_net*>(net);
+  launch_net_features(c, x, nullptr, s);
+  const int64_t m = c->fine.m;
+  const int nb = c->fine.nb;
+  for (int64_t e0 = 0; e0 < m; e0 += t->d.batch_max) {
+    const int b = (int)((m - e0) < t->d.batch_max ? (m - e0) : t->d.batch_max);
+    net_forward(t, x + e0 * nb, b, s);
+    MSMG_CUDA_TRY(cudaMemcpyAsync(g + e0 * t->n_out, t->out, (size_t)b * t->n_out * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s));
+  }
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+bool net_matches(const msmg_ctx* c, const msmg_net* net) {
+  return net && net->d.n_in == c->fine.nb && net->d.n_vec == c->fine.L - 1;
+}
+
+}  // namespace msmg
+
+extern "C" {
+
+size_t msmg_net_workspace_size(const msmg_net_desc* desc) {
+  if (!desc_ok(desc)) return 0;
+  Arena ar;
+  net_carve(desc, ar, nullptr);
+  return ar.off + 256;
+}
+
+int msmg_net_create(const msmg_net_desc* desc, void* workspace, size_t workspace_bytes, uint64_t seed,
+                    msmg_stream stream, msmg_net** out) {
+  if (!out || !desc_ok(desc) || !workspace) return MSMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return MSMG_ERR_WORKSPACE;
+  if (workspace_bytes < msmg_net_workspace_size(desc)) return MSMG_ERR_WORKSPACE;
+  msmg_net* t = new (std::nothrow) msmg_net{};
+  if (!t) return MSMG_ERR_INVALID_ARG;
+  Arena ar;
+  ar.base = static_cast<char*>(workspace);
+  ar.cap = workspace_bytes;
+  net_carve(desc, ar, t);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MSMG_CUDA_TRY(cudaMemsetAsync(t->w32, 0, (size_t)t->n_param * sizeof(float), s));
+  MSMG_CUDA_TRY(cudaMemsetAsync(t->adam_m, 0, (size_t)t->n_param * sizeof(float), s));
+  MSMG_CUDA_TRY(cudaMemsetAsync(t->adam_v, 0, (size_t)t->n_param * sizeof(float), s));
+  const int64_t dims[4] = {desc->n_in, desc->hidden[0], desc->hidden[1], t->n_out};
+  for (int l = 0; l < 3; ++l) {
+    const int64_t n = dims[l] * dims[l + 1];
+    k_init_uniform<<<g256(n), 256, 0, s>>>(t->w32 + t->off_w[l], n, seed * 4 + (uint64_t)l,
+                                           sqrtf(6.f / (float)dims[l]) * (l == 2 ? 0.25f : 1.f));
+  }
+  k_to_bf16<<<g256(t->n_param), 256, 0, s>>>(t->w32, t->w16, t->n_param);
+  MSMG_CUDA_TRY(cudaGetLastError());
+  *out = t;
+  return 0;
+}
+
+void msmg_net_destroy(msmg_net* net) { delete net; }
+
+int64_t msmg_net_param_count(const msmg_net* net) { return net ? net->n_param : 0; }
+
+int msmg_net_param_offsets(const msmg_net* net, int64_t* w_off, int64_t* b_off) {
+  if (!net || !w_off || !b_off) return MSMG_ERR_INVALID_ARG;
+  for (int l = 0; l < 3; ++l) { w_off[l] = net->off_w[l]; b_off[l] = net->off_b[l]; }
+  return 0;
+}
+
+int msmg_net_get_params(const msmg_net* net, float* params, msmg_stream stream) {
+  if (!net || !params) return MSMG_ERR_INVALID_ARG;
+  MSMG_CUDA_TRY(cudaMemcpyAsync(params, net->w32, (size_t)net->n_param * sizeof(float), cudaMemcpyDeviceToDevice,
+                                reinterpret_cast<cudaStream_t>(stream)));
+  return 0;
+}
+
+int msmg_net_set_params(msmg_net* net, const float* params, msmg_stream stream) {
+  if (!net || !params) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MSMG_CUDA_TRY(cudaMemcpyAsync(net->w32, params, (size_t)net->n_param * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  k_to_bf16<<<g256(net->n_param), 256, 0, s>>>(net->w32, net->w16, net->n_param);
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_net_forward(msmg_net* net, const float* x, float* y, int batch, msmg_stream stream) {
+  if (!net || !x || !y || batch < 0) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int b0 = 0; b0 < batch; b0 += net->d.batch_max) {
+    const int b = batch - b0 < net->d.batch_max ? batch - b0 : net->d.batch_max;
+    net_forward(net, x + (int64_t)b0 * net->d.n_in, b, s);
+    MSMG_CUDA_TRY(cudaMemcpyAsync(y + (int64_t)b0 * net->n_out, net->out, (size_t)b * net->n_out * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s));
+  }
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_net_gradients(msmg_net* net, const float* x, const float* target, int batch, float* grad, float* loss_host,
+                       msmg_stream stream) {
+  if (!net || !x || !target || batch < 1 || batch > net->d.batch_max) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  net_backward(net, x, target, batch, s);
+  if (grad)
+    MSMG_CUDA_TRY(cudaMemcpyAsync(grad, net->grad, (size_t)net->n_param * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (loss_host) {
+    const int nl = batch * net->d.n_vec;
+    MSMG_CUDA_TRY(cudaMemcpyAsync(loss_host, net->loss + nl, sizeof(float), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *loss_host /= (float)nl;
+  }
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_net_train_step(msmg_net* net, const float* x, const float* target, int batch, float lr, float* loss_host,
+                        msmg_stream stream) {
+  if (!net || !x || !target || batch < 1 || batch > net->d.batch_max || !(lr > 0.f)) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  net_backward(net, x, target, batch, s);
+  net->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.f - powf(b1, (float)net->step), c2 = 1.f - powf(b2, (float)net->step);
+  k_adam<<<g256(net->n_param), 256, 0, s>>>(net->w32, net->w16, net->grad, net->adam_m, net->adam_v, net->n_param, lr,
+                                            b1, b2, eps, c1, c2);
+  if (loss_host) {
+    const int nl = batch * net->d.n_vec;
+    MSMG_CUDA_TRY(cudaMemcpyAsync(loss_host, net->loss + nl, sizeof(float), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *loss_host /= (float)nl;
+  }
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int msmg_learning_data(msmg_ctx* c, float* x, float* y, msmg_stream stream) {
+  if (!c || !x || !y || c->fine.L < 2) return MSMG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_net_features(c, x, c->fine.lex_of_hid, s);
+  const int64_t total = c->fine.m * (c->fine.L - 1) * c->fine.nb;
+  k_net_targets<<<g256(total), 256, 0, s>>>(c->fine.S, c->fine.Phi, c->fine.nb, c->fine.L, c->fine.m,
+                                            c->fine.lex_of_hid, y);
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+}  // extern "C"

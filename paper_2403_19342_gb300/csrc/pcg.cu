@@ -414,11 +414,16 @@ struct PcgRun {
     launches += 2;
     MSMG_CUDA_TRY(cudaMemcpyAsync(hsc_last(), B.sc, (size_t)R * sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     MSMG_CUDA_TRY(cudaMemcpyAsync(c->hres, B.dres, (size_t)2 * R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaMemcpyAsync(c->hmask + c->max_rhs, c->flags + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
     MSMG_CUDA_TRY(cudaEventRecord(c->poll_evs[2], s));
     return 0;
   }
 
   int finish(msmg_solve_info* info) const {
+    if (c->hmask[c->max_rhs]) {
+      set_last_cuda_error(cudaErrorLaunchFailure);   // the cooperative coarse cycle did not run
+      return MSMG_ERR_CUDA;
+    }
     const PcgScalars* h = hsc_last();
     int worst = MSMG_OK;
     for (int r = 0; r < R; ++r) {

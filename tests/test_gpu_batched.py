@@ -236,3 +236,34 @@ def test_batched_workload_full_size(pkg):
     assert torch.equal(x1, X[0][3])
     for S in solvers:
         S.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_tuned_variants_give_the_same_bits(pkg, form, solver_fp64, solver_mixed):
+    # the autotuner's variants (prolongation fused into post-smoothing or apart) change
+    # only the time: single and batched solves agree bit for bit across them
+    S = solver_fp64 if form == "fp64" else solver_mixed
+    F = torch.tensor(rhs_set(S.shape, 4, seed=13), device="cuda")
+    out = []
+    forms = [0]
+    for form in (1, 2):
+        try:
+            pkg.msmg_set_tuning(S.ctx, (0, 0, form, form))
+            forms.append(form)
+        except pkg.MsmgError:
+            pass
+    assert 2 in forms                     # the cooperative coarse cycle is available here
+    tunes = [(0, 0, 0, 0), (1, 1, 0, 0)] + [(f % 2, (f + 1) % 2, f, f) for f in forms[1:]]
+    for tune in tunes:
+        pkg.msmg_set_tuning(S.ctx, tune)
+        X, infos, _ = S.solve(F, rtol=1e-8)
+        x1, info1, _ = S.solve(F[1], rtol=1e-8)
+        out.append((X, [i["iterations"] for i in infos], x1))
+    for o in out[1:]:
+        assert torch.equal(out[0][0], o[0]) and out[0][1] == o[1]
+        assert torch.equal(out[0][2], o[2])
+    pkg.msmg_autotune(S.ctx, 1, 2)
+    pkg.msmg_autotune(S.ctx, 4, 2)
+    assert all(v in (0, 1) for v in S.info["tuning"])
+    X2, _, _ = S.solve(F, rtol=1e-8)
+    assert torch.equal(X2, out[0][0])
