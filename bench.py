@@ -199,9 +199,17 @@ def max_over_ranks(world, v: float) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(world: int, units_per_rank: float, ms_per_step_local: float) -> tuple[float, float]:
+    """Whole-job throughput of N independent replicas (weak scaling): the units all
+    ranks processed divided by the slowest rank's time; returns (value, max ms)."""
+    ms = max_over_ranks(world, ms_per_step_local)
+    return world * units_per_rank / (ms * 1e-3), ms
 
 
 # ------------------------------------------------------------------ reference arm / CPU baseline
