@@ -13,6 +13,7 @@ flushed (256 MiB write) before every timed step.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batched [--steps K] [--warmup W]
   python bench.py --workload layered [--steps K] [--warmup W]
+  python bench.py --workload scale [--steps K] [--warmup W]
 
 The default line also carries ``batched_rhs``: the same workload with 16
 zero-mean random right-hand sides solved in one call (one launch sequence for
@@ -23,9 +24,11 @@ length 0.1) on 64^3, 64^3, 96^3, 96^3, 128^3, 128^3, 192^3, 192^3 grids with
 msmg_solve_batched call (one stream per problem, CUDA graphs).
 ``--workload layered`` measures the learned warm start: a 512^3 layered field
 with sinuous channels (85 layers, contrast 1e6-1e8, seed 100), 8^3 elements,
-6 levels, 6 eigenvectors per local problem; the network is trained first on
+6 levels, 12 eigenvectors per local problem; the network is trained first on
 eigenpairs the library computes for held-out 128^3 fields of the same kind
 (seeds 101-110); set-up is timed cold and warm-started, then the mixed solve.
+``--workload scale`` is the single-GPU limit: a 1024^3 lognormal field (contrast
+1e6), 8^3 elements, 7 levels, 4 eigenvectors per local problem, mixed form.
 
 With N > 1 (torchrun) every rank solves its own replica of the workload (the
 problem does not shard across the one-GPU machines of this pool): weak scaling,
@@ -317,7 +320,7 @@ def run_gpu(args, world, rank, local):
     for form, prec in (("fp64", pkg.FP64), ("mixed", pkg.MIXED)):
         opts = pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec, eig_tol=1e-8,
                            autotune=True)
-        S = pkg.Solver(kappa, opts, n_rhs=BATCH_RHS if form == "mixed" else 1)
+        S = pkg.Solver(kappa, opts, n_rhs=BATCH_RHS if form == "mixed" else 1, tuning_cache=args.tuning_cache)
         info0 = S.info
         for _ in range(args.warmup):
             pkg.msmg_solve(S.ctx, f_dev, x_dev, RTOL, 1000, 0)
@@ -495,7 +498,7 @@ def run_batched(args, world, rank, local):
 LAYERED_N = 512
 LAYERED_WORKLOAD = ("512^3 layered field: 85 z-layers of laterally upsampled 60x220 lognormal lattices, sinuous "
                     "binary channels in 50 layers, contrast U(1e6, 1e8) (seed 100); corner source/sink; 8^3 "
-                    "elements, 6 levels (ratio 2), 6 eigenvectors per local problem; PCG rtol 1e-8; learned "
+                    "elements, 6 levels (ratio 2), 12 eigenvectors per local problem; PCG rtol 1e-8; learned "
                     "warm start trained on 128^3 fields of the same kind (seeds 101-110)")
 
 
@@ -536,7 +539,7 @@ def run_layered(args, world, rank, local):
     pkg.load_library()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    L = 6
+    L = 12            # the channels cross many elements: 6 eigenvectors leave ~1000 PCG iterations at 128^3
     net, train = train_warm_start(pkg, torch, fields, L)
     kappa = torch.tensor(fields.layered_channels((LAYERED_N,) * 3, seed=100), device=dev)
     n = LAYERED_N ** 3
@@ -588,6 +591,70 @@ def run_layered(args, world, rank, local):
     return 0
 
 
+SCALE_N = 1024
+SCALE_WORKLOAD = ("1024^3 lognormal field (exponential covariance, correlation length 0.1, 1024 random Fourier "
+                  "modes in FP32 on the GPU, seed 5) rescaled to contrast 1e6; corner source/sink; 8^3 elements, "
+                  "7 levels (ratio 2), 4 eigenvectors per local problem; PCG rtol 1e-8")
+
+
+def run_scale(args, world, rank, local):
+    """The single-GPU limit: a 1024^3 problem in the mixed form."""
+    import torch
+    import fields
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    _build.build()
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = SCALE_N
+    n = N ** 3
+    opts = pkg.Options(n_levels=7, block=(8, 8, 8), ratio=[(2, 2, 2)] * 5, n_eig=[4] * 6, precision=pkg.MIXED,
+                       eig_tol=1e-8)
+    need = pkg.msmg_workspace_size(pkg.make_grid((N, N, N)), opts.to_c(), 1)
+    free, total = torch.cuda.mem_get_info()
+    vec_bytes = 2 * 8 * n + 4 * n                       # rhs, x (FP64) and kappa (FP32)
+    if need + vec_bytes + (8 << 30) > free:
+        print(json.dumps({"workload": SCALE_WORKLOAD, "skipped": f"needs {(need + vec_bytes) / 2**30:.1f} GiB, "
+                          f"{free / 2**30:.1f} GiB free"}), flush=True)
+        return 0
+    t0 = time.perf_counter()
+    kappa = fields.grf_lognormal_device((N, N, N), seed=5, contrast=1e6, device="cuda")
+    torch.cuda.synchronize()
+    t_field = time.perf_counter() - t0
+    S = pkg.Solver(kappa, opts)
+    info0 = S.info
+    del kappa
+    f = torch.tensor(rhs((N, N, N)), device=dev)
+    x = torch.zeros_like(f)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pkg.msmg_solve(S.ctx, f, x, RTOL, 2000, 0)
+    torch.cuda.synchronize()
+    ms, info = [], None
+    for k in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, info = pkg.msmg_solve(S.ctx, f, x, RTOL, 2000, 0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    step = max_over_ranks(world, float(np.mean(ms)))
+    kt = S.time_kernels(reps=3)
+    line = {"metric": METRIC, "value": world * n / (step * 1e-3), "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": SCALE_WORKLOAD, "form": "mixed", "l2": "working set far above L2"},
+            "iterations": info[0]["iterations"], "true_rel_residual": info[0]["true_rel_residual"],
+            "converged": info[0]["converged"], "setup_ms": info0["setup_ms"], "eig_ms": info0["eig_ms"],
+            "eig_iterations_max": info0["eig_iterations_max"], "workspace_gib": need / 2**30,
+            "field_s": t_field, "kernel_ms": kt, "gpu_launches": int(info[0]["kernel_launches"])}
+    S.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile(args):
     """Short run for ncu: set-up of the default workload, then one solve capped at
     ``--max-iter`` PCG iterations in the chosen form."""
@@ -600,7 +667,8 @@ def run_profile(args):
     x = torch.zeros_like(f)
     prec = pkg.MIXED if args.form == "mixed" else pkg.FP64
     S = pkg.Solver(kappa, pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec,
-                                      eig_tol=1e-8))
+                                      eig_tol=1e-8, autotune=True),
+                   n_rhs=BATCH_RHS if args.form == "mixed" else 1, tuning_cache=args.tuning_cache)
     st, info = pkg.msmg_solve(S.ctx, f, x, RTOL, args.max_iter, 0)
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.form, "iterations": info[0]["iterations"],
@@ -619,7 +687,9 @@ def main():
     ap.add_argument("--profile", action="store_true", help="short run for ncu (no timing output)")
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--max-iter", type=int, default=4)
-    ap.add_argument("--workload", default="inclusions", choices=["inclusions", "batched", "layered"])
+    ap.add_argument("--workload", default="inclusions", choices=["inclusions", "batched", "layered", "scale"])
+    ap.add_argument("--tuning-cache", default=os.path.join(os.environ.get("TMPDIR", "/tmp"), "msmg_tuning.json"),
+                    help="autotune cache (JSON): a later run, e.g. under a profiler, reuses the variants found")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
@@ -627,7 +697,7 @@ def main():
                                                                    int(os.environ.get("RANK", "0")), 0)
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    run = {"batched": run_batched, "layered": run_layered}.get(args.workload, run_gpu)
+    run = {"batched": run_batched, "layered": run_layered, "scale": run_scale}.get(args.workload, run_gpu)
     rc = run(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist

@@ -31,7 +31,7 @@ import numpy as np
 import torch
 
 __all__ = [
-    "grf_modes", "grf_values", "grf_lognormal", "inclusions", "layered_channels",
+    "grf_modes", "grf_values", "grf_lognormal", "grf_lognormal_device", "inclusions", "layered_channels",
     "rhs_corners", "rhs_line_sources", "rhs_random", "contrast_rescale",
 ]
 
@@ -66,6 +66,32 @@ def grf_values(shape, seed: int, corr_len: float = 0.1, n_modes: int = 1024,
         x = torch.stack([(i + 0.5) / nx, (j + 0.5) / ny, (kk + 0.5) / nz], dim=1).to(torch.float64)
         out[s:s + idx.numel()] = scale * torch.cos(x @ kt.T + pt).sum(dim=1)
     return out.reshape(nz, ny, nx).cpu().numpy()
+
+
+def grf_lognormal_device(shape, seed: int, contrast: float = 1e6, corr_len: float = 0.1, n_modes: int = 1024,
+                         device: str = "cuda", dtype=torch.float32, chunk: int = 1 << 22) -> torch.Tensor:
+    """The lognormal field of ``grf_lognormal`` (same modes for the same seed),
+    evaluated and rescaled to ``max/min = contrast`` on ``device`` in ``dtype``
+    and returned there: for grids too large to stage through the host.  In
+    float32 the values differ from the float64 field by the rounding of the
+    phases (a different, equally seeded realisation)."""
+    nz, ny, nx = shape
+    k, phi = grf_modes(seed, corr_len, n_modes)
+    kt = torch.tensor(k, dtype=dtype, device=device)
+    pt = torch.tensor(phi, dtype=dtype, device=device)
+    n = nx * ny * nz
+    out = torch.empty(n, dtype=dtype, device=device)
+    scale = math.sqrt(2.0 / n_modes)
+    for s in range(0, n, chunk):
+        idx = torch.arange(s, min(n, s + chunk), device=device, dtype=torch.int64)
+        i = idx % nx
+        j = (idx // nx) % ny
+        kk = idx // (nx * ny)
+        x = torch.stack([(i + 0.5) / nx, (j + 0.5) / ny, (kk + 0.5) / nz], dim=1).to(dtype)
+        out[s:s + idx.numel()] = scale * torch.cos(x @ kt.T + pt).sum(dim=1)
+    lo, hi = out.min(), out.max()
+    out.sub_(lo).div_(hi - lo).mul_(math.log(contrast)).exp_()
+    return out.reshape(nz, ny, nx)
 
 
 def contrast_rescale(y: np.ndarray, contrast: float) -> np.ndarray:

@@ -108,6 +108,9 @@ typedef struct {
     int eig_iterations_max;            /* subspace iterations of the slowest element     */
     int64_t eig_iterations_total;      /* subspace iterations summed over the elements   */
     int warm_started;                  /* 1 when the learned warm start seeded level 1   */
+    double face_contrast;              /* max / min interior face coefficient (Fig. (kappa */
+                                       /* edge)): the permeability contrast the hierarchy */
+                                       /* sees; high values call for more eigenvectors    */
     int tuning[4];                     /* V-cycle variants in use, for batch width 1 and  */
                                        /* wider: [0], [1] fine prolongation inside the    */
                                        /* post-smoothing kernel (1) or apart (0); [2], [3] */

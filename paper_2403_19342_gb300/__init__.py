@@ -12,6 +12,8 @@ The functions carry the C entry points' names (``msmg_setup``,
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
+import json
 import os
 from dataclasses import dataclass, field
 
@@ -54,7 +56,8 @@ class msmg_options(C.Structure):
 class msmg_setup_info(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("dims", C.c_int64 * MAX_LEVELS), ("elements", C.c_int64 * MAX_LEVELS),
                 ("setup_ms", C.c_double), ("eig_ms", C.c_double), ("eig_iterations_max", C.c_int),
-                ("eig_iterations_total", C.c_int64), ("warm_started", C.c_int), ("tuning", C.c_int * 4),
+                ("eig_iterations_total", C.c_int64), ("warm_started", C.c_int), ("face_contrast", C.c_double),
+                ("tuning", C.c_int * 4),
                 ("eig_residual_max", C.c_double), ("workspace_bytes", C.c_int64)]
 
 
@@ -338,7 +341,7 @@ def msmg_get_setup_info(ctx: int) -> dict:
     return dict(n_levels=nL, dims=list(i.dims[:nL]), elements=list(i.elements[:nL - 1]), setup_ms=i.setup_ms,
                 eig_ms=i.eig_ms, eig_iterations_max=i.eig_iterations_max,
                 eig_iterations_total=i.eig_iterations_total, warm_started=bool(i.warm_started),
-                tuning=list(i.tuning),
+                tuning=list(i.tuning), face_contrast=i.face_contrast,
                 eig_residual_max=i.eig_residual_max, workspace_bytes=i.workspace_bytes)
 
 
@@ -456,11 +459,19 @@ class WarmStartNet:
 
 
 # ----------------------------------------------------------------- convenience
+def _read_cache(path: str) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
 class Solver:
     """setup(permeability, grid, block sizes, eigenvectors per element, levels)
     then solve(rhs, rtol), on the current CUDA device and stream."""
 
-    def __init__(self, kappa, opts: Options, h=None, n_rhs: int = 1, stream=None):
+    def __init__(self, kappa, opts: Options, h=None, n_rhs: int = 1, stream=None, tuning_cache: str | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("msmg needs a CUDA device (no CPU fallback)")
         k = torch.as_tensor(kappa)
@@ -474,11 +485,29 @@ class Solver:
         self.n = shape[0] * shape[1] * shape[2]
         self.opts = opts
         self.grid = make_grid(shape, h)
-        self.copts = opts.to_c()
+        # autotune cache: a JSON file of tunings keyed by the problem's shape; a hit
+        # applies the stored variants instead of timing them again
+        key = None
+        cached = None
+        if tuning_cache:
+            key = json.dumps([list(shape), list(opts.block), list(opts.n_eig[:opts.n_levels - 1]), opts.n_levels,
+                              opts.precision, n_rhs])
+            cached = _read_cache(tuning_cache).get(key)
+        copts_opts = opts
+        if cached is not None and opts.autotune:
+            copts_opts = dataclasses.replace(opts, autotune=False)
+        self.copts = copts_opts.to_c()
         nbytes = msmg_workspace_size(self.grid, self.copts, n_rhs)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=k.device)
         self.ctx, self.setup_status = msmg_setup(self.grid, k, self.copts, self.workspace, stream)
         self.stream = stream
+        if cached is not None:
+            msmg_set_tuning(self.ctx, cached)
+        elif tuning_cache and opts.autotune:
+            c = _read_cache(tuning_cache)
+            c[key] = self.info["tuning"]
+            with open(tuning_cache, "w") as fh:
+                json.dump(c, fh)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -232,7 +232,7 @@ static void build_tables(const msmg_ctx* c, const LevelShape& sh, std::vector<st
 
 static int check_flags(msmg_ctx* c, cudaStream_t s) {
   int h[8];
-  double d[2];
+  double d[4];   // [0] eig residual max, [1] factorisation failure, [2] max T, [3] max 1/T
   MSMG_CUDA_TRY(cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, s));
   MSMG_CUDA_TRY(cudaMemcpyAsync(d, c->dtmp, sizeof(d), cudaMemcpyDeviceToHost, s));
   MSMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -240,6 +240,7 @@ static int check_flags(msmg_ctx* c, cudaStream_t s) {
   if (h[0]) return MSMG_ERR_BAD_KAPPA;
   if (h[1] || d[1] != 0.0) return MSMG_ERR_NOT_FACTORIZABLE;
   c->info.eig_residual_max = d[0];
+  c->info.face_contrast = d[2] * d[3];
   c->info.eig_iterations_max = h[3];
   c->info.eig_iterations_total = h[4];
   if (h[2]) return MSMG_ERR_EIG_NOT_CONVERGED;

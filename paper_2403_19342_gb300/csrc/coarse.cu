@@ -325,6 +325,20 @@ __device__ __forceinline__ TailItem tail_item(int64_t i, int64_t mP, int r0, int
   return it;
 }
 
+// asynchronous copy of count doubles by the nt threads of a parent group (thread t)
+__device__ __forceinline__ void group_cp(double* dst, const double* src, int count, int t, int nt) {
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 && (count & 1) == 0) {
+    for (int i = t; i < count / 2; i += nt) cp16(dst + 2 * i, src + 2 * i);
+  } else {
+    for (int i = t; i < count; i += nt) cp8(dst + i, src + i);
+  }
+}
+
+// per-group shared memory: [nP * nP] smoother inverse | [nP] vector | [Ln][gw] partials
+__host__ __device__ inline int tail_group_doubles(int nP, int Ln, int gw) {
+  return (nP * nP + nP + Ln * gw + 2 + 1) / 2 * 2;
+}
+
 template <int LT, typename Bar>
 __device__ void tail_level_down(const TailArgs& A, int l, int r0, int r1, int cta, int ncta, double* sm,
                                 const PcgScalars* sc, Bar bar) {
@@ -336,16 +350,19 @@ __device__ void tail_level_down(const TailArgs& A, int l, int r0, int r1, int ct
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp / gw, t = (warp % gw) * 32 + lane;
   const int64_t items = (int64_t)(r1 - r0) * lv.mP;
-  double* fs = sm + (size_t)grp * (nP + Ln * gw + 2);       // [nP] right side, then [Ln][gw] partials
-  // pre-smoothing from zero: u_P = Minv_P f_P
+  double* Mi = sm + (size_t)grp * tail_group_doubles(nP, Ln, gw);
+  double* fs = Mi + (size_t)nP * nP;                        // [nP] right side, then [Ln][gw] partials
+  // pre-smoothing from zero: u_P = Minv_P f_P (the inverse staged, all copies in flight)
   for (int64_t i0 = (int64_t)cta * G; i0 < items; i0 += (int64_t)ncta * G) {
     const TailItem it = tail_item(i0 + grp, lv.mP, r0, r1, sc);
     const bool live = grp < G && it.live;
     const double* f = A.f[l] + (int64_t)it.r * lv.n;
     double* u = A.u[l] + (int64_t)it.r * lv.n;
+    if (live) group_cp(Mi, D.Minv + (size_t)it.P * nP * nP, nP * nP, t, gw * 32);
     if (live && t < nP) fs[t] = f[it.P * nP + t];
+    cp_wait();
     __syncthreads();
-    if (live && t < nP) u[it.P * nP + t] = smem_gemv_col(D.Minv + (size_t)it.P * nP * nP, fs, nP, t);
+    if (live && t < nP) u[it.P * nP + t] = smem_gemv_col(Mi, fs, nP, t);
     __syncthreads();
   }
   bar();
@@ -386,7 +403,8 @@ __device__ void tail_level_up(const TailArgs& A, int l, int r0, int r1, int cta,
   const int grp = warp / gw, t = (warp % gw) * 32 + lane;
   const int64_t items = (int64_t)(r1 - r0) * lv.mP;
   const double* ebase = (l + 1 == A.nL) ? A.u[l + 1] : A.w[l + 1];
-  double* rs = sm + (size_t)grp * (nP + Ln * gw + 2);
+  double* Mi = sm + (size_t)grp * tail_group_doubles(nP, Ln, gw);
+  double* rs = Mi + (size_t)nP * nP;
   // prolongation: u_P += Psi_P^T e_P
   for (int64_t i0 = (int64_t)cta * G; i0 < items; i0 += (int64_t)ncta * G) {
     const TailItem it = tail_item(i0 + grp, lv.mP, r0, r1, sc);
@@ -409,10 +427,12 @@ __device__ void tail_level_up(const TailArgs& A, int l, int r0, int r1, int cta,
     const double* u = A.u[l] + (int64_t)it.r * lv.n;
     double* w = A.w[l] + (int64_t)it.r * lv.n;
     float* o32 = (l == 2 && A.out32) ? A.out32 + (int64_t)it.r * lv.n : nullptr;
+    if (live) group_cp(Mi, D.Minv + (size_t)it.P * nP * nP, nP * nP, t, gw * 32);
     if (live && t < nP) rs[t] = coarse_residual_row<LT>(lv, D, it.P, t, f, u);
+    cp_wait();
     __syncthreads();
     if (live && t < nP) {
-      const double v = u[it.P * nP + t] + smem_gemv_col(D.Minv + (size_t)it.P * nP * nP, rs, nP, t);
+      const double v = u[it.P * nP + t] + smem_gemv_col(Mi, rs, nP, t);
       w[it.P * nP + t] = v;
       if (o32) o32[it.P * nP + t] = (float)v;
     }
@@ -543,10 +563,11 @@ static bool tail_shape(const msmg_ctx* c, int l0, int* lt_out, size_t* sm_out) {
     const int gw = (int)(coarse_threads_d(lv.nP, lv.Lnext) / 32);
     if (gw > kTailThreads / 32) return false;
     const int G = (kTailThreads / 32) / gw;
-    const size_t need = (size_t)G * (lv.nP + lv.Lnext * gw + 2) * sizeof(double);
+    const size_t need = (size_t)G * tail_group_doubles(lv.nP, lv.Lnext, gw) * sizeof(double);
     if (need > sm) sm = need;
   }
   if (lt != 4 && lt != 6 && lt != 7 && lt != 8) lt = 0;
+  if (sm + 64 > 200 * 1024) return false;        // keep well inside 227 KB per CTA
   *lt_out = lt;
   *sm_out = sm + 64;
   return true;

@@ -11,6 +11,7 @@
 // (their data is one contiguous chunk each in the block-major layout).
 #include "msmg_internal.cuh"
 #include "reduce.cuh"
+#include "linalg_small.cuh"
 
 namespace msmg {
 
@@ -117,10 +118,11 @@ __device__ __forceinline__ V apply_A_cell(const V* ut, const V* t0, const V* t1,
 template <typename KT>
 __global__ void k_faces(const KT* __restrict__ kappa, int comps, int nx, int ny, int nz, double ihx2, double ihy2,
                         double ihz2, Geo g, int64_t m, const int* __restrict__ lex_of_hid, int gx, int gy,
-                        double* __restrict__ T, double* __restrict__ S, int* flags) {
+                        double* __restrict__ T, double* __restrict__ S, int* flags, double* tstats) {
   const int64_t n = (int64_t)nx * ny * nz;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  double tmax = 0.0, tinv = 0.0;                  // largest face coefficient, largest 1 / coefficient
+  if (i < n) {
   const int64_t e = i / g.nb;
   const int p = (int)(i % g.nb);
   const int lex = lex_of_hid[e];
@@ -147,9 +149,23 @@ __global__ void k_faces(const KT* __restrict__ kappa, int comps, int nx, int ny,
       t = (kn > 0.0 && isfinite(kn) && a > 0.0) ? 2.0 / (1.0 / a + 1.0 / b) : 0.0;
     }
     T[d * n + i] = t;
+    if (t > 0.0) {
+      tmax = fmax(tmax, t);
+      tinv = fmax(tinv, 1.0 / t);
+    }
   }
   S[i] = s;
   if (bad) atomicExch(&flags[0], 1);
+  }
+  // face-coefficient contrast of the field: one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    tinv = fmax(tinv, __shfl_xor_sync(0xffffffffu, tinv, o));
+  }
+  if ((threadIdx.x & 31) == 0 && tmax > 0.0) {
+    atomic_max_pos(&tstats[0], tmax);
+    atomic_max_pos(&tstats[1], tinv);
+  }
 }
 
 // IC(0) pivots of each element's diagonal block of the global A:
@@ -264,11 +280,11 @@ void launch_faces(msmg_ctx* c, const void* kappa, int comps, int dtype, cudaStre
   if (dtype == MSMG_F32)
     k_faces<float><<<grid, 256, 0, s>>>((const float*)kappa, comps, c->grid.nx, c->grid.ny, c->grid.nz, ihx2, ihy2,
                                         ihz2, g, c->fine.m, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->fine.T,
-                                        c->fine.S, c->flags);
+                                        c->fine.S, c->flags, c->dtmp + 2);
   else
     k_faces<double><<<grid, 256, 0, s>>>((const double*)kappa, comps, c->grid.nx, c->grid.ny, c->grid.nz, ihx2, ihy2,
                                          ihz2, g, c->fine.m, c->fine.lex_of_hid, c->fine.gx, c->fine.gy, c->fine.T,
-                                         c->fine.S, c->flags);
+                                         c->fine.S, c->flags, c->dtmp + 2);
 }
 
 void launch_pivots(msmg_ctx* c, cudaStream_t s) {

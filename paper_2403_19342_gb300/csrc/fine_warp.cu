@@ -33,6 +33,7 @@
 // are read from HBM once per launch and from L2 by the other R - 1 CTAs.
 #include "msmg_internal.cuh"
 #include "reduce.cuh"
+#include <type_traits>
 
 namespace msmg {
 
@@ -171,26 +172,38 @@ __device__ __forceinline__ void w_cp_tminus(V* tm0, V* tm1, V* tm2, const V* __r
   }
 }
 
-// per-warp shared-memory carve of the staged working set
+// per-warp shared-memory carve of the staged working set; each kernel carves
+// only what it uses (more warps fit on an SM):
+//   kStageFull      u tile with halo, T, 1/d, y, -d face coefficients (k_post)
+//   kStagePre       T, 1/d, y, -d face coefficients             (k_pre)
+//   kStageRestrict  u tile with halo, T, -d face coefficients     (k_restrict)
 template <typename V>
 struct WStage {
   V *ut, *t0, *t1, *t2, *tm0, *tm1, *tm2, *dinv, *y;
 };
+constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2;
 __host__ __device__ constexpr int r4(int x) { return (x + 3) / 4 * 4; }
-template <typename G>
+template <int LAYOUT, typename G>
 __host__ __device__ inline int wstage_elems(const G& g) {
-  return r4(g.P) + 5 * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
+  const int tut = LAYOUT == kStagePre ? 0 : r4(g.P);
+  const int nv = LAYOUT == kStageRestrict ? 3 : 5;
+  return tut + nv * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
 }
-template <typename V, typename G>
+template <typename V, int LAYOUT = kStageFull, typename G>
 __device__ __forceinline__ WStage<V> w_stage(unsigned char* base, const G& g, int warp) {
-  V* p = reinterpret_cast<V*>(base) + (size_t)warp * wstage_elems(g);
+  V* p = reinterpret_cast<V*>(base) + (size_t)warp * wstage_elems<LAYOUT>(g);
   WStage<V> s;
-  s.ut = p; p += r4(g.P);
+  s.ut = nullptr;
+  s.dinv = nullptr;
+  s.y = nullptr;
+  if (LAYOUT != kStagePre) { s.ut = p; p += r4(g.P); }
   s.t0 = p; p += r4(g.nb);
   s.t1 = p; p += r4(g.nb);
   s.t2 = p; p += r4(g.nb);
-  s.dinv = p; p += r4(g.nb);
-  s.y = p; p += r4(g.nb);
+  if (LAYOUT != kStageRestrict) {
+    s.dinv = p; p += r4(g.nb);
+    s.y = p; p += r4(g.nb);
+  }
   s.tm0 = p; p += r4(g.by * g.bz);
   s.tm1 = p; p += r4(g.bx * g.bz);
   s.tm2 = p;
@@ -224,11 +237,100 @@ __device__ __forceinline__ V w_apply_A_s(const WStage<V>& s, const G& g, int c) 
   return acc;
 }
 
+// Cells of an 8^3 element by hyperplane lx + ly + lz = w (w = 0 .. 21), each plane in
+// (lz, ly) order; kPlane8Off[w] is the first entry of plane w.  With these, a
+// warp gives every lane at most two cells of the current plane (30 warp-steps
+// per sweep instead of 44 with two fixed x-lines per lane).
+struct Plane8 {
+  unsigned short cell[512];
+  unsigned short off[23];
+};
+constexpr Plane8 make_plane8() {
+  Plane8 p{};
+  int k = 0;
+  for (int w = 0; w <= 21; ++w) {
+    p.off[w] = (unsigned short)k;
+    for (int lz = 0; lz < 8; ++lz)
+      for (int ly = 0; ly < 8; ++ly) {
+        const int lx = w - ly - lz;
+        if (lx >= 0 && lx < 8) p.cell[k++] = (unsigned short)(lx + 8 * ly + 64 * lz);
+      }
+  }
+  p.off[22] = (unsigned short)k;
+  return p;
+}
+__device__ const Plane8 kPlane8 = make_plane8();
+
+template <typename G>
+struct IsCube8 : std::false_type {};
+template <>
+struct IsCube8<GeoC<8, 8, 8>> : std::true_type {};
+
+// The table is read at every wavefront step, so each CTA keeps a copy in shared
+// memory (after the warps' staging areas): a global read there would queue
+// behind the kernel's outstanding loads.
+constexpr int kPlaneShorts = 512 + 23;
+constexpr size_t kPlaneSmemBytes = 1088;
+template <typename G>
+__host__ __device__ constexpr size_t plane_smem(const G&) { return IsCube8<G>::value ? kPlaneSmemBytes : 0; }
+
+// copy the table (all threads of the CTA; ends with a CTA barrier); returns it
+template <typename G>
+__device__ __forceinline__ const unsigned short* w_plane_table(unsigned char* at) {
+  if constexpr (IsCube8<G>::value) {
+    unsigned short* t = reinterpret_cast<unsigned short*>(at);
+    const unsigned short* src = reinterpret_cast<const unsigned short*>(&kPlane8);
+    for (int i = threadIdx.x; i < kPlaneShorts; i += blockDim.x) t[i] = src[i];
+    __syncthreads();
+    return t;
+  }
+  return nullptr;
+}
+
 // y <- M^{-1} y from the staged tiles, M = (D~ + L) D~^{-1} (D~ + L^T):
-// forward then backward wavefronts lx + ly + lz = w; lane l owns the lines
-// l, l + 32, ... (line = ly + by * lz).
+// forward then backward wavefronts lx + ly + lz = w.  8^3 elements: the cells of
+// each plane are dealt to the lanes from kPlane8; other shapes: lane l owns the
+// lines l, l + 32, ... (line = ly + by * lz).  The arithmetic per cell is the same.
 template <typename V, typename G>
-__device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane) {
+__device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane, const unsigned short* tab) {
+  if constexpr (IsCube8<G>::value) {
+    const unsigned short* cell = tab;
+    const unsigned short* off = tab + 512;
+    V* y = s.y;
+    for (int w = 0; w <= 21; ++w) {
+      const int o0 = off[w], o1 = off[w + 1];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int k = o0 + lane + 32 * j;
+        if (k >= o1) continue;
+        const int c = cell[k];
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        V acc = y[c];
+        if (lx > 0) acc += s.t0[c - 1] * y[c - 1];
+        if (ly > 0) acc += s.t1[c - 8] * y[c - 8];
+        if (lz > 0) acc += s.t2[c - 64] * y[c - 64];
+        y[c] = acc * s.dinv[c];
+      }
+      __syncwarp();
+    }
+    for (int w = 21; w >= 0; --w) {
+      const int o0 = off[w], o1 = off[w + 1];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int k = o0 + lane + 32 * j;
+        if (k >= o1) continue;
+        const int c = cell[k];
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        V acc = (V)0;
+        if (lx < 7) acc += s.t0[c] * y[c + 1];
+        if (ly < 7) acc += s.t1[c] * y[c + 8];
+        if (lz < 7) acc += s.t2[c] * y[c + 64];
+        y[c] += s.dinv[c] * acc;
+      }
+      __syncwarp();
+    }
+    return;
+  }
   const int smax = g.bx + g.by + g.bz - 3;
   const int bxy = g.bx * g.by;
   V* y = s.y;
@@ -289,7 +391,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
   const bool act = e < m;
-  const WStage<V> s = w_stage<V>(smem, g, warp);
+  const WStage<V> s = w_stage<V, kStagePre>(smem, g, warp);
+  const unsigned short* tab =
+      w_plane_table<G>(smem + (size_t)kWarpsPerCta * wstage_elems<kStagePre>(g) * sizeof(V));
   double acc = 0.0;
   if (act) {
     const WElem E = w_elem(e, nbr, g);
@@ -328,7 +432,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
     }
     cp_async_wait_all();
     __syncwarp();
-    w_ic0_s(s, g, lane);
+    w_ic0_s(s, g, lane, tab);
 #pragma unroll 4
     for (int i = 0; i < (g.nb + 31) / 32; ++i) {
       const int c = lane + 32 * i;
@@ -367,13 +471,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_restrict(const V* __restr
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
   if (e >= m) return;
-  const WStage<V> s = w_stage<V>(smem, g, warp);
+  const WStage<V> s = w_stage<V, kStageRestrict>(smem, g, warp);
   const WElem E = w_elem(e, nbr, g);
   w_cp_padded(s.ut, u + E.base, g, lane);
   w_cp_halo(s.ut, u, E, g, lane);
   w_stage_T(s, T, (const V*)nullptr, n, E, g, lane, false);
-  const int ncl = (g.nb + 31) / 32;
-  if (ncl <= kC) {
+  const int ncl = (g.nb + 31) / 32;            // <= kC: elements have at most 512 cells
+  {
     V w[kC];
 #pragma unroll
     for (int i = 0; i < kC; ++i) {
@@ -397,18 +501,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_restrict(const V* __restr
         const int c = lane + 32 * i;
         if (i < ncl && c < g.nb) acc += (V)__ldg(ph + c) * w[i];
       }
-      acc = warp_sum_t(acc);
-      if (lane == 0) rc[e * L + k] = (double)acc;
-    }
-  } else {
-    cp_async_wait_all();
-    __syncwarp();
-    for (int c = lane; c < g.nb; c += 32) s.y[c] = __ldg(f + E.base + c) - w_apply_A_s(s, g, c);
-    __syncwarp();
-    for (int k = 0; k < L; ++k) {
-      const BT* ph = Phi + (e * L + k) * g.nb;
-      V acc = (V)0;
-      for (int c = lane; c < g.nb; c += 32) acc += (V)__ldg(ph + c) * s.y[c];
       acc = warp_sum_t(acc);
       if (lane == 0) rc[e * L + k] = (double)acc;
     }
@@ -593,6 +685,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
   const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
   const bool act = e < m;
   const WStage<V> s = w_stage<V>(smem, g, warp);
+  const unsigned short* tab =
+      w_plane_table<G>(smem + (size_t)kWarpsPerCta * wstage_elems<kStageFull>(g) * sizeof(V));
   const int ncl = (g.nb + 31) / 32;
   double v[2] = {0.0, 0.0};
   if (act && ncl <= kC) {
@@ -630,7 +724,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
       qq[i] = (in && qv) ? __ldg(qv + base + c) : 0.0;
     }
     __syncwarp();
-    w_ic0_s(s, g, lane);
+    w_ic0_s(s, g, lane, tab);
 #pragma unroll
     for (int i = 0; i < kC; ++i) {
       const int c = lane + 32 * i;
@@ -655,7 +749,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
     }
     for (int c = lane; c < g.nb; c += 32) s.y[c] = __ldg(f + base + c) - w_apply_A_s(s, g, c);
     __syncwarp();
-    w_ic0_s(s, g, lane);
+    w_ic0_s(s, g, lane, tab);
     for (int c = lane; c < g.nb; c += 32) {
       const int lx = c % g.bx, t = c / g.bx;
       const double zc = (double)(s.ut[wpad(g, lx, t % g.by, t / g.by)] + s.y[c]);
@@ -817,9 +911,9 @@ struct FineOps {
   const BT* Phi;
 };
 
-template <typename G>
+template <int LAYOUT, typename G>
 static inline size_t wsmem(const G& g, size_t vsize) {
-  return (size_t)kWarpsPerCta * wstage_elems(g) * vsize;
+  return (size_t)kWarpsPerCta * wstage_elems<LAYOUT>(g) * vsize + (LAYOUT == kStageRestrict ? 0 : plane_smem(g));
 }
 template <typename G>
 static inline size_t wsmem_p(const G& g) {
@@ -843,7 +937,7 @@ static inline unsigned fine_wgrid(const msmg_ctx* c) {
 template <typename V, typename BT, typename G>
 static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  k_pre<V, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+  k_pre<V, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStagePre>(g, sizeof(V)), s>>>(
       B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv, (V*)B.vu[1], c->n, g, c->fine.m, c->fine.nbr, update, c->red, sc,
       B.R);
 }
@@ -851,7 +945,7 @@ static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* 
 template <typename V, typename BT, typename G>
 static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  k_restrict<V, BT, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+  k_restrict<V, BT, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStageRestrict>(g, sizeof(V)), s>>>(
       (const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
       c->fine.nbr, sc, B.R);
 }
@@ -861,11 +955,11 @@ static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, const doub
                    cudaStream_t s, const G& g, bool fuse) {
   SolveBuffers& B = c->sb;
   if (fuse)
-    k_post<V, BT, G, true><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+    k_post<V, BT, G, true><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStageFull>(g, sizeof(V)), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
         c->fine.m, c->fine.nbr, c->red, sc, B.R);
   else
-    k_post<V, BT, G, false><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem(g, sizeof(V)), s>>>(
+    k_post<V, BT, G, false><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStageFull>(g, sizeof(V)), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
         c->fine.m, c->fine.nbr, c->red, sc, B.R);
 }
@@ -890,9 +984,11 @@ static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s, const G& g) {
 // during stream capture).
 template <typename V, typename BT, typename G>
 static void prepare_t(const G& g) {
-  const int smv = (int)wsmem(g, sizeof(V)), smd = (int)wsmem_p(g);
-  cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
-  cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+  const int smv = (int)wsmem<kStageFull>(g, sizeof(V)), smd = (int)wsmem_p(g);
+  cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)wsmem<kStagePre>(g, sizeof(V)));
+  cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)wsmem<kStageRestrict>(g, sizeof(V)));
   cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_post<V, BT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
