@@ -84,17 +84,24 @@ def rhs(shape):
 # a V-cycle value (4 mixed, 8 FP64).
 #   pre:      x, r read+write, p, q read (FP64); r copy and u written (v); T (3), 1/d read (v)
 #   restrict: r copy, u (v); T (3) (v); basis (L values, v)
-#   post:     r copy, u (v); T (3), 1/d (v); basis (L values, v: the prolongation
-#             runs inside it); r read (FP64); q read (FP64, flexible beta only);
-#             z written (FP64)
+#   prolong:  (separate variant) basis (L values, v); u read and written (v)
+#   post:     r copy, u (v); T (3), 1/d (v); the basis (L values, v) only in the
+#             fused variant, where the prolongation runs inside it; r read (FP64);
+#             q read (FP64, flexible beta only); z written (FP64)
 #   pmatvec:  z, p_old read, p_new, q written (FP64); T (3) and the diagonal D (FP64)
 # With R right-hand sides in one launch the coefficients (T, 1/d, D, basis) are read
-# once for all R: bytes per cell and right-hand side.
-def kernel_bytes(form: str, L: int, R: int = 1) -> dict:
+# once for all R: bytes per cell and right-hand side.  fused: the variant the
+# autotuner picked (Solver.info["tuning"][0] for one right-hand side, [1] for R).
+def kernel_bytes(form: str, L: int, R: int = 1, fused: bool = False) -> dict:
     v = 4 if form == "mixed" else 8
     flex = 8 if form == "mixed" else 0
-    return {"pre": 48 + 2 * v + 4 * v / R, "restrict": 2 * v + (3 * v + L * v) / R, "prolong": 0.0,
-            "post": 2 * v + (4 * v + L * v) / R + 8 + flex + 8, "pmatvec": 32 + 32 / R}
+    basis = L * v / R
+    return {"pre": 48 + 2 * v + 4 * v / R, "restrict": 2 * v + (3 * v) / R + basis,
+            "prolong": 0.0 if fused else basis + 2 * v,
+            "post": 2 * v + (4 * v) / R + (basis if fused else 0.0) + 8 + flex + 8, "pmatvec": 32 + 32 / R}
+
+
+VCYCLE_FINE = ("pre", "restrict", "prolong", "post")
 
 
 def load_peaks():
@@ -107,9 +114,10 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel: str):
+def traffic_record(kernel: str, fused: bool):
     """Per-launch DRAM bytes of ``kernel`` from the committed ncu summary, if it
-    was captured on the current source of the kernel file."""
+    was captured on the current source of the kernel file and in the same
+    prolongation variant."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -118,7 +126,8 @@ def traffic_record(kernel: str):
         src = os.path.join(ROOT, "paper_2403_19342_gb300", "csrc", rec["source"])
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         ent = rec["kernels"].get(kernel)
-        if ent and rec.get("source_sha") == sha:
+        variant = "fused" if fused else "separate"
+        if ent and rec.get("source_sha") == sha and rec.get("prolongation") == variant:
             return ent["dram_bytes_per_launch_full_size"]
     except Exception:
         pass
@@ -284,8 +293,8 @@ def batched_rhs(pkg, S, shape, n, args, world, flush, stream):
     step = max_over_ranks(world, float(np.mean(ms)))
     its = [i["iterations"] for i in infos]
     kt = S.time_kernels(reps=5, n_rhs=BATCH_RHS)
-    kb = kernel_bytes("mixed", N_EIG[0], BATCH_RHS)
-    vc = sum(kb[k] for k in ("pre", "restrict", "post")) * n * BATCH_RHS
+    kb = kernel_bytes("mixed", N_EIG[0], BATCH_RHS, fused=S.info["tuning"][1] == 1)
+    vc = sum(kb[k] for k in VCYCLE_FINE) * n * BATCH_RHS
     peak, _ = load_peaks()
     return {"n_rhs": BATCH_RHS, "value": world * n * BATCH_RHS / (step * 1e-3), "unit": "DOF/s",
             "ms_per_step": step, "iterations_min": min(its), "iterations_max": max(its),
@@ -377,19 +386,19 @@ def run_gpu(args, world, rank, local):
     # roofline of the dominant fine-level kernel of the mixed V-cycle
     peak, peak_kind = load_peaks()
     L = N_EIG[0]
-    kb = kernel_bytes("mixed", L)
+    kb = kernel_bytes("mixed", L, fused=forms["mixed"]["tuning"][0] == 1)
     kt = kernel_times["mixed"]
-    fine = {k: kt[k] for k in ("pre", "restrict", "post", "pmatvec")}
+    fine = {k: kt[k] for k in ("pre", "restrict", "prolong", "post", "pmatvec") if kb[k] > 0}
     dom = max(fine, key=fine.get)
     achieved = kb[dom] * n / (kt[dom] * 1e-3) / 1e9
-    traffic = traffic_record(dom)
+    traffic = traffic_record(dom, forms["mixed"]["tuning"][0] == 1)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": kb[dom] * n, "avg_launch_ms": kt[dom]}
-    vc_keys = ("pre", "restrict", "post")
-    vc_bytes = sum(kb[k] for k in vc_keys) * n
+    vc_bytes = sum(kb[k] for k in VCYCLE_FINE) * n
     vc_frac = vc_bytes / (kt["vcycle"] * 1e-3) / 1e9 / peak
-    vc64 = sum(kernel_bytes("fp64", L)[k] for k in vc_keys) * n / (kernel_times["fp64"]["vcycle"] * 1e-3) / 1e9 / peak
+    kb64 = kernel_bytes("fp64", L, fused=forms["fp64"]["tuning"][0] == 1)
+    vc64 = sum(kb64[k] for k in VCYCLE_FINE) * n / (kernel_times["fp64"]["vcycle"] * 1e-3) / 1e9 / peak
     line = {"metric": METRIC, "value": forms["mixed"]["value"], "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms["mixed"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
