@@ -13,7 +13,7 @@ void set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
 void launch_mixed_copies(msmg_ctx* c, cudaStream_t s);
 void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s);
-int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess);
+int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess, float* block);
 int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream_t s);
 bool net_matches(const msmg_ctx* c, const msmg_net* net);
 int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
@@ -398,19 +398,24 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   if (c->fine.nb <= 96) {
     st = launch_level1_eigen(c, s);
   } else {
-    // learned warm start: features and guesses in the (still unused) solve
-    // buffers, which span at least 56 n bytes
+    // Scratch in buffers that are still unused: the solve buffers span at
+    // least 56 n bytes (64 n in the mixed form), Phi 8 L n bytes.
+    //   FP64 form   features, then the learned guesses, in the solve buffers
+    //   mixed form  features, then the FP32 block handed from the first phase
+    //               to the second (4 K n <= 64 n bytes), in the solve buffers;
+    //               the guesses in Phi, which only the second phase writes
+    const bool mixed = c->opts.precision == MSMG_MIXED;
+    float* span = reinterpret_cast<float*>(c->sb.b);
     const float* guess = nullptr;
     const msmg_net* net = opts->warm_start;
-    if (net && net_matches(c, net) && (size_t)4 * c->fine.L * c->n <= (size_t)56 * c->n) {
-      float* x = reinterpret_cast<float*>(c->sb.b);
-      float* g = x + c->n;
-      st = net_guesses(c, net, x, g, s);
+    if (net && net_matches(c, net) && (mixed || (size_t)4 * c->fine.L * c->n <= (size_t)56 * c->n)) {
+      float* g = mixed ? reinterpret_cast<float*>(c->fine.Phi) : span + c->n;
+      st = net_guesses(c, net, span, g, s);
       if (st) return st;
       guess = g;
       c->info.warm_started = 1;
     }
-    st = launch_level1_chfsi(c, s, guess);
+    st = launch_level1_chfsi(c, s, guess, mixed ? span : nullptr);
   }
   cudaEventRecord(e_eig1, s);
   if (st) return st;

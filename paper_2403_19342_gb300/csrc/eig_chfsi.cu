@@ -1,7 +1,11 @@
 // Level-1 local eigensolver for large elements (Eq. (spepb)): Chebyshev-
 // filtered subspace iteration (the filtered Rayleigh-Ritz scheme of Zhou,
-// Saad, Tiago and Chelikowsky, 2006), FP64, one CTA per element, everything in
-// shared memory.
+// Saad, Tiago and Chelikowsky, 2006), one CTA per element, everything in
+// shared memory.  The FP64 form iterates in FP64 throughout; the mixed form
+// first iterates in FP32 (vectors, filter, orthonormalisation, Rayleigh-Ritz
+// projections; only the K x K eigensolve in FP64) to a residual near FP32's
+// reach and then polishes the whole block in FP64 to the requested tolerance,
+// so the bases it keeps are the FP64 form's to within that tolerance.
 //
 // The generalised problem A_K phi = lambda S_K phi is solved in its symmetric
 // form A~ y = lambda y, A~ = S^{-1/2} A_K S^{-1/2}, phi = S^{-1/2} y.  A~ is the
@@ -31,30 +35,37 @@ namespace msmg {
 constexpr int kKMax = 16;
 
 // Sum over the CTA of cnt (<= kKMax) values per thread; out[0..cnt) in smem,
-// valid for every thread on return.
-__device__ __forceinline__ void block_sum_many(const double (&vals)[kKMax], int cnt, double* out, double* scr) {
+// valid for every thread on return.  A is the accumulation type; outr, if
+// given, receives the sums (or, with rsq, their reciprocal square roots) in A,
+// so that no thread converts or divides per use.
+template <typename A>
+__device__ __forceinline__ void block_sum_many(const A (&vals)[kKMax], int cnt, double* out, double* scr,
+                                               A* outr = nullptr, bool rsq = false) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  A* sa = reinterpret_cast<A*>(scr);
 #pragma unroll
   for (int i = 0; i < kKMax; ++i) {
     if (i < cnt) {
-      const double t = warp_sum(vals[i]);
-      if (lane == 0) scr[i * 32 + warp] = t;
+      const A t = warp_sum_t(vals[i]);
+      if (lane == 0) sa[i * 32 + warp] = t;
     }
   }
   __syncthreads();
   if (threadIdx.x < cnt) {
-    double acc = 0.0;
-    for (int w = 0; w < nwarp; ++w) acc += scr[threadIdx.x * 32 + w];
-    out[threadIdx.x] = acc;
+    A acc = (A)0;
+    for (int w = 0; w < nwarp; ++w) acc += sa[threadIdx.x * 32 + w];
+    out[threadIdx.x] = (double)acc;
+    if (outr) outr[threadIdx.x] = rsq ? (A)(1.0 / sqrt((double)acc)) : acc;
   }
   __syncthreads();
 }
 
+template <typename R>
 struct ElemOp {
-  const double *g, *wx, *wy, *wz;
+  const R *g, *wx, *wy, *wz;
   int bx, by, bz, bxy;
-  __device__ __forceinline__ double apply(const double* v, int c, int lx, int ly, int lz) const {
-    double r = g[c] * v[c];
+  __device__ __forceinline__ R apply(const R* v, int c, int lx, int ly, int lz) const {
+    R r = g[c] * v[c];
     if (lx > 0) r -= wx[c - 1] * v[c - 1];
     if (lx < bx - 1) r -= wx[c] * v[c + 1];
     if (ly > 0) r -= wy[c - bx] * v[c - bx];
@@ -71,19 +82,45 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c) 
   return (double)h * (1.0 / 4294967296.0) - 0.5;
 }
 
-__global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__ T, const double* __restrict__ S, int64_t n, int bx, int by,
-                               int bz, int64_t m, int L, int K, int mdeg, int max_iter, double tol,
-                               const float* __restrict__ guess, double* __restrict__ Phi, double* __restrict__ lam,
-                               double* stats, int* flags) {
-  extern __shared__ double sm[];
+// Shared memory: (4 + 2K) nb values of R, then the FP64 Rayleigh-Ritz work, then ints.
+__host__ __device__ inline size_t chfsi_r_bytes(int nb, int K, size_t rsize) {
+  return ((size_t)(4 + 2 * K) * nb * rsize + 15) / 16 * 16;
+}
+constexpr int kMdegMax = 32;
+// R-typed scalars shared by the CTA: rotation Q (K x K, Ritz order), Ritz values,
+// block sums, filter coefficients
+constexpr int kRScal = kKMax * kKMax + kKMax + (kKMax + 1) + 2 + 2 * kMdegMax;
+__host__ __device__ inline size_t chfsi_smem(int nb, int K, size_t rsize) {
+  return chfsi_r_bytes(nb, K, rsize) +
+         (size_t)(2 * K * K + kKMax * 2 + kKMax * 32 + kKMax + 2 + 72 + 8 + kRScal) * sizeof(double) +
+         (size_t)(kKMax + 2 + kKMax + 3 * kKMax) * sizeof(int) + 64;
+}
+
+// R: arithmetic of the filter, orthonormalisation and residuals (FP64, or FP32
+// for the first phase of the mixed form); the K x K Rayleigh-Ritz eigensolve is
+// FP64 either way.
+//   guess, guess_vecs   starting vectors (symmetric form, FP32): guess_vecs == L - 1
+//                       fills slots 1 .. L-1 (learned warm start), == K fills every slot
+//                       (the block a first phase left), 0: none
+//   block_out           first phase: the K vectors of the final block (symmetric form,
+//                       FP32) are written here and Phi, lam and the convergence flag
+//                       are left to the second phase
+template <typename R>
+__global__ void __launch_bounds__(512, 2) k_eig_l1_chfsi(const double* __restrict__ T, const double* __restrict__ S,
+                                                      int64_t n, int bx, int by, int bz, int64_t m, int L, int K,
+                                                      int mdeg, int max_iter, double tol,
+                                                      const float* __restrict__ guess, int guess_vecs,
+                                                      float* __restrict__ block_out, double* __restrict__ Phi,
+                                                      double* __restrict__ lam, double* stats, int* flags) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int nb = bx * by * bz, bxy = bx * by;
-  double* g = sm;
-  double* wx = g + nb;
-  double* wy = wx + nb;
-  double* wz = wy + nb;
-  double* X = wz + nb;               // [K][nb]
-  double* Y = X + K * nb;            // [K][nb]
-  double* H = Y + K * nb;            // [K][K]
+  R* g = reinterpret_cast<R*>(smraw);
+  R* wx = g + nb;
+  R* wy = wx + nb;
+  R* wz = wy + nb;
+  R* X = wz + nb;                    // [K][nb]
+  R* Y = X + K * nb;                 // [K][nb]
+  double* H = reinterpret_cast<double*>(smraw + chfsi_r_bytes(nb, K, sizeof(R)));   // [K][K]
   double* Q = H + K * K;             // [K][K]
   double* theta = Q + K * K;         // [K]
   double* proj = theta + kKMax;      // [kKMax]
@@ -91,7 +128,11 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
   double* cs = scr + kKMax * 32;     // [K + 2]
   double* red = cs + kKMax + 2;      // [72]
   double* misc = red + 72;           // [8]
-  int* pr = reinterpret_cast<int*>(misc + 8);   // [K + 2]
+  R* Qr = reinterpret_cast<R*>(misc + 8);       // [K][K] in R, columns in Ritz order
+  R* theta_r = Qr + kKMax * kKMax;              // [K]
+  R* sum_r = theta_r + kKMax;                   // [kKMax + 1]
+  R* coef = sum_r + kKMax + 1;                  // [2 + 2 mdeg]: sig/e, c, then (2 s_j/e, s_{j-1} s_j) per degree
+  int* pr = reinterpret_cast<int*>(misc + 8 + kRScal);   // [K + 2]
   int* order = pr + kKMax + 2;                  // [K]
   int* modes = order + kKMax;                   // [K][3]
 
@@ -101,23 +142,24 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
   const int lx = act ? c % bx : 0, ly = act ? (c / bx) % by : 0, lz = act ? c / bxy : 0;
   const double* Te = T + e * nb;
   double sq = 1.0;
+  double* isq_s = H;                 // 1 / sqrt(s) staged in the (not yet used) FP64 area
   if (act) {
     sq = sqrt(S[e * nb + c]);
-    Y[c] = 1.0 / sq;                 // isq staged in Y for the weights
+    isq_s[c] = 1.0 / sq;
   }
   __syncthreads();
   if (act) {
-    const double isq = Y[c];
+    const double isq = isq_s[c];
     double diag = 0.0;
     double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-    if (lx < bx - 1) { const double t = Te[c]; diag += t; w0 = t * isq * Y[c + 1]; }
+    if (lx < bx - 1) { const double t = Te[c]; diag += t; w0 = t * isq * isq_s[c + 1]; }
     if (lx > 0) diag += Te[c - 1];
-    if (ly < by - 1) { const double t = Te[n + c]; diag += t; w1 = t * isq * Y[c + bx]; }
+    if (ly < by - 1) { const double t = Te[n + c]; diag += t; w1 = t * isq * isq_s[c + bx]; }
     if (ly > 0) diag += Te[n + c - bx];
-    if (lz < bz - 1) { const double t = Te[2 * n + c]; diag += t; w2 = t * isq * Y[c + bxy]; }
+    if (lz < bz - 1) { const double t = Te[2 * n + c]; diag += t; w2 = t * isq * isq_s[c + bxy]; }
     if (lz > 0) diag += Te[2 * n + c - bxy];
-    g[c] = diag * isq * isq;
-    wx[c] = w0; wy[c] = w1; wz[c] = w2;
+    g[c] = (R)(diag * isq * isq);
+    wx[c] = (R)w0; wy[c] = (R)w1; wz[c] = (R)w2;
   }
   // starting modes: separable cosines ranked by sum (k_d / b_d)^2 (mode 0 = constant)
   const int cx = bx < 4 ? bx : 4, cy = by < 4 ? by : 4, cz = bz < 4 ? bz : 4;
@@ -134,19 +176,17 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
     if (rank < K) { modes[3 * rank] = kx; modes[3 * rank + 1] = ky; modes[3 * rank + 2] = kz; }
   }
   __syncthreads();
-  const ElemOp op{g, wx, wy, wz, bx, by, bz, bxy};
+  const ElemOp<R> op{g, wx, wy, wz, bx, by, bz, bxy};
   // Gershgorin upper bound of the spectrum
   {
-    double v[1] = {0.0};
+    double t = 0.0;
     if (act) {
-      double r = g[c] + wx[c] + wy[c] + wz[c];
-      if (lx > 0) r += wx[c - 1];
-      if (ly > 0) r += wy[c - bx];
-      if (lz > 0) r += wz[c - bxy];
-      v[0] = r;
+      double r = (double)g[c] + (double)wx[c] + (double)wy[c] + (double)wz[c];
+      if (lx > 0) r += (double)wx[c - 1];
+      if (ly > 0) r += (double)wy[c - bx];
+      if (lz > 0) r += (double)wz[c - bxy];
+      t = r;
     }
-    // max via warp shuffles
-    double t = v[0];
     for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
     if ((threadIdx.x & 31) == 0) scr[threadIdx.x >> 5] = t;
     __syncthreads();
@@ -161,20 +201,21 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
   const double PI = 3.141592653589793238462643383279502884;
   if (act) {
     for (int q = 0; q < K; ++q) {
-      if (guess && q >= 1 && q < L) {
-        X[q * nb + c] = (double)guess[((size_t)e * (L - 1) + (q - 1)) * nb + c];
+      if (guess && ((guess_vecs == K) || (guess_vecs == L - 1 && q >= 1 && q < L))) {
+        const int slot = guess_vecs == K ? q : q - 1;
+        X[q * nb + c] = (R)guess[((size_t)e * guess_vecs + slot) * nb + c];
         continue;
       }
       const double v = cos(PI * modes[3 * q] * (lx + 0.5) / bx) * cos(PI * modes[3 * q + 1] * (ly + 0.5) / by) *
                        cos(PI * modes[3 * q + 2] * (lz + 0.5) / bz);
-      X[q * nb + c] = sq * v;
+      X[q * nb + c] = (R)(sq * v);
     }
   }
   __syncthreads();
 
-  double vals[kKMax];
-  int it = 0;
-  double rmax = 0.0;
+  R vals[kKMax];
+  int it = 0, stall = 0;
+  double rmax = 0.0, rbest = 1e300;
   for (;; ++it) {
     // ---- orthonormalise X (two-pass classical Gram-Schmidt)
     for (int j = 0; j < K; ++j) {
@@ -182,27 +223,27 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
         for (int pass = 0; pass < 2; ++pass) {
           if (j == 0) break;
 #pragma unroll
-          for (int i = 0; i < kKMax; ++i) vals[i] = (act && i < j) ? X[i * nb + c] * X[j * nb + c] : 0.0;
-          block_sum_many(vals, j, proj, scr);
+          for (int i = 0; i < kKMax; ++i) vals[i] = (act && i < j) ? X[i * nb + c] * X[j * nb + c] : (R)0;
+          block_sum_many(vals, j, proj, scr, sum_r);
           if (act) {
-            double x = X[j * nb + c];
-            for (int i = 0; i < j; ++i) x -= proj[i] * X[i * nb + c];
+            R x = X[j * nb + c];
+            for (int i = 0; i < j; ++i) x -= sum_r[i] * X[i * nb + c];
             X[j * nb + c] = x;
           }
           __syncthreads();
         }
 #pragma unroll
-        for (int i = 0; i < kKMax; ++i) vals[i] = 0.0;
-        vals[0] = act ? X[j * nb + c] * X[j * nb + c] : 0.0;
-        block_sum_many(vals, 1, proj, scr);
+        for (int i = 0; i < kKMax; ++i) vals[i] = (R)0;
+        vals[0] = act ? X[j * nb + c] * X[j * nb + c] : (R)0;
+        block_sum_many(vals, 1, proj, scr, sum_r, true);
         const double nrm2 = proj[0];
-        if (nrm2 > 1e-24) {
-          if (act) X[j * nb + c] *= 1.0 / sqrt(nrm2);
+        if (nrm2 > (sizeof(R) == 4 ? 1e-12 : 1e-24)) {
+          if (act) X[j * nb + c] *= sum_r[0];
           __syncthreads();
           break;
         }
         // collapsed: reseed deterministically and project again
-        if (act) X[j * nb + c] = sq * hash_unit((uint32_t)c, (uint32_t)j, (uint32_t)(it * 4 + tries));
+        if (act) X[j * nb + c] = (R)(sq * hash_unit((uint32_t)c, (uint32_t)j, (uint32_t)(it * 4 + tries)));
         __syncthreads();
       }
     }
@@ -215,7 +256,7 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
       const int cnt = npair - b0 < kKMax ? npair - b0 : kKMax;
 #pragma unroll
       for (int t = 0; t < kKMax; ++t) {
-        vals[t] = 0.0;
+        vals[t] = (R)0;
         if (t < cnt && act) {
           // pair index -> (i, j), i <= j
           int p = b0 + t, i = 0;
@@ -236,32 +277,37 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
     }
     jacobi_eig(H, Q, K, cs, pr, red, 30, 1e-15);
     sort_diag(H, K, order);
-    if (threadIdx.x < K) theta[threadIdx.x] = H[order[threadIdx.x] * K + order[threadIdx.x]];
+    if (threadIdx.x < K) {
+      const double t = H[order[threadIdx.x] * K + order[threadIdx.x]];
+      theta[threadIdx.x] = t;
+      theta_r[threadIdx.x] = (R)t;
+    }
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) Qr[t] = (R)Q[(t / K) * K + order[t % K]];
+    __syncthreads();
     if (act) {
-      double xn[kKMax], yn[kKMax];
+      // each thread rotates its own cell of X, then of Y (one accumulator set live)
+      for (int pass = 0; pass < 2; ++pass) {
+        R* V = pass ? Y : X;
+        R vn[kKMax];
 #pragma unroll
-      for (int j = 0; j < kKMax; ++j) { xn[j] = 0.0; yn[j] = 0.0; }
-      for (int i = 0; i < K; ++i) {
-        const double xi = X[i * nb + c], yi = Y[i * nb + c];
+        for (int j = 0; j < kKMax; ++j) vn[j] = (R)0;
+        for (int i = 0; i < K; ++i) {
+          const R vi = V[i * nb + c];
 #pragma unroll
-        for (int j = 0; j < kKMax; ++j) {
-          if (j < K) {
-            const double qij = Q[i * K + order[j]];
-            xn[j] += xi * qij;
-            yn[j] += yi * qij;
-          }
+          for (int j = 0; j < kKMax; ++j)
+            if (j < K) vn[j] += vi * Qr[i * K + j];
         }
-      }
 #pragma unroll
-      for (int j = 0; j < kKMax; ++j)
-        if (j < K) { X[j * nb + c] = xn[j]; Y[j * nb + c] = yn[j]; }
+        for (int j = 0; j < kKMax; ++j)
+          if (j < K) V[j * nb + c] = vn[j];
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kKMax; ++j) {
-      vals[j] = 0.0;
+      vals[j] = (R)0;
       if (j < L && act) {
-        const double r = Y[j * nb + c] - theta[j] * X[j * nb + c];
+        const R r = Y[j * nb + c] - theta_r[j] * X[j * nb + c];
         vals[j] = r * r;
       }
     }
@@ -269,34 +315,65 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
     rmax = 0.0;
     for (int j = 0; j < L; ++j) rmax = fmax(rmax, sqrt(fmax(proj[j], 0.0)));
     if (rmax <= tol || it >= max_iter) break;
+    // a first phase stops where its arithmetic stops making progress (three
+    // iterations without a 10% gain): the second phase takes over from there
+    if (block_out) {
+      stall = rmax < 0.9 * rbest ? 0 : stall + 1;
+      rbest = fmin(rbest, rmax);
+      if (stall >= 3) break;
+    }
     // ---- Chebyshev filter of degree mdeg on [a, bup], normalised at 0
-    double a = theta[K - 1];
-    if (!(a < 0.95 * bup)) a = 0.5 * bup;
-    const double c0 = 0.5 * (a + bup), e0 = 0.5 * (bup - a);
-    const double sig = -e0 / c0;
-    double* Yc = Y;   // current  (degree j)
-    double* Xp = X;   // previous (degree j-1)
-    if (act)
-      for (int q = 0; q < K; ++q)
-        Yc[q * nb + c] = (sig / e0) * (op.apply(Xp + q * nb, c, lx, ly, lz) - c0 * Xp[q * nb + c]);
+    // (three-term recurrence with scaling sigma_j; the coefficients are
+    // computed once by one thread)
+    if (threadIdx.x == 0) {
+      double a = theta[K - 1];
+      if (!(a < 0.95 * bup)) a = 0.5 * bup;
+      const double c0 = 0.5 * (a + bup), e0 = 0.5 * (bup - a);
+      const double sig = -e0 / c0;
+      coef[0] = (R)(sig / e0);
+      coef[1] = (R)c0;
+      double sj = sig;
+      for (int step = 2; step <= mdeg; ++step) {
+        const double sn = 1.0 / (2.0 / sig - sj);
+        coef[2 * step - 2] = (R)(2.0 * sn / e0);
+        coef[2 * step - 1] = (R)(sj * sn);
+        sj = sn;
+      }
+    }
     __syncthreads();
-    double sj = sig;
+    R* Yc = Y;   // current  (degree j)
+    R* Xp = X;   // previous (degree j-1)
+    const R cc = coef[1];
+    if (act) {
+      const R f0 = coef[0];
+      for (int q = 0; q < K; ++q) Yc[q * nb + c] = f0 * (op.apply(Xp + q * nb, c, lx, ly, lz) - cc * Xp[q * nb + c]);
+    }
+    __syncthreads();
     for (int step = 2; step <= mdeg; ++step) {
-      const double sn = 1.0 / (2.0 / sig - sj);
-      if (act)
+      if (act) {
+        const R f1 = coef[2 * step - 2], f2 = coef[2 * step - 1];
         for (int q = 0; q < K; ++q)
-          Xp[q * nb + c] = (2.0 * sn / e0) * (op.apply(Yc + q * nb, c, lx, ly, lz) - c0 * Yc[q * nb + c]) -
-                           sj * sn * Xp[q * nb + c];
+          Xp[q * nb + c] = f1 * (op.apply(Yc + q * nb, c, lx, ly, lz) - cc * Yc[q * nb + c]) - f2 * Xp[q * nb + c];
+      }
       __syncthreads();
-      double* t = Yc; Yc = Xp; Xp = t;
-      sj = sn;
+      R* t = Yc; Yc = Xp; Xp = t;
     }
     X = Yc;
     Y = Xp;
   }
+  if (block_out) {
+    // first phase: hand the whole block to the second
+    if (act)
+      for (int q = 0; q < K; ++q) block_out[((size_t)e * K + q) * nb + c] = (float)X[q * nb + c];
+    if (threadIdx.x == 0) {
+      atomicMax(&flags[3], it);
+      atomicAdd(&flags[4], it);
+    }
+    return;
+  }
   // ---- output: Phi = S^{-1/2} y for the L smallest
   if (act)
-    for (int k = 0; k < L; ++k) Phi[(e * L + k) * nb + c] = X[k * nb + c] / sq;
+    for (int k = 0; k < L; ++k) Phi[(e * L + k) * nb + c] = (double)X[k * nb + c] / sq;
   if (threadIdx.x < L) lam[e * L + threadIdx.x] = theta[threadIdx.x];
   if (threadIdx.x == 0) {
     atomic_max_pos(&stats[0], rmax);
@@ -306,7 +383,13 @@ __global__ void __launch_bounds__(512) k_eig_l1_chfsi(const double* __restrict__
   }
 }
 
-int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess) {
+// Mixed form: a first FP32 phase to residual kMixedPhase1Tol (on the symmetric
+// form, whose spectrum lies in [0, 8]: FP32 resolves residuals down to ~1e-6),
+// then an FP64 phase from that block to eig_tol.  The FP64 form runs the FP64
+// phase alone.  block is scratch for the FP32 block (m K nb floats) or null.
+constexpr double kMixedPhase1Tol = 2e-5;
+
+int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess, float* block) {
   FineLevel& f = c->fine;
   const int L = f.L;
   int guard = L / 2 > 4 ? L / 2 : 4;
@@ -314,15 +397,26 @@ int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess) {
   if (K > kKMax) K = kKMax;
   if (K > f.nb) K = f.nb;
   const int cx = f.bx < 4 ? f.bx : 4, cy = f.by < 4 ? f.by : 4, cz = f.bz < 4 ? f.bz : 4;
+  constexpr int mdeg = 10;
+  static_assert(mdeg <= kMdegMax, "filter degree");
   if (L >= kKMax || K > cx * cy * cz || f.nb > 512) return MSMG_ERR_UNSUPPORTED;
   const int max_iter = c->opts.eig_max_iter > 0 ? c->opts.eig_max_iter : 200;
   const double tol = c->opts.eig_tol > 0 ? c->opts.eig_tol : 1e-12;
-  const size_t sm = (size_t)(4 * f.nb + 2 * K * f.nb + 2 * K * K + kKMax * 2 + kKMax * 32 + kKMax + 2 + 72 + 8) *
-                        sizeof(double) + (size_t)(kKMax + 2 + kKMax + 3 * kKMax) * sizeof(int) + 64;
-  cudaFuncSetAttribute(k_eig_l1_chfsi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const unsigned thr = (unsigned)((f.nb + 31) / 32 * 32);
-  k_eig_l1_chfsi<<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, L, K, 10, max_iter, tol, guess,
-                                                f.Phi, f.lam, c->dtmp, c->flags);
+  const int guess_vecs = guess ? L - 1 : 0;
+  if (block) {
+    const size_t sm1 = chfsi_smem(f.nb, K, sizeof(float));
+    cudaFuncSetAttribute(k_eig_l1_chfsi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    const double tol1 = tol > kMixedPhase1Tol ? tol : kMixedPhase1Tol;
+    k_eig_l1_chfsi<float><<<(unsigned)f.m, thr, sm1, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, L, K, mdeg, max_iter,
+                                                          tol1, guess, guess_vecs, block, nullptr, nullptr, c->dtmp,
+                                                          c->flags);
+  }
+  const size_t sm = chfsi_smem(f.nb, K, sizeof(double));
+  cudaFuncSetAttribute(k_eig_l1_chfsi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_eig_l1_chfsi<double><<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, L, K, mdeg, max_iter, tol,
+                                                        block ? block : guess, block ? K : guess_vecs, nullptr, f.Phi,
+                                                        f.lam, c->dtmp, c->flags);
   return 0;
 }
 

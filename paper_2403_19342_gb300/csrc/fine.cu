@@ -370,7 +370,11 @@ int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s) {
     pcg_step_pmatvec(c, B.sc, s);
     cudaEventRecord(ev[7], s);
     cudaError_t e = cudaEventSynchronize(ev[7]);
-    if (e != cudaSuccess) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e);
+      for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+      return MSMG_ERR_CUDA;
+    }
     float ms;
     const int seg[5][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {2, 3}};
     for (int k = 0; k < 5; ++k) {

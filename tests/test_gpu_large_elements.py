@@ -92,3 +92,27 @@ def test_homogeneous_closed_form_eigenvalues(pkg):
     vals = np.sort((2 * (1 - np.cos(np.pi * k[:, None, None] / 8)) + 2 * (1 - np.cos(np.pi * k[None, :, None] / 8))
                     + 2 * (1 - np.cos(np.pi * k[None, None, :] / 8))).ravel() / 3)[:7]
     np.testing.assert_allclose(lam.cpu().numpy(), np.tile(vals, (8, 1)), atol=1e-12)
+
+
+def test_mixed_form_two_phase_eigenpairs(pkg, incl):
+    """The mixed form's eigensolve (an FP32 phase, then FP64 polishing of the
+    whole block) reaches the same tolerance and the same eigenpairs as LAPACK."""
+    kappa, H, _ = incl
+    go = pkg.Options(n_levels=3, block=(8, 8, 8), ratio=[(2, 2, 2)], n_eig=[7, 7], eig_tol=1e-12,
+                     precision=pkg.MIXED)
+    S = pkg.Solver(torch.tensor(kappa, device="cuda"), go)
+    assert S.setup_status == 0
+    assert S.info["eig_residual_max"] <= 1e-12
+    Phi, lam = S.export_basis(1)
+    Phi, lam = Phi.cpu().numpy(), lam.cpu().numpy()
+    np.testing.assert_allclose(lam, H.lam[0], atol=1e-10)
+    Po = H.basis[0]
+    L = Po.shape[1]
+    lam_next, _, _ = oracle.level1_eigenpairs(H.T, H.S, (8, 8, 8), L + 1)
+    for e in range(Phi.shape[0]):
+        gap = lam_next[e, L] - lam_next[e, L - 1]
+        if gap < 1e-6:
+            continue
+        P1, P2 = Phi[e].T @ Phi[e], Po[e].T @ Po[e]
+        assert np.abs(P1 - P2).max() <= max(1e-8, 1e-10 / gap) * np.abs(P2).max(), (e, gap)
+    S.close()
