@@ -103,6 +103,20 @@ def kernel_bytes(form: str, L: int, R: int = 1, fused: bool = False) -> dict:
 
 VCYCLE_FINE = ("pre", "restrict", "prolong", "post")
 
+# Algorithmic FP64 flops per fine cell and launch in the mixed form (FMA = 2):
+#   pre      x += alpha p, r -= alpha q, r.r                          3 FMA
+#   post     r.z and z.q (flexible beta)                              2 FMA
+#   pmatvec  p = z + beta p_old, (A p)_c = D_c p_c - 6 T p_nb, p.q   1 MUL + 8 FMA
+# (restrict and prolong run in FP32.)  GB300 issues FP64 at 2 FMA per clock
+# per SM, so these are the kernels whose FP64 rate can bind before HBM does.
+FP64_FLOPS_MIXED = {"pre": 6, "restrict": 0, "prolong": 0, "post": 4, "pmatvec": 17}
+N_SMS = 152
+
+
+def fp64_peak_gflops(sm_mhz: float) -> float:
+    """FP64 peak from unit counts and clock: 152 SMs x 2 FMA/clock x 2 flops."""
+    return N_SMS * 2 * 2 * sm_mhz * 1e-3
+
 
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -390,11 +404,30 @@ def run_gpu(args, world, rank, local):
     kt = kernel_times["mixed"]
     fine = {k: kt[k] for k in ("pre", "restrict", "prolong", "post", "pmatvec") if kb[k] > 0}
     dom = max(fine, key=fine.get)
-    achieved = kb[dom] * n / (kt[dom] * 1e-3) / 1e9
+    # each fine kernel against both of its ceilings: HBM bandwidth (measured copy
+    # peak) and the FP64 rate (from unit counts at the maximum SM clock)
+    f64_peak = fp64_peak_gflops(float(clocks.get("sm_max_mhz") or 2070.0))
+    per_kernel = {}
+    for k, t in fine.items():
+        gbs = kb[k] * n / (t * 1e-3) / 1e9
+        gfl = FP64_FLOPS_MIXED[k] * n / (t * 1e-3) / 1e9
+        per_kernel[k] = {"ms": t, "hbm_gbs": gbs, "hbm_frac": gbs / peak, "fp64_gflops": gfl,
+                         "fp64_frac": gfl / f64_peak}
+    pk = per_kernel[dom]
     traffic = traffic_record(dom, forms["mixed"]["tuning"][0] == 1)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": kb[dom] * n, "avg_launch_ms": kt[dom]}
+    if pk["fp64_frac"] > pk["hbm_frac"]:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": pk["fp64_gflops"] * 1e-3,
+                    "peak": f64_peak * 1e-3, "unit": "TFLOP/s", "frac": pk["fp64_frac"], "traffic": traffic,
+                    "peak_source": "derived: FP64, 152 SMs x 2 FMA/clock x 2 flops x max SM clock",
+                    "algorithmic_flops_per_launch": FP64_FLOPS_MIXED[dom] * n,
+                    "hbm": {"achieved": pk["hbm_gbs"], "peak": peak, "unit": "GB/s", "frac": pk["hbm_frac"],
+                            "peak_source": peak_kind},
+                    "algorithmic_bytes_per_launch": kb[dom] * n, "avg_launch_ms": kt[dom]}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": pk["hbm_gbs"], "peak": peak, "unit": "GB/s",
+                    "frac": pk["hbm_frac"], "traffic": traffic, "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": kb[dom] * n, "avg_launch_ms": kt[dom]}
+    roofline["per_kernel"] = per_kernel
     vc_bytes = sum(kb[k] for k in VCYCLE_FINE) * n
     vc_frac = vc_bytes / (kt["vcycle"] * 1e-3) / 1e9 / peak
     kb64 = kernel_bytes("fp64", L, fused=forms["fp64"]["tuning"][0] == 1)

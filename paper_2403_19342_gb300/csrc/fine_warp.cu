@@ -182,6 +182,15 @@ struct WStage {
   V *ut, *t0, *t1, *t2, *tm0, *tm1, *tm2, *dinv, *y;
 };
 constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2;
+// Warps (one element each) per CTA of the staged kernels: the CTA size that
+// keeps the most warps resident per SM for the staging footprint of an 8^3
+// element (FP32: 11 KB per warp for k_pre and k_restrict, 15 KB for k_post;
+// FP64 twice that), which also sets how many elements one wave covers.
+template <int LAYOUT, typename V>
+__host__ __device__ constexpr int stage_warps() {
+  if (sizeof(V) == 4) return LAYOUT == kStageFull ? 2 : 4;
+  return LAYOUT == kStageFull ? 1 : 2;
+}
 __host__ __device__ constexpr int r4(int x) { return (x + 3) / 4 * 4; }
 template <int LAYOUT, typename G>
 __host__ __device__ inline int wstage_elems(const G& g) {
@@ -374,7 +383,7 @@ __device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane
 // update != 0: x += alpha p, r -= alpha q, rr = r.r (convergence bookkeeping);
 // then f = r (in V precision, also written to rv) and u = M^{-1} f.
 template <typename V, typename G>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ x, double* __restrict__ r,
+__global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double* __restrict__ x, double* __restrict__ r,
                                                            const double* __restrict__ p, const double* __restrict__ q,
                                                            const V* __restrict__ T, const V* __restrict__ invd,
                                                            V* __restrict__ rv, V* __restrict__ u, int64_t n, G g,
@@ -389,11 +398,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
   }
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
+  constexpr int W = stage_warps<kStagePre, V>();
+  const int64_t e = (int64_t)bi.blk * W + warp;
   const bool act = e < m;
   const WStage<V> s = w_stage<V, kStagePre>(smem, g, warp);
-  const unsigned short* tab =
-      w_plane_table<G>(smem + (size_t)kWarpsPerCta * wstage_elems<kStagePre>(g) * sizeof(V));
+  const unsigned short* tab = w_plane_table<G>(smem + (size_t)W * wstage_elems<kStagePre>(g) * sizeof(V));
   double acc = 0.0;
   if (act) {
     const WElem E = w_elem(e, nbr, g);
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pre(double* __restrict__ 
 // Residual in registers (each lane's cells), then one warp reduction per local
 // eigenvector; every global load is issued before the first use.
 template <typename V, typename BT, typename G>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_restrict(const V* __restrict__ f, const V* __restrict__ u,
+__global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32) k_restrict(const V* __restrict__ f, const V* __restrict__ u,
                                                                 const V* __restrict__ T, const BT* __restrict__ Phi,
                                                                 int L, double* __restrict__ rc, int64_t nc, int64_t n,
                                                                 G g, int64_t m, const int* __restrict__ nbr,
@@ -469,7 +478,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_restrict(const V* __restr
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kC = 16;                                   // cells per lane held in registers
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
+  const int64_t e = (int64_t)bi.blk * stage_warps<kStageRestrict, V>() + warp;
   if (e >= m) return;
   const WStage<V> s = w_stage<V, kStageRestrict>(smem, g, warp);
   const WElem E = w_elem(e, nbr, g);
@@ -663,7 +672,7 @@ __global__ void __launch_bounds__(256) k_prolong(V* __restrict__ u, const BT* __
 // z = u + M^{-1} (f - A u), written in FP64; reductions: r.z and z.q (flexible
 // beta).  f, r and q are loaded into registers before the wavefronts start.
 template <typename V, typename BT, typename G, bool FUSE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict__ f, const double* __restrict__ r,
+__global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(const V* __restrict__ f, const double* __restrict__ r,
                                                             const V* __restrict__ u, const V* __restrict__ T,
                                                             const V* __restrict__ invd, const BT* __restrict__ Phi,
                                                             const V* __restrict__ ec, int L, int64_t nc,
@@ -682,11 +691,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_post(const V* __restrict_
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kC = 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
+  constexpr int W = stage_warps<kStageFull, V>();
+  const int64_t e = (int64_t)bi.blk * W + warp;
   const bool act = e < m;
   const WStage<V> s = w_stage<V>(smem, g, warp);
-  const unsigned short* tab =
-      w_plane_table<G>(smem + (size_t)kWarpsPerCta * wstage_elems<kStageFull>(g) * sizeof(V));
+  const unsigned short* tab = w_plane_table<G>(smem + (size_t)W * wstage_elems<kStageFull>(g) * sizeof(V));
   const int ncl = (g.nb + 31) / 32;
   double v[2] = {0.0, 0.0};
   if (act && ncl <= kC) {
@@ -911,9 +920,10 @@ struct FineOps {
   const BT* Phi;
 };
 
-template <int LAYOUT, typename G>
-static inline size_t wsmem(const G& g, size_t vsize) {
-  return (size_t)kWarpsPerCta * wstage_elems<LAYOUT>(g) * vsize + (LAYOUT == kStageRestrict ? 0 : plane_smem(g));
+template <int LAYOUT, typename V, typename G>
+static inline size_t wsmem(const G& g) {
+  return (size_t)stage_warps<LAYOUT, V>() * wstage_elems<LAYOUT>(g) * sizeof(V) +
+         (LAYOUT == kStageRestrict ? 0 : plane_smem(g));
 }
 template <typename G>
 static inline size_t wsmem_p(const G& g) {
@@ -930,14 +940,15 @@ static void with_geo(const msmg_ctx* c, F&& f) {
 }
 
 // CTAs of a batched fine-level launch: element groups x right-hand sides
-static inline unsigned fine_wgrid(const msmg_ctx* c) {
-  return (unsigned)((c->fine.m + kWarpsPerCta - 1) / kWarpsPerCta * c->sb.R);
+static inline unsigned fine_wgrid(const msmg_ctx* c, int W = kWarpsPerCta) {
+  return (unsigned)((c->fine.m + W - 1) / W * c->sb.R);
 }
 
 template <typename V, typename BT, typename G>
 static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  k_pre<V, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStagePre>(g, sizeof(V)), s>>>(
+  constexpr int W = stage_warps<kStagePre, V>();
+  k_pre<V, G><<<fine_wgrid(c, W), W * 32, wsmem<kStagePre, V>(g), s>>>(
       B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv, (V*)B.vu[1], c->n, g, c->fine.m, c->fine.nbr, update, c->red, sc,
       B.R);
 }
@@ -945,7 +956,8 @@ static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* 
 template <typename V, typename BT, typename G>
 static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  k_restrict<V, BT, G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStageRestrict>(g, sizeof(V)), s>>>(
+  constexpr int W = stage_warps<kStageRestrict, V>();
+  k_restrict<V, BT, G><<<fine_wgrid(c, W), W * 32, wsmem<kStageRestrict, V>(g), s>>>(
       (const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
       c->fine.nbr, sc, B.R);
 }
@@ -954,12 +966,13 @@ template <typename V, typename BT, typename G>
 static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, const double* qv, PcgScalars* sc,
                    cudaStream_t s, const G& g, bool fuse) {
   SolveBuffers& B = c->sb;
+  constexpr int W = stage_warps<kStageFull, V>();
   if (fuse)
-    k_post<V, BT, G, true><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStageFull>(g, sizeof(V)), s>>>(
+    k_post<V, BT, G, true><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
         c->fine.m, c->fine.nbr, c->red, sc, B.R);
   else
-    k_post<V, BT, G, false><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem<kStageFull>(g, sizeof(V)), s>>>(
+    k_post<V, BT, G, false><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
         c->fine.m, c->fine.nbr, c->red, sc, B.R);
 }
@@ -984,11 +997,10 @@ static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s, const G& g) {
 // during stream capture).
 template <typename V, typename BT, typename G>
 static void prepare_t(const G& g) {
-  const int smv = (int)wsmem<kStageFull>(g, sizeof(V)), smd = (int)wsmem_p(g);
-  cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)wsmem<kStagePre>(g, sizeof(V)));
+  const int smv = (int)wsmem<kStageFull, V>(g), smd = (int)wsmem_p(g);
+  cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem<kStagePre, V>(g));
   cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)wsmem<kStageRestrict>(g, sizeof(V)));
+                       (int)wsmem<kStageRestrict, V>(g));
   cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_post<V, BT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);

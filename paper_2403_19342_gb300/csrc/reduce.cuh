@@ -53,6 +53,9 @@ __device__ __forceinline__ void grid_reduce_b(double (&v)[W], const RedSlot& red
   double acc[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) acc[w] = 0.0;
+  // (unrolled so that the loads are in flight together; the order of the sums
+  // is unchanged)
+#pragma unroll 8
   for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) {
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] += __ldcg(&red.partials[(size_t)i * W + w]);
