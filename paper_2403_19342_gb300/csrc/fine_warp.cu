@@ -782,8 +782,12 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
 
 // ------------------------------------------------------------------ k_pmatvec
 // p = z + beta p_old on the element and its halo, q = A p (FP64), reduce p.q.
+// FP64-rate bound on GB300, so it is built for residency: three warps per CTA
+// (8 KB tile each) and at most 72 registers, nine CTAs per SM, 27 warps -- one
+// wave for 4104 elements.
+constexpr int kPmWarps = 3, kPmCtasPerSm = 9;
 template <typename G>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __restrict__ z, const double* __restrict__ pold,
+__global__ void __launch_bounds__(kPmWarps * 32, kPmCtasPerSm) k_pmatvec(const double* __restrict__ z, const double* __restrict__ pold,
                                                                double* __restrict__ pnew, double* __restrict__ q,
                                                                const double* __restrict__ T,
                                                                const double* __restrict__ Dg, int64_t n, G g,
@@ -798,7 +802,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __r
   }
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)bi.blk * kWarpsPerCta + warp;
+  const int64_t e = (int64_t)bi.blk * kPmWarps + warp;
   const bool act = e < m;
   double* ut = reinterpret_cast<double*>(smem) + (size_t)warp * r4(g.P);
   double acc = 0.0;
@@ -806,9 +810,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __r
     const double beta = sc->beta;
     const WElem E = w_elem(e, nbr, g);
     const int64_t base = E.base;
-    constexpr int kC = 16;                       // cells per lane (8^3 elements)
+    constexpr int kC = 8;                        // cells per lane and batch
     const int ncl = (g.nb + 31) / 32;
-    // p on the element: every load issued before the first use
+    // p on the element: every load of a batch issued before the first use
     for (int i0 = 0; i0 < ncl; i0 += kC) {
       double zz[kC], po[kC];
 #pragma unroll
@@ -864,11 +868,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __r
     }
     __syncwarp();
     const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
-    // q = A p: coefficients of a group of 4 cells loaded before the products
-    for (int i0 = 0; i0 < ncl; i0 += 4) {
-      double t0[4], t1[4], t2[4], dg[4], mx[4], my[4], mz[4];
+    // q = A p: coefficients of a group of kQ cells loaded before the products
+    constexpr int kQ = 2;
+    for (int i0 = 0; i0 < ncl; i0 += kQ) {
+      double t0[kQ], t1[kQ], t2[kQ], dg[kQ], mx[kQ], my[kQ], mz[kQ];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kQ; ++j) {
         const int c = lane + 32 * (i0 + j);
         t0[j] = t1[j] = t2[j] = dg[j] = mx[j] = my[j] = mz[j] = 0.0;
         if (!(i0 + j < ncl && c < g.nb)) continue;
@@ -885,7 +890,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_pmatvec(const double* __r
                        : (E.nb6[4] >= 0 ? __ldg(T + 2 * n + E.nb6[4] + c + g.bx * g.by * (g.bz - 1)) : 0.0);
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kQ; ++j) {
         const int c = lane + 32 * (i0 + j);
         if (!(i0 + j < ncl && c < g.nb)) continue;
         const int lx = c % g.bx, t = c / g.bx, ly = t % g.by, lz = t / g.by;
@@ -927,7 +932,7 @@ static inline size_t wsmem(const G& g) {
 }
 template <typename G>
 static inline size_t wsmem_p(const G& g) {
-  return (size_t)kWarpsPerCta * r4(g.P) * sizeof(double);
+  return (size_t)kPmWarps * r4(g.P) * sizeof(double);
 }
 
 // run f(geometry) with the compile-time geometry of the element when available
@@ -988,7 +993,7 @@ static void prolong_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, PcgScal
 template <typename G>
 static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  k_pmatvec<G><<<fine_wgrid(c), kWarpsPerCta * 32, wsmem_p(g), s>>>(B.z, B.pcur, B.pnext, B.q, c->fine.T, c->fine.D,
+  k_pmatvec<G><<<fine_wgrid(c, kPmWarps), kPmWarps * 32, wsmem_p(g), s>>>(B.z, B.pcur, B.pnext, B.q, c->fine.T, c->fine.D,
                                                                       c->n, g, c->fine.m, c->fine.nbr, c->red, sc, B.R);
 }
 
@@ -1004,6 +1009,7 @@ static void prepare_t(const G& g) {
   cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_post<V, BT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
+  cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
 void prepare_fine_kernels(msmg_ctx* c) {
