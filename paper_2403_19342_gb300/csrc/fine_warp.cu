@@ -55,6 +55,7 @@ static inline GeoR make_geor(int bx, int by, int bz) {
 }
 
 constexpr int kWarpsPerCta = 4;
+constexpr int kProlongLMax = 8;   // local basis sizes with all loads of a cell in flight at once
 
 template <typename G>
 __device__ __forceinline__ int wpad(const G& g, int lx, int ly, int lz) {
@@ -176,7 +177,8 @@ __device__ __forceinline__ void w_cp_tminus(V* tm0, V* tm1, V* tm2, const V* __r
 // only what it uses (more warps fit on an SM):
 //   kStageFull      u tile with halo, T, 1/d, y, -d face coefficients (k_post)
 //   kStagePre       T, 1/d, y, -d face coefficients             (k_pre)
-//   kStageRestrict  u tile with halo, T, -d face coefficients     (k_restrict)
+//   kStageRestrict  u tile with halo                              (k_restrict,
+//                   which reads its face coefficients into registers)
 template <typename V>
 struct WStage {
   V *ut, *t0, *t1, *t2, *tm0, *tm1, *tm2, *dinv, *y;
@@ -188,15 +190,16 @@ constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2;
 // FP64 twice that), which also sets how many elements one wave covers.
 template <int LAYOUT, typename V>
 __host__ __device__ constexpr int stage_warps() {
+  if (LAYOUT == kStageRestrict) return 4;
   if (sizeof(V) == 4) return LAYOUT == kStageFull ? 2 : 4;
   return LAYOUT == kStageFull ? 1 : 2;
 }
 __host__ __device__ constexpr int r4(int x) { return (x + 3) / 4 * 4; }
 template <int LAYOUT, typename G>
 __host__ __device__ inline int wstage_elems(const G& g) {
+  if (LAYOUT == kStageRestrict) return r4(g.P);
   const int tut = LAYOUT == kStagePre ? 0 : r4(g.P);
-  const int nv = LAYOUT == kStageRestrict ? 3 : 5;
-  return tut + nv * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
+  return tut + 5 * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
 }
 template <typename V, int LAYOUT = kStageFull, typename G>
 __device__ __forceinline__ WStage<V> w_stage(unsigned char* base, const G& g, int warp) {
@@ -462,13 +465,16 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
 
 // ------------------------------------------------------------------ k_restrict
 // Residual in registers (each lane's cells), then one warp reduction per local
-// eigenvector; every global load is issued before the first use.
+// eigenvector.  Only the u tile is staged (4 KB per warp in FP32): the face
+// coefficients of a group of cells are read straight into registers, so seven
+// CTAs of four warps fit on an SM and the 4096 elements of a 128^3 grid take
+// one wave.  The basis loads of all eigenvectors are issued cell by cell into
+// L accumulators (the sum over each eigenvector's cells keeps its order).
 template <typename V, typename BT, typename G>
-__global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32) k_restrict(const V* __restrict__ f, const V* __restrict__ u,
-                                                                const V* __restrict__ T, const BT* __restrict__ Phi,
-                                                                int L, double* __restrict__ rc, int64_t nc, int64_t n,
-                                                                G g, int64_t m, const int* __restrict__ nbr,
-                                                                const PcgScalars* sc, int R) {
+__global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32, sizeof(V) == 4 ? 7 : 4)
+    k_restrict(const V* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T, const BT* __restrict__ Phi,
+               int L, double* __restrict__ rc, int64_t nc, int64_t n, G g, int64_t m, const int* __restrict__ nbr,
+               const PcgScalars* sc, int R) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -480,35 +486,83 @@ __global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32) k_restr
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)bi.blk * stage_warps<kStageRestrict, V>() + warp;
   if (e >= m) return;
-  const WStage<V> s = w_stage<V, kStageRestrict>(smem, g, warp);
+  V* ut = reinterpret_cast<V*>(smem) + (size_t)warp * r4(g.P);
   const WElem E = w_elem(e, nbr, g);
-  w_cp_padded(s.ut, u + E.base, g, lane);
-  w_cp_halo(s.ut, u, E, g, lane);
-  w_stage_T(s, T, (const V*)nullptr, n, E, g, lane, false);
+  w_cp_padded(ut, u + E.base, g, lane);
+  w_cp_halo(ut, u, E, g, lane);
   const int ncl = (g.nb + 31) / 32;            // <= kC: elements have at most 512 cells
-  {
-    V w[kC];
+  const int bxy = g.bx * g.by;
+  const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
+  V w[kC];
+#pragma unroll
+  for (int i = 0; i < kC; ++i) {
+    const int c = lane + 32 * i;
+    w[i] = (i < ncl && c < g.nb) ? __ldg(f + E.base + c) : (V)0;
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  // w -= A u: the six face coefficients of kG cells loaded before the products
+  // (-d faces on the element boundary are held by the -d neighbour)
+  constexpr int kG = 2;
+#pragma unroll
+  for (int i0 = 0; i0 < kC; i0 += kG) {
+    V t0[kG], t1[kG], t2[kG], mx[kG], my[kG], mz[kG];
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const int c = lane + 32 * (i0 + j);
+      t0[j] = t1[j] = t2[j] = mx[j] = my[j] = mz[j] = (V)0;
+      if (!(i0 + j < ncl && c < g.nb)) continue;
+      const int lx = c % g.bx, t = c / g.bx, ly = t % g.by, lz = t / g.by;
+      t0[j] = __ldg(T + E.base + c);
+      t1[j] = __ldg(T + n + E.base + c);
+      t2[j] = __ldg(T + 2 * n + E.base + c);
+      mx[j] = lx > 0 ? __ldg(T + E.base + c - 1) : (E.nb6[0] >= 0 ? __ldg(T + E.nb6[0] + c + g.bx - 1) : (V)0);
+      my[j] = ly > 0 ? __ldg(T + n + E.base + c - g.bx)
+                     : (E.nb6[2] >= 0 ? __ldg(T + n + E.nb6[2] + c + g.bx * (g.by - 1)) : (V)0);
+      mz[j] = lz > 0 ? __ldg(T + 2 * n + E.base + c - bxy)
+                     : (E.nb6[4] >= 0 ? __ldg(T + 2 * n + E.nb6[4] + c + bxy * (g.bz - 1)) : (V)0);
+    }
+#pragma unroll
+    for (int j = 0; j < kG; ++j) {
+      const int c = lane + 32 * (i0 + j);
+      if (!(i0 + j < ncl && c < g.nb)) continue;
+      const int lx = c % g.bx, t = c / g.bx;
+      const int pc = wpad(g, lx, t % g.by, t / g.by);
+      const V uc = ut[pc];
+      V acc = t0[j] * (uc - ut[pc + 1]) + mx[j] * (uc - ut[pc - 1]);
+      acc += t1[j] * (uc - ut[pc + sy]) + my[j] * (uc - ut[pc - sy]);
+      acc += t2[j] * (uc - ut[pc + sz]) + mz[j] * (uc - ut[pc - sz]);
+      w[i0 + j] -= acc;
+    }
+  }
+  // rc_k = Phi_k . w, accumulated in the V-cycle precision (FP32 in the mixed
+  // form: the FP64 pipe runs at 1/64 of the FP32 rate)
+  const BT* ph = Phi + (size_t)e * L * g.nb;
+  if (L <= kProlongLMax) {
+    V acc[kProlongLMax];
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k) acc[k] = (V)0;
 #pragma unroll
     for (int i = 0; i < kC; ++i) {
       const int c = lane + 32 * i;
-      w[i] = (i < ncl && c < g.nb) ? __ldg(f + E.base + c) : (V)0;
-    }
-    cp_async_wait_all();
-    __syncwarp();
+      if (!(i < ncl && c < g.nb)) continue;
 #pragma unroll
-    for (int i = 0; i < kC; ++i) {
-      const int c = lane + 32 * i;
-      if (i < ncl && c < g.nb) w[i] -= w_apply_A_s(s, g, c);
+      for (int k = 0; k < kProlongLMax; ++k)
+        if (k < L) acc[k] += (V)__ldg(ph + (size_t)k * g.nb + c) * w[i];
     }
-    // accumulate in the V-cycle precision (FP32 in the mixed form: the FP64 pipe
-    // runs at 1/64 of the FP32 rate)
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k) {
+      if (k >= L) break;
+      const V a = warp_sum_t(acc[k]);
+      if (lane == 0) rc[e * L + k] = (double)a;
+    }
+  } else {
     for (int k = 0; k < L; ++k) {
-      const BT* ph = Phi + (e * L + k) * g.nb;
       V acc = (V)0;
 #pragma unroll
       for (int i = 0; i < kC; ++i) {
         const int c = lane + 32 * i;
-        if (i < ncl && c < g.nb) acc += (V)__ldg(ph + c) * w[i];
+        if (i < ncl && c < g.nb) acc += (V)__ldg(ph + (size_t)k * g.nb + c) * w[i];
       }
       acc = warp_sum_t(acc);
       if (lane == 0) rc[e * L + k] = (double)acc;
@@ -523,7 +577,6 @@ __global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32) k_restr
 // sum_k Phi[ne][k][c] ec[ne][k], accumulated in the V-cycle precision in k
 // order.  All L basis loads of a group of cells are issued before the first
 // product (L <= kProlongLMax; larger L takes the plain loop).
-constexpr int kProlongLMax = 8;
 
 template <typename V, typename BT>
 __device__ __forceinline__ void w_corr_group(V* ut, const BT* __restrict__ ph, const V (&ev)[kProlongLMax], int L,
@@ -1006,6 +1059,8 @@ static void prepare_t(const G& g) {
   cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem<kStagePre, V>(g));
   cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)wsmem<kStageRestrict, V>(g));
+  cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_post<V, BT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
