@@ -18,6 +18,7 @@ int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream
 bool net_matches(const msmg_ctx* c, const msmg_net* net);
 int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
 int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s);
+int time_iterations(msmg_ctx* c, int R, int reps, double* ms_out, cudaStream_t s);
 int pcg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs, double* const* x,
                       const int* n_rhs, double rtol, int max_iter, int flags, cudaStream_t s,
                       msmg_solve_info* info);
@@ -261,10 +262,10 @@ static int autotune(msmg_ctx* c, int R, int reps, cudaStream_t s) {
       if (!((forms >> tail) & 1)) continue;
       c->tune_fused[cls] = v;
       c->tune_tail[cls] = tail;
-      double acc[7];
-      int st = time_kernels(c, R, reps, acc, s);
+      double ms = 0.0;
+      int st = time_iterations(c, R, reps, &ms, s);
       if (st) return st;
-      if (acc[6] < best) { best = acc[6]; bf = v; bt = tail; }
+      if (ms < best) { best = ms; bf = v; bt = tail; }
     }
   c->tune_fused[cls] = bf;
   c->tune_tail[cls] = bt;

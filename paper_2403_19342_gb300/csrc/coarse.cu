@@ -279,7 +279,9 @@ __global__ void k_dense_gemv(const double* __restrict__ A, const S* __restrict__
 //   grid:    a cooperative launch over the whole GPU for all right-hand sides
 //            and all coarse levels, grid barriers.
 // Work items are (right-hand side, parent) pairs: each is handled by a group of
-// ceil(max(nP, Lnext, 64) / 32) warps with thread t on row t, and every row,
+// ceil(max(nP, Lnext, 64) / 32) warps with thread t on row t; item i goes to
+// CTA i mod ncta (group i / ncta), so a level with fewer items than group slots
+// still spreads over every CTA's SM.  Every row,
 // restriction and GEMV is evaluated by the same code and reduction order as the
 // per-level kernels above, so every form gives the same bits.  A right-hand
 // side that has converged skips its items but every thread reaches every
@@ -353,8 +355,8 @@ __device__ void tail_level_down(const TailArgs& A, int l, int r0, int r1, int ct
   double* Mi = sm + (size_t)grp * tail_group_doubles(nP, Ln, gw);
   double* fs = Mi + (size_t)nP * nP;                        // [nP] right side, then [Ln][gw] partials
   // pre-smoothing from zero: u_P = Minv_P f_P (the inverse staged, all copies in flight)
-  for (int64_t i0 = (int64_t)cta * G; i0 < items; i0 += (int64_t)ncta * G) {
-    const TailItem it = tail_item(i0 + grp, lv.mP, r0, r1, sc);
+  for (int64_t b0 = 0; b0 < items; b0 += (int64_t)ncta * G) {
+    const TailItem it = tail_item(b0 + (int64_t)grp * ncta + cta, lv.mP, r0, r1, sc);
     const bool live = grp < G && it.live;
     const double* f = A.f[l] + (int64_t)it.r * lv.n;
     double* u = A.u[l] + (int64_t)it.r * lv.n;
@@ -367,8 +369,8 @@ __device__ void tail_level_down(const TailArgs& A, int l, int r0, int r1, int ct
   }
   bar();
   // residual and restriction: fn[P][j] = sum_i Psi[P][j][i] (f - A_l u)_i
-  for (int64_t i0 = (int64_t)cta * G; i0 < items; i0 += (int64_t)ncta * G) {
-    const TailItem it = tail_item(i0 + grp, lv.mP, r0, r1, sc);
+  for (int64_t b0 = 0; b0 < items; b0 += (int64_t)ncta * G) {
+    const TailItem it = tail_item(b0 + (int64_t)grp * ncta + cta, lv.mP, r0, r1, sc);
     const bool live = grp < G && it.live;
     const double* f = A.f[l] + (int64_t)it.r * lv.n;
     const double* u = A.u[l] + (int64_t)it.r * lv.n;
@@ -406,8 +408,8 @@ __device__ void tail_level_up(const TailArgs& A, int l, int r0, int r1, int cta,
   double* Mi = sm + (size_t)grp * tail_group_doubles(nP, Ln, gw);
   double* rs = Mi + (size_t)nP * nP;
   // prolongation: u_P += Psi_P^T e_P
-  for (int64_t i0 = (int64_t)cta * G; i0 < items; i0 += (int64_t)ncta * G) {
-    const TailItem it = tail_item(i0 + grp, lv.mP, r0, r1, sc);
+  for (int64_t b0 = 0; b0 < items; b0 += (int64_t)ncta * G) {
+    const TailItem it = tail_item(b0 + (int64_t)grp * ncta + cta, lv.mP, r0, r1, sc);
     if (grp < G && it.live && t < nP) {
       const double* e = ebase + (int64_t)it.r * lv.mP * Ln;
       double* u = A.u[l] + (int64_t)it.r * lv.n;
@@ -420,8 +422,8 @@ __device__ void tail_level_up(const TailArgs& A, int l, int r0, int r1, int cta,
   }
   bar();
   // post-smoothing: w = u + Minv (f - A_l u)
-  for (int64_t i0 = (int64_t)cta * G; i0 < items; i0 += (int64_t)ncta * G) {
-    const TailItem it = tail_item(i0 + grp, lv.mP, r0, r1, sc);
+  for (int64_t b0 = 0; b0 < items; b0 += (int64_t)ncta * G) {
+    const TailItem it = tail_item(b0 + (int64_t)grp * ncta + cta, lv.mP, r0, r1, sc);
     const bool live = grp < G && it.live;
     const double* f = A.f[l] + (int64_t)it.r * lv.n;
     const double* u = A.u[l] + (int64_t)it.r * lv.n;

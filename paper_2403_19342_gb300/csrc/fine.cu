@@ -343,6 +343,7 @@ __global__ void k_reset_scalars(PcgScalars* scs, int R) {
 void pcg_step_vcycle_timed(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s,
                            cudaEvent_t* ev);
 void pcg_step_pmatvec(msmg_ctx* c, PcgScalars* sc, cudaStream_t s);
+void pcg_step_vcycle(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s);
 
 // Per-kernel device times of one PCG iteration's fine-level work (events on s),
 // for a batch of R right-hand sides.
@@ -388,6 +389,45 @@ int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s) {
   }
   for (int i = 0; i < 7; ++i) acc[i] /= reps;
   for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+  return 0;
+}
+
+// Mean time of one whole PCG iteration (V-cycle and the p / A p kernel),
+// reps of them launched back to back as a solve runs them; the autotuner's
+// criterion.  Same scratch contents as time_kernels.
+int time_iterations(msmg_ctx* c, int R, int reps, double* ms_out, cudaStream_t s) {
+  SolveBuffers& B = c->sb;
+  if (R < 1 || R > B.n_rhs || reps < 1) return MSMG_ERR_INVALID_ARG;
+  B.R = R;
+  const int64_t n = c->n * R;
+  const unsigned g1 = (unsigned)((n + 255) / 256);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.r, n, 0.3);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.p0, n, 1.1);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.q, n, 2.0);
+  k_fill_pattern<<<g1, 256, 0, s>>>(B.x, n, 0.7);
+  B.pcur = B.p0;
+  B.pnext = B.p1;
+  const bool flexible = c->opts.precision == MSMG_MIXED;
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  for (int r = 0; r <= reps; ++r) {      // the first iteration warms up
+    if (r == 1) cudaEventRecord(ev[0], s);
+    k_reset_scalars<<<1, 32 * ((R + 31) / 32), 0, s>>>(B.sc, R);
+    pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, B.sc, s);
+    pcg_step_pmatvec(c, B.sc, s);
+  }
+  cudaEventRecord(ev[1], s);
+  const cudaError_t e = cudaEventSynchronize(ev[1]);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e);
+    return MSMG_ERR_CUDA;
+  }
+  *ms_out = ms / reps;
   return 0;
 }
 
