@@ -256,6 +256,20 @@ int msmg_dot(const double* a, const double* b, int64_t n, void* scratch, double*
 int msmg_dot_noalloc(const double* a, const double* b, int64_t n, double* result_host, msmg_stream stream);
 
 /*
+ * Diagnostics: the FP32 <-> FP64 conversions the mixed-form V-cycle kernels perform
+ * on the integer pipes (GB300 runs the hardware conversions on its FP64 pipe, which
+ * the FP64 PCG arithmetic already keeps busy), applied element by element so that a
+ * caller can compare them bit for bit with the hardware conversions (IEEE 754 round to
+ * nearest, ties to even; the widening is exact; NaN stays NaN).  Not part of the
+ * method: the paper fixes the precisions, not how a conversion is carried out.
+ *   in64   device, n doubles; out32[i] = in64[i] rounded to binary32
+ *   in32   device, n floats;  out64[i] = in32[i] widened to binary64
+ * n <= 0 does nothing.  Asynchronous on ``stream``; MSMG_ERR_CUDA if the launch fails.
+ */
+int msmg_check_conversions(const double* in64, const float* in32, int64_t n, float* out32, double* out64,
+                           msmg_stream stream);
+
+/*
  * Level data in the layouts of the paper's matrices (for parity checks).
  * level l = 1 .. n_levels-1.  Elements of E_l are in lexicographic order (x fastest) of
  * the element grid; the dofs of a level-l local problem are its child elements in

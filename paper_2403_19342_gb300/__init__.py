@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_net_train_step": (I, [P, P, P, I, C.c_float, C.POINTER(C.c_float), P]),
         "msmg_learning_data": (I, [P, P, P, P]),
         "msmg_dot_noalloc": (I, [P, P, I64, C.POINTER(D), P]),
+        "msmg_check_conversions": (I, [P, P, I64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -137,7 +138,7 @@ def exported_symbols():
             "msmg_net_workspace_size", "msmg_net_create",
             "msmg_net_destroy", "msmg_net_param_count", "msmg_net_param_offsets", "msmg_net_get_params",
             "msmg_net_set_params", "msmg_net_forward", "msmg_net_gradients", "msmg_net_train_step",
-            "msmg_learning_data"]
+            "msmg_learning_data", "msmg_check_conversions"]
 
 
 def _check(status: int) -> int:
@@ -312,6 +313,19 @@ def msmg_dot_noalloc(a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
     _check(load_library().msmg_dot_noalloc(_ptr(a, torch.float64), _ptr(b, torch.float64), a.numel(),
                                            C.byref(out), _stream(stream)))
     return out.value
+
+
+def msmg_check_conversions(in64: torch.Tensor, in32: torch.Tensor, stream=None):
+    """The V-cycle kernels' integer-pipe conversions applied element by element:
+    (in64 rounded to FP32, in32 widened to FP64), for comparison with the hardware's."""
+    n = in64.numel()
+    if in32.numel() != n:
+        raise ValueError("in64 and in32 must have the same length")
+    out32 = torch.empty(n, dtype=torch.float32, device=in64.device)
+    out64 = torch.empty(n, dtype=torch.float64, device=in64.device)
+    _check(load_library().msmg_check_conversions(_ptr(in64, torch.float64), _ptr(in32, torch.float32), n,
+                                                 _ptr(out32), _ptr(out64), _stream(stream)))
+    return out32, out64
 
 
 def msmg_export_basis(ctx: int, level: int, basis: torch.Tensor, lam: torch.Tensor | None = None,

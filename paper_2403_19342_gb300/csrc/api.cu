@@ -19,6 +19,8 @@ bool net_matches(const msmg_ctx* c, const msmg_net* net);
 int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s);
 int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s);
 int time_iterations(msmg_ctx* c, int R, int reps, double* ms_out, cudaStream_t s);
+int launch_check_conversions(const double* in64, const float* in32, int64_t n, float* out32, double* out64,
+                             cudaStream_t s);
 int pcg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs, double* const* x,
                       const int* n_rhs, double rtol, int max_iter, int flags, cudaStream_t s,
                       msmg_solve_info* info);
@@ -630,6 +632,12 @@ int msmg_time_kernels(msmg_ctx* c, int n_rhs, int reps, double* ms_out, int n_ou
   if (st) return st;
   for (int i = 0; i < n_out && i < 7; ++i) ms_out[i] = acc[i];
   return 0;
+}
+
+int msmg_check_conversions(const double* in64, const float* in32, int64_t n, float* out32, double* out64,
+                           msmg_stream stream) {
+  if (n > 0 && (!in64 || !in32 || !out32 || !out64)) return MSMG_ERR_INVALID_ARG;
+  return launch_check_conversions(in64, in32, n, out32, out64, reinterpret_cast<cudaStream_t>(stream));
 }
 
 const char* msmg_status_string(int s) {

@@ -431,6 +431,22 @@ int time_iterations(msmg_ctx* c, int R, int reps, double* ms_out, cudaStream_t s
   return 0;
 }
 
+// ---- integer-pipe conversions, element by element (diagnostics)
+__global__ void k_check_conversions(const double* __restrict__ in64, const float* __restrict__ in32, int64_t n,
+                                    float* __restrict__ out32, double* __restrict__ out64) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out32[i] = f32_of_f64_rn(in64[i]);
+  out64[i] = f64_of_f32(in32[i]);
+}
+int launch_check_conversions(const double* in64, const float* in32, int64_t n, float* out32, double* out64,
+                             cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_check_conversions<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in64, in32, n, out32, out64);
+  MSMG_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
 // ---- mixed-precision copies
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

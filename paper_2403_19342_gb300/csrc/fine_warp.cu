@@ -437,7 +437,9 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
           r[base + c] = rc;
           acc = fma(rc, rc, acc);
         }
-        const V fv = (V)rc;
+        V fv;
+        if constexpr (std::is_same<V, float>::value) fv = f32_of_f64_rn(rc);   // integer pipes
+        else fv = rc;
         s.y[c] = fv;
         rv[base + c] = fv;
       }
@@ -792,7 +794,10 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
       const int c = lane + 32 * i;
       if (!(i < ncl && c < g.nb)) continue;
       const int lx = c % g.bx, t = c / g.bx;
-      const double zc = (double)(s.ut[wpad(g, lx, t % g.by, t / g.by)] + s.y[c]);
+      const V zv = s.ut[wpad(g, lx, t % g.by, t / g.by)] + s.y[c];
+      double zc;
+      if constexpr (std::is_same<V, float>::value) zc = f64_of_f32(zv);       // integer pipes
+      else zc = zv;
       z[base + c] = zc;
       v[0] = fma(rr[i], zc, v[0]);
       v[1] = fma(zc, qq[i], v[1]);

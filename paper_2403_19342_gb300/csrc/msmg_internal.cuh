@@ -248,4 +248,67 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// FP32 <-> FP64 conversions on the integer pipes.  GB300 runs conversions on
+// its FP64 pipe (2 per clock per SM), which the FP64 PCG arithmetic already
+// saturates; these rebuild the IEEE 754 encodings with integer operations.
+// binary32: 1 sign, 8 exponent (bias 127), 23 fraction bits; binary64: 1, 11
+// (bias 1023), 52.  Results equal the hardware conversions bit for bit
+// (round to nearest, ties to even), NaNs stay NaNs.
+
+// Exact widening.
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint32_t mag = u & 0x7fffffffu;
+  uint64_t out;
+  if (mag >= 0x00800000u && mag < 0x7f800000u) {
+    // normal: exponent re-biased by 1023 - 127, fraction moved up 29 bits
+    out = ((uint64_t)mag + ((uint64_t)(1023 - 127) << 23)) << 29;
+  } else if (mag >= 0x7f800000u) {
+    out = 0x7ff0000000000000ull | ((uint64_t)(mag & 0x007fffffu) << 29);   // inf, NaN
+  } else if (mag == 0u) {
+    out = 0;
+  } else {
+    // subnormal m 2^-149: the leading one at bit p gives exponent p - 149
+    const int p = 31 - __clz((int)mag);
+    out = ((uint64_t)(p - 149 + 1023) << 52) | (((uint64_t)mag << (52 - p)) & 0x000fffffffffffffull);
+  }
+  return __longlong_as_double((long long)(sign | out));
+}
+
+// Narrowing, round to nearest, ties to even.
+__device__ __forceinline__ float f32_of_f64_rn(double d) {
+  const uint64_t u = (uint64_t)__double_as_longlong(d);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  const uint64_t frac = u & 0x000fffffffffffffull;
+  uint32_t out;
+  if (e == 0x7ff) {
+    out = frac ? (0x7fc00000u | (uint32_t)(frac >> 29)) : 0x7f800000u;
+  } else {
+    const int ef = e - 1023 + 127;        // binary32 biased exponent
+    if (ef >= 0xff) {
+      out = 0x7f800000u;                   // beyond the binary32 range
+    } else if (ef >= 1) {
+      const uint32_t m = (uint32_t)(frac >> 29);
+      const uint32_t rem = (uint32_t)(frac & 0x1fffffffu);
+      out = ((uint32_t)ef << 23) | m;
+      // a carry out of the fraction steps the exponent (up to inf)
+      out += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    } else {
+      // binary32 subnormal or zero: significand with its leading one, shifted by 30 - ef
+      const int sh = 30 - ef;
+      if (e == 0 || sh > 54) {
+        out = 0;                           // below half the smallest subnormal
+      } else {
+        const uint64_t sig = frac | 0x0010000000000000ull;
+        const uint32_t m = (uint32_t)(sig >> sh);
+        const uint64_t rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        out = m + ((rem > half || (rem == half && (m & 1u))) ? 1u : 0u);
+      }
+    }
+  }
+  return __uint_as_float(sign | out);
+}
+
 }  // namespace msmg
