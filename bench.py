@@ -652,7 +652,7 @@ def run_scale(args, world, rank, local):
     N = SCALE_N
     n = N ** 3
     opts = pkg.Options(n_levels=7, block=(8, 8, 8), ratio=[(2, 2, 2)] * 5, n_eig=[4] * 6, precision=pkg.MIXED,
-                       eig_tol=1e-8)
+                       eig_tol=1e-8, autotune=True)
     need = pkg.msmg_workspace_size(pkg.make_grid((N, N, N)), opts.to_c(), 1)
     free, total = torch.cuda.mem_get_info()
     vec_bytes = 2 * 8 * n + 4 * n                       # rhs, x (FP64) and kappa (FP32)
