@@ -90,7 +90,7 @@ typedef struct {
     int nu[MSMG_MAX_LEVELS];           /* nu[i]: smoothing sweeps on W_{i+1} (nu, nu_c)              */
     int precision;                     /* MSMG_FP64 or MSMG_MIXED                                    */
     double eig_tol;                    /* local eigen-residual tolerance (see msmg_setup)            */
-    int eig_max_iter;                  /* cap on subspace iterations per element (0: default 200)    */
+    int eig_max_iter;                  /* cap on subspace iterations per element (0: default 1000)   */
     int autotune;                      /* 1: msmg_setup times the V-cycle variants (msmg_autotune)   */
                                        /* for batch width 1 and the context's widest batch           */
     const msmg_net* warm_start;        /* NULL: cold start; else a network whose n_in equals the     */
