@@ -116,7 +116,8 @@ typedef struct {
                                        /* post-smoothing kernel (1) or apart (0); [2], [3] */
                                        /* coarse cycle: a launch per step (0), the small  */
                                        /* levels as one cluster launch (1), every coarse  */
-                                       /* level as one cooperative grid launch (2)        */
+                                       /* level as one cooperative grid launch (2), the   */
+                                       /* small levels as one cooperative grid launch (3) */
     double eig_residual_max;           /* largest final eigen-residual (level 1)         */
     int64_t workspace_bytes;
 } msmg_setup_info;
@@ -209,8 +210,9 @@ int msmg_max_batch_rhs(const msmg_ctx* ctx);
  * post-smoothing kernel or a kernel of its own; the coarse cycle as a launch per step, its
  * small levels and the coarsest solve as one thread-block-cluster launch (when the
  * hierarchy has such a tail: at most 256 parents on its first level, at most 1536
- * coarsest unknowns), or every coarse level as one cooperative launch over the whole GPU
- * (at most 4096 coarsest unknowns) -- give the same bits: only the time moves.  Overwrites the solve buffers; call between
+ * coarsest unknowns), every coarse level as one cooperative launch over the whole GPU
+ * (at most 4096 coarsest unknowns), or the same small levels as one cooperative launch
+ * over the whole GPU -- give the same bits: only the time moves.  Overwrites the solve buffers; call between
  * solves.  msmg_setup runs it when options.autotune is set; the choice is reported in
  * msmg_setup_info.tuning.
  */

@@ -259,7 +259,7 @@ static int autotune(msmg_ctx* c, int R, int reps, cudaStream_t s) {
   double best = 1e300;
   int bf = c->tune_fused[cls], bt = c->tune_tail[cls];
   const int forms = coarse_forms(c);
-  for (int tail = 0; tail < 3; ++tail)
+  for (int tail = 0; tail < 4; ++tail)
     for (int v = 0; v < 2; ++v) {
       if (!((forms >> tail) & 1)) continue;
       c->tune_fused[cls] = v;
@@ -492,7 +492,7 @@ int msmg_set_tuning(msmg_ctx* c, const int* tuning) {
   for (int k = 0; k < 2; ++k)
     if (tuning[k] != 0 && tuning[k] != 1) return MSMG_ERR_INVALID_ARG;
   for (int k = 2; k < 4; ++k) {
-    if (tuning[k] < 0 || tuning[k] > 2) return MSMG_ERR_INVALID_ARG;
+    if (tuning[k] < 0 || tuning[k] > 3) return MSMG_ERR_INVALID_ARG;
     if (!((coarse_forms(c) >> tuning[k]) & 1)) return MSMG_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < 2; ++k) {

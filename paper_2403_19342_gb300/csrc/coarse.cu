@@ -674,9 +674,10 @@ static int launch_tail(msmg_ctx* c, PcgScalars* sc, cudaStream_t s) {
   return 0;
 }
 
-// grid form: the whole coarse cycle, cooperative launch
-static int launch_coop(msmg_ctx* c, PcgScalars* sc, cudaStream_t s) {
-  const TailArgs A = tail_args(c, 2);
+// grid form: the coarse cycle from level l0 (2: all of it; tail_l0: the small
+// levels), cooperative launch
+static int launch_coop(msmg_ctx* c, int l0, PcgScalars* sc, cudaStream_t s) {
+  const TailArgs A = tail_args(c, l0);
   const int R = c->sb.R;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)c->coop_grid);
@@ -700,13 +701,17 @@ void prepare_coarse_kernels(msmg_ctx* c) {
   prepare_t<double>(c);
   tail_prepare(c);
   for (int k = 0; k < 2; ++k) {
+    if (c->tune_tail[k] == 3 && !(c->coop_grid && c->tail_l0)) c->tune_tail[k] = c->coop_grid ? 2 : 0;
     if (c->tune_tail[k] == 2 && !c->coop_grid) c->tune_tail[k] = c->tail_l0 ? 1 : 0;
     if (c->tune_tail[k] == 1 && !c->tail_l0) c->tune_tail[k] = c->coop_grid ? 2 : 0;
   }
 }
 
-// available forms of the coarse cycle: bit 0 per level (always), bit 1 cluster, bit 2 grid
-int coarse_forms(const msmg_ctx* c) { return 1 | (c->tail_l0 ? 2 : 0) | (c->coop_grid ? 4 : 0); }
+// available forms of the coarse cycle: bit 0 per level (always), bit 1 cluster tail,
+// bit 2 grid (all coarse levels), bit 3 grid tail
+int coarse_forms(const msmg_ctx* c) {
+  return 1 | (c->tail_l0 ? 2 : 0) | (c->coop_grid ? 4 : 0) | (c->coop_grid && c->tail_l0 ? 8 : 0);
+}
 
 
 // Level-l part of the V-cycle (l >= 2): on entry vf[l] holds the right side;
@@ -720,11 +725,15 @@ static const S* coarse_cycle_t(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t 
   const int R = c->sb.R;
   const int form = c->tune_tail[R > 1 ? 1 : 0];
   if (l == 2 && form == 2 && c->coop_grid) {
-    launch_coop(c, sc, s);
+    launch_coop(c, 2, sc, s);
     return (const S*)(c->nL == 2 ? c->sb.vu[2] : c->sb.vw[2]);
   }
   if (l == c->tail_l0 && form == 1) {
     launch_tail(c, sc, s);
+    return (const S*)c->sb.vw[l];
+  }
+  if (l == c->tail_l0 && form == 3 && c->coop_grid) {
+    launch_coop(c, l, sc, s);
     return (const S*)c->sb.vw[l];
   }
   if (l == c->nL) {

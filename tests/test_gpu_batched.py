@@ -246,7 +246,7 @@ def test_tuned_variants_give_the_same_bits(pkg, form, solver_fp64, solver_mixed)
     F = torch.tensor(rhs_set(S.shape, 4, seed=13), device="cuda")
     out = []
     forms = [0]
-    for form in (1, 2):
+    for form in (1, 2, 3):
         try:
             pkg.msmg_set_tuning(S.ctx, (0, 0, form, form))
             forms.append(form)
@@ -264,6 +264,7 @@ def test_tuned_variants_give_the_same_bits(pkg, form, solver_fp64, solver_mixed)
         assert torch.equal(out[0][2], o[2])
     pkg.msmg_autotune(S.ctx, 1, 2)
     pkg.msmg_autotune(S.ctx, 4, 2)
-    assert all(v in (0, 1) for v in S.info["tuning"])
+    tuning = S.info["tuning"]
+    assert tuning[0] in (0, 1) and tuning[1] in (0, 1) and tuning[2] in forms and tuning[3] in forms
     X2, _, _ = S.solve(F, rtol=1e-8)
     assert torch.equal(X2, out[0][0])
