@@ -177,13 +177,17 @@ __device__ __forceinline__ void w_cp_tminus(V* tm0, V* tm1, V* tm2, const V* __r
 // only what it uses (more warps fit on an SM):
 //   kStageFull      u tile with halo, T, 1/d, y, -d face coefficients (k_post)
 //   kStagePre       T, 1/d, y, -d face coefficients             (k_pre)
-//   kStageRestrict  u tile with halo                              (k_restrict,
+//   kStageRestrict  u tile with halo                              (k_restrict FP32,
 //                   which reads its face coefficients into registers)
+//   kStageRestrictT u tile with halo, T, -d face coefficients     (k_restrict FP64,
+//                   register-bound with the coefficients in registers)
 template <typename V>
 struct WStage {
   V *ut, *t0, *t1, *t2, *tm0, *tm1, *tm2, *dinv, *y;
 };
-constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2;
+constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2, kStageRestrictT = 3;
+template <typename V>
+__host__ __device__ constexpr int restrict_layout() { return sizeof(V) == 8 ? kStageRestrictT : kStageRestrict; }
 // Warps (one element each) per CTA of the staged kernels: the CTA size that
 // keeps the most warps resident per SM for the staging footprint of an 8^3
 // element (FP32: 11 KB per warp for k_pre and k_restrict, 15 KB for k_post;
@@ -191,6 +195,7 @@ constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2;
 template <int LAYOUT, typename V>
 __host__ __device__ constexpr int stage_warps() {
   if (LAYOUT == kStageRestrict) return 4;
+  if (LAYOUT == kStageRestrictT) return 2;
   if (sizeof(V) == 4) return LAYOUT == kStageFull ? 2 : 4;
   return LAYOUT == kStageFull ? 1 : 2;
 }
@@ -199,7 +204,8 @@ template <int LAYOUT, typename G>
 __host__ __device__ inline int wstage_elems(const G& g) {
   if (LAYOUT == kStageRestrict) return r4(g.P);
   const int tut = LAYOUT == kStagePre ? 0 : r4(g.P);
-  return tut + 5 * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
+  const int nv = LAYOUT == kStageRestrictT ? 3 : 5;
+  return tut + nv * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
 }
 template <typename V, int LAYOUT = kStageFull, typename G>
 __device__ __forceinline__ WStage<V> w_stage(unsigned char* base, const G& g, int warp) {
@@ -212,7 +218,7 @@ __device__ __forceinline__ WStage<V> w_stage(unsigned char* base, const G& g, in
   s.t0 = p; p += r4(g.nb);
   s.t1 = p; p += r4(g.nb);
   s.t2 = p; p += r4(g.nb);
-  if (LAYOUT != kStageRestrict) {
+  if (LAYOUT != kStageRestrictT) {
     s.dinv = p; p += r4(g.nb);
     s.y = p; p += r4(g.nb);
   }
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
 // one wave.  The basis loads of all eigenvectors are issued cell by cell into
 // L accumulators (the sum over each eigenvector's cells keeps its order).
 template <typename V, typename BT, typename G>
-__global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32, sizeof(V) == 4 ? 7 : 4)
+__global__ void __launch_bounds__(stage_warps<restrict_layout<V>(), V>() * 32, sizeof(V) == 4 ? 7 : 1)
     k_restrict(const V* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T, const BT* __restrict__ Phi,
                int L, double* __restrict__ rc, int64_t nc, int64_t n, G g, int64_t m, const int* __restrict__ nbr,
                const PcgScalars* sc, int R) {
@@ -486,12 +492,15 @@ __global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32, sizeof(
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kC = 16;                                   // cells per lane held in registers
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t e = (int64_t)bi.blk * stage_warps<kStageRestrict, V>() + warp;
+  constexpr int LAY = restrict_layout<V>();
+  const int64_t e = (int64_t)bi.blk * stage_warps<LAY, V>() + warp;
   if (e >= m) return;
-  V* ut = reinterpret_cast<V*>(smem) + (size_t)warp * r4(g.P);
+  const WStage<V> s = w_stage<V, kStageRestrictT>(smem, g, warp);   // used in the FP64 layout only
+  V* ut = LAY == kStageRestrictT ? s.ut : reinterpret_cast<V*>(smem) + (size_t)warp * r4(g.P);
   const WElem E = w_elem(e, nbr, g);
   w_cp_padded(ut, u + E.base, g, lane);
   w_cp_halo(ut, u, E, g, lane);
+  if constexpr (LAY == kStageRestrictT) w_stage_T(s, T, (const V*)nullptr, n, E, g, lane, false);
   const int ncl = (g.nb + 31) / 32;            // <= kC: elements have at most 512 cells
   const int bxy = g.bx * g.by;
   const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
@@ -503,6 +512,13 @@ __global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32, sizeof(
   }
   cp_async_wait_all();
   __syncwarp();
+  if constexpr (LAY == kStageRestrictT) {
+#pragma unroll
+    for (int i = 0; i < kC; ++i) {
+      const int c = lane + 32 * i;
+      if (i < ncl && c < g.nb) w[i] -= w_apply_A_s(s, g, c);
+    }
+  } else {
   // w -= A u: the six face coefficients of kG cells loaded before the products
   // (-d faces on the element boundary are held by the -d neighbour)
   constexpr int kG = 2;
@@ -537,10 +553,11 @@ __global__ void __launch_bounds__(stage_warps<kStageRestrict, V>() * 32, sizeof(
       w[i0 + j] -= acc;
     }
   }
+  }
   // rc_k = Phi_k . w, accumulated in the V-cycle precision (FP32 in the mixed
   // form: the FP64 pipe runs at 1/64 of the FP32 rate)
   const BT* ph = Phi + (size_t)e * L * g.nb;
-  if (L <= kProlongLMax) {
+  if (sizeof(V) == 4 && L <= kProlongLMax) {     // (FP64: one pass per eigenvector, fewer registers)
     V acc[kProlongLMax];
 #pragma unroll
     for (int k = 0; k < kProlongLMax; ++k) acc[k] = (V)0;
@@ -986,7 +1003,7 @@ struct FineOps {
 template <int LAYOUT, typename V, typename G>
 static inline size_t wsmem(const G& g) {
   return (size_t)stage_warps<LAYOUT, V>() * wstage_elems<LAYOUT>(g) * sizeof(V) +
-         (LAYOUT == kStageRestrict ? 0 : plane_smem(g));
+         (LAYOUT == kStageRestrict || LAYOUT == kStageRestrictT ? 0 : plane_smem(g));
 }
 template <typename G>
 static inline size_t wsmem_p(const G& g) {
@@ -1019,8 +1036,8 @@ static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* 
 template <typename V, typename BT, typename G>
 static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  constexpr int W = stage_warps<kStageRestrict, V>();
-  k_restrict<V, BT, G><<<fine_wgrid(c, W), W * 32, wsmem<kStageRestrict, V>(g), s>>>(
+  constexpr int W = stage_warps<restrict_layout<V>(), V>();
+  k_restrict<V, BT, G><<<fine_wgrid(c, W), W * 32, wsmem<restrict_layout<V>(), V>(g), s>>>(
       (const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
       c->fine.nbr, sc, B.R);
 }
@@ -1063,7 +1080,7 @@ static void prepare_t(const G& g) {
   const int smv = (int)wsmem<kStageFull, V>(g), smd = (int)wsmem_p(g);
   cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem<kStagePre, V>(g));
   cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)wsmem<kStageRestrict, V>(g));
+                       (int)wsmem<restrict_layout<V>(), V>(g));
   cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
