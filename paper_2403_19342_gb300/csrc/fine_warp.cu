@@ -740,6 +740,60 @@ __global__ void __launch_bounds__(256) k_prolong(V* __restrict__ u, const BT* __
   u[i] += acc;
 }
 
+// The same for FP32 vectors and bases, four consecutive cells of one element
+// per thread (16-byte loads and stores; elements of a multiple of 4 cells):
+// per cell the same products in the same order.
+template <typename G>
+__global__ void __launch_bounds__(256) k_prolong4(float* __restrict__ u, const float* __restrict__ Phi, int L,
+                                                  const float* __restrict__ ec, int64_t n, int64_t nc, G g,
+                                                  const PcgScalars* sc, int R) {
+  const BatchIdx bi = batch_idx(R);
+  if (sc) sc += bi.r;
+  if (sc && sc->done) return;
+  u += (int64_t)bi.r * n;
+  ec += (int64_t)bi.r * nc;
+  const int64_t i = ((int64_t)bi.blk * blockDim.x + threadIdx.x) * 4;
+  if (i >= n) return;
+  const int64_t e = i / g.nb;
+  const int c = (int)(i - e * g.nb);
+  const float* ph = Phi + (size_t)e * L * g.nb + c;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (L <= kProlongLMax) {
+    float4 v[kProlongLMax];
+    float ev[kProlongLMax];
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k)
+      if (k < L) {
+        v[k] = __ldg(reinterpret_cast<const float4*>(ph + (size_t)k * g.nb));
+        ev[k] = __ldg(ec + e * L + k);
+      }
+#pragma unroll
+    for (int k = 0; k < kProlongLMax; ++k)
+      if (k < L) {
+        acc.x += v[k].x * ev[k];
+        acc.y += v[k].y * ev[k];
+        acc.z += v[k].z * ev[k];
+        acc.w += v[k].w * ev[k];
+      }
+  } else {
+    for (int k = 0; k < L; ++k) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(ph + (size_t)k * g.nb));
+      const float ek = __ldg(ec + e * L + k);
+      acc.x += v.x * ek;
+      acc.y += v.y * ek;
+      acc.z += v.z * ek;
+      acc.w += v.w * ek;
+    }
+  }
+  float4* up = reinterpret_cast<float4*>(u + i);
+  float4 uu = *up;
+  uu.x += acc.x;
+  uu.y += acc.y;
+  uu.z += acc.z;
+  uu.w += acc.w;
+  *up = uu;
+}
+
 // ------------------------------------------------------------------ k_post
 // z = u + M^{-1} (f - A u), written in FP64; reductions: r.z and z.q (flexible
 // beta).  f, r and q are loaded into registers before the wavefronts start.
@@ -1061,6 +1115,13 @@ template <typename V, typename BT, typename G>
 static void prolong_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, PcgScalars* sc, cudaStream_t s,
                       const G& g) {
   SolveBuffers& B = c->sb;
+  if constexpr (std::is_same<V, float>::value && std::is_same<BT, float>::value) {
+    if (c->fine.nb % 4 == 0) {
+      const unsigned grid = (unsigned)((c->n / 4 + 255) / 256 * B.R);
+      k_prolong4<G><<<grid, 256, 0, s>>>((float*)B.vu[1], o.Phi, c->fine.L, ec, c->n, c->lev[2].n, g, sc, B.R);
+      return;
+    }
+  }
   const unsigned grid = (unsigned)((c->n + 255) / 256 * B.R);
   k_prolong<V, BT, G><<<grid, 256, 0, s>>>((V*)B.vu[1], o.Phi, c->fine.L, ec, c->n, c->lev[2].n, g, sc, B.R);
 }
