@@ -393,7 +393,8 @@ int time_kernels(msmg_ctx* c, int R, int reps, double* acc, cudaStream_t s) {
 }
 
 // Mean time of one whole PCG iteration (V-cycle and the p / A p kernel),
-// reps of them launched back to back as a solve runs them; the autotuner's
+// reps of them captured in one CUDA graph and launched as a solve launches its
+// iterations (kernel by kernel if capture is not possible); the autotuner's
 // criterion.  Same scratch contents as time_kernels.
 int time_iterations(msmg_ctx* c, int R, int reps, double* ms_out, cudaStream_t s) {
   SolveBuffers& B = c->sb;
@@ -411,16 +412,38 @@ int time_iterations(msmg_ctx* c, int R, int reps, double* ms_out, cudaStream_t s
   cudaEvent_t ev[2];
   cudaEventCreate(&ev[0]);
   cudaEventCreate(&ev[1]);
-  for (int r = 0; r <= reps; ++r) {      // the first iteration warms up
-    if (r == 1) cudaEventRecord(ev[0], s);
-    k_reset_scalars<<<1, 32 * ((R + 31) / 32), 0, s>>>(B.sc, R);
-    pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, B.sc, s);
-    pcg_step_pmatvec(c, B.sc, s);
+  cudaGraphExec_t ge = nullptr;
+  if (!c->cap_stream) cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (c->cap_stream && cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    for (int r = 0; r < reps; ++r) {
+      k_reset_scalars<<<1, 32 * ((R + 31) / 32), 0, c->cap_stream>>>(B.sc, R);
+      pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, B.sc, c->cap_stream);
+      pcg_step_pmatvec(c, B.sc, c->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && g) {
+      if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+      cudaGraphDestroy(g);
+    }
+  }
+  cudaGetLastError();   // a failed capture leaves the eager path below
+  if (ge) {
+    cudaGraphLaunch(ge, s);              // warm-up
+    cudaEventRecord(ev[0], s);
+    cudaGraphLaunch(ge, s);
+  } else {
+    for (int r = 0; r <= reps; ++r) {    // the first iteration warms up
+      if (r == 1) cudaEventRecord(ev[0], s);
+      k_reset_scalars<<<1, 32 * ((R + 31) / 32), 0, s>>>(B.sc, R);
+      pcg_step_vcycle(c, 1, flexible ? B.q : nullptr, B.sc, s);
+      pcg_step_pmatvec(c, B.sc, s);
+    }
   }
   cudaEventRecord(ev[1], s);
   const cudaError_t e = cudaEventSynchronize(ev[1]);
   float ms = 0.f;
   if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  if (ge) cudaGraphExecDestroy(ge);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (e != cudaSuccess) {
