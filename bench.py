@@ -31,8 +31,8 @@ eigenpairs the library computes for held-out 128^3 fields of the same kind
 1e6), 8^3 elements, 7 levels, 4 eigenvectors per local problem, mixed form.
 
 With N > 1 (torchrun) every rank solves its own replica of the workload (the
-problem does not shard across the one-GPU machines of this pool): weak scaling,
-no data-path collective; value = DOF solved by all ranks / max time.
+solve is not sharded across GPUs): weak scaling, no data-path collective;
+value = DOF solved by all ranks / max time.
 ``--impl reference`` times the FP64 CPU oracle (the reference arm).
 """
 from __future__ import annotations

@@ -603,7 +603,7 @@ int pcg_solve_batched(msmg_ctx* const* ctxs, int n_ctx, const double* const* rhs
       }
     }
     if (!progressed && !err) {
-      // nothing completed this round: block on the oldest outstanding work of one context
+      // nothing completed in this pass: block on the oldest outstanding work of one context
       for (auto& J : jobs) {
         if (J.finished || !J.active) continue;
         const int st = J.run.step(true);
