@@ -98,6 +98,38 @@ __device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Bulk asynchronous copies (the TMA engine, untiled form) of contiguous arrays
+// into shared memory, completion tracked by one mbarrier per warp: one lane
+// issues them, every lane waits.  Addresses 16-byte aligned, sizes multiples of
+// 16 bytes.
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned bar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// Waits for phase ``parity`` of the barrier to complete; gives up (false) after
+// about a million polls instead of waiting without bound.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // one element's chunk of an array; 16-byte copies when the chunk allows it
 template <typename V, typename G>
 __device__ __forceinline__ void w_cp_array(V* dst, const V* __restrict__ src, const G& g, int lane) {
@@ -236,6 +268,35 @@ __device__ __forceinline__ void w_stage_T(const WStage<V>& s, const V* __restric
   w_cp_array(s.t2, T + 2 * n + E.base, g, lane);
   if (with_dinv) w_cp_array(s.dinv, invd + E.base, g, lane);
   w_cp_tminus(s.tm0, s.tm1, s.tm2, T, n, E, g, lane);
+}
+
+// The same with the four in-element arrays (T[0..2], 1/d) as bulk copies on the
+// warp's mbarrier ``bar`` (lane 0 issues them) where their size allows, the -d
+// halo coefficients (gathered from three neighbours) by per-lane copies when
+// asked for.  Returns whether the caller must wait on ``bar`` (phase 0).
+template <typename V, typename G>
+__device__ __forceinline__ bool w_stage_T_bulk(const WStage<V>& s, const V* __restrict__ T,
+                                               const V* __restrict__ invd, int64_t n, const WElem& E, const G& g,
+                                               int lane, unsigned bar, bool with_tm) {
+  const bool bulk = (g.nb * (int)sizeof(V)) % 16 == 0;
+  if (bulk) {
+    if (lane == 0) {
+      const unsigned bytes = (unsigned)(g.nb * sizeof(V));
+      mbar_init(bar, 1);
+      mbar_expect_tx(bar, 4 * bytes);
+      bulk_g2s(s.t0, T + E.base, bytes, bar);
+      bulk_g2s(s.t1, T + n + E.base, bytes, bar);
+      bulk_g2s(s.t2, T + 2 * n + E.base, bytes, bar);
+      bulk_g2s(s.dinv, invd + E.base, bytes, bar);
+    }
+  } else {
+    w_cp_array(s.t0, T + E.base, g, lane);
+    w_cp_array(s.t1, T + n + E.base, g, lane);
+    w_cp_array(s.t2, T + 2 * n + E.base, g, lane);
+    w_cp_array(s.dinv, invd + E.base, g, lane);
+  }
+  if (with_tm) w_cp_tminus(s.tm0, s.tm1, s.tm2, T, n, E, g, lane);
+  return bulk;
 }
 
 // (A u)_c from the staged tiles
@@ -412,10 +473,14 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
   const bool act = e < m;
   const WStage<V> s = w_stage<V, kStagePre>(smem, g, warp);
   const unsigned short* tab = w_plane_table<G>(smem + (size_t)W * wstage_elems<kStagePre>(g) * sizeof(V));
+  __shared__ __align__(8) unsigned long long s_bar[W];   // one mbarrier per warp
+  const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp]);
   double acc = 0.0;
   if (act) {
     const WElem E = w_elem(e, nbr, g);
-    w_stage_T(s, T, invd, n, E, g, lane, true);
+    // the element's face coefficients and inverse pivots (the sweeps use no
+    // halo coefficients)
+    const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, false);
     const double alpha = update ? sc->alpha : 0.0;
     const int64_t base = E.base;
     // batches of 8 cells per lane: all loads of a batch are issued before use
@@ -451,6 +516,7 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
       }
     }
     cp_async_wait_all();
+    if (bulk && !mbar_wait(bar, 0) && sc) sc->done = 2;   // copies never landed: stop the solve
     __syncwarp();
     w_ic0_s(s, g, lane, tab);
 #pragma unroll 4
@@ -822,6 +888,8 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
   const bool act = e < m;
   const WStage<V> s = w_stage<V>(smem, g, warp);
   const unsigned short* tab = w_plane_table<G>(smem + (size_t)W * wstage_elems<kStageFull>(g) * sizeof(V));
+  __shared__ __align__(8) unsigned long long s_bar[W];   // one mbarrier per warp
+  const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp]);
   const int ncl = (g.nb + 31) / 32;
   double v[2] = {0.0, 0.0};
   if (act && ncl <= kC) {
@@ -829,8 +897,9 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
     const int64_t base = E.base;
     w_cp_padded(s.ut, u + base, g, lane);
     w_cp_halo(s.ut, u, E, g, lane);
-    w_stage_T(s, T, invd, n, E, g, lane, true);
+    const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, true);
     cp_async_wait_all();
+    if (bulk && !mbar_wait(bar, 0) && sc) sc->done = 2;   // copies never landed: stop the solve
     __syncwarp();
     if (FUSE) {
       w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
@@ -878,8 +947,9 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
     const int64_t base = E.base;
     w_cp_padded(s.ut, u + base, g, lane);
     w_cp_halo(s.ut, u, E, g, lane);
-    w_stage_T(s, T, invd, n, E, g, lane, true);
+    const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, true);
     cp_async_wait_all();
+    if (bulk && !mbar_wait(bar, 0) && sc) sc->done = 2;   // copies never landed: stop the solve
     __syncwarp();
     if (FUSE) {
       w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
