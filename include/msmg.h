@@ -60,7 +60,8 @@ typedef struct msmg_net msmg_net;                /* opaque: learned warm-start n
 /* precision modes */
 #define MSMG_FP64   0   /* every step in FP64                                           */
 #define MSMG_MIXED  1   /* FP32 fine-level V-cycle and bases, FP64 coarse levels,       */
-                        /* coarsest solve, eigenbasis orthonormalisation and outer PCG  */
+                        /* coarsest solve and outer PCG; the level-1 eigensolve runs in */
+                        /* FP32 to a residual near FP32's reach, then FP64 to eig_tol   */
 
 /* kappa element types */
 #define MSMG_F64 0
