@@ -56,6 +56,7 @@ typedef struct msmg_net msmg_net;                /* opaque: learned warm-start n
 #define MSMG_ERR_CUDA               -8
 #define MSMG_ERR_NOT_FACTORIZABLE   -9   /* a smoother or coarsest factor failed */
 #define MSMG_ERR_UNSUPPORTED       -10
+#define MSMG_ERR_DEVICE_TIMEOUT    -11   /* a bounded device-side wait gave up   */
 
 /* precision modes */
 #define MSMG_FP64   0   /* every step in FP64                                           */
@@ -182,7 +183,8 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
  *              time of the system's batch, kernel_launches the batch's launches
  * x is returned with zero mean (Section 2.1).  In MSMG_MIXED the V-cycle runs in FP32
  * and the outer recurrence in FP64 with the flexible (Polak-Ribiere) beta.  Returns the
- * worst status over the systems: MSMG_ERR_BREAKDOWN, MSMG_NOT_CONVERGED, or MSMG_OK.
+ * worst status over the systems: MSMG_ERR_BREAKDOWN, MSMG_NOT_CONVERGED, or MSMG_OK (or
+ * MSMG_ERR_DEVICE_TIMEOUT when a kernel's bounded wait for its staged data gave up).
  * Blocks the calling thread until the solution is in x.
  */
 int msmg_solve(msmg_ctx* ctx, const double* rhs, double* x, int n_rhs, double rtol, int max_iter,
@@ -227,7 +229,9 @@ int msmg_set_tuning(msmg_ctx* ctx, const int* tuning);
 /* q = A p, FP64, natural order (Eq. (discrete varia)). */
 int msmg_apply_A(msmg_ctx* ctx, const double* p, double* q, msmg_stream stream);
 
-/* z = P^{-1} r: one V-cycle from zero (Algorithm 1 generalised), natural order. */
+/* z = P^{-1} r: one V-cycle from zero (Algorithm 1 generalised), natural order.  Synchronises
+ * the stream; MSMG_ERR_DEVICE_TIMEOUT if a kernel's bounded wait for its staged data gave up
+ * (z is then not valid). */
 int msmg_apply_precond(msmg_ctx* ctx, const double* r, double* z, msmg_stream stream);
 
 /* Deterministic FP64 dot product of two device vectors of length n with the PCG's
@@ -250,10 +254,11 @@ int msmg_dot(const double* a, const double* b, int64_t n, void* scratch, double*
  *   result_host  host; the call synchronises the stream
  * Scratch: a fixed array of (MSMG_DOT_NOALLOC_MAX_N / 1024 + 32) doubles (about 128 KiB)
  * in this library's device memory, which every GPU that loads the library holds until
- * the process exits.  The first call on a device looks up the array's device address
- * (with that device current); make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU (concurrent streams or threads)
- * race and give wrong results.
+ * the process exits.  Every call looks up the array's address on the current device
+ * (a and b must be on that device).  The call copies the result to the host and
+ * synchronises the stream, so it must not be used while the stream is being captured.
+ * All calls share the array: calls that overlap on the GPU (concurrent streams or
+ * threads) race and give wrong results.
  */
 #define MSMG_DOT_NOALLOC_MAX_N 16777216
 int msmg_dot_noalloc(const double* a, const double* b, int64_t n, double* result_host, msmg_stream stream);
@@ -376,17 +381,15 @@ int msmg_learning_data(msmg_ctx* ctx, float* x, float* y, msmg_stream stream);
  * the context's own buffers (fixed synthetic data), at batch width n_rhs (1 .. the
  * context's).  ms_out[0 .. n_out) receives:
  *   [0] PCG update of x and r fused with the pre-smoothing   [1] residual + restriction
- *   [2] 0 (the prolongation runs inside [3])
- *   [3] prolongation + residual + post-smoothing (with the r.z reduction)
+ *   [2] fine prolongation, when it runs as a kernel of its own (about 0 when the context's
+ *       tuning for this batch width runs it inside [3])
+ *   [3] residual + post-smoothing (with the r.z reduction), plus the prolongation when fused
  *   [4] all coarse levels (levels >= 2)   [5] search-direction update fused with q = A p
  *   [6] [0]..[3] and [4] together (one preconditioner application)
  * Used for roofline figures; no effect on results.
  */
 int msmg_time_kernels(msmg_ctx* ctx, int n_rhs, int reps, double* ms_out, int n_out, msmg_stream stream);
 
-/* Measured plain-ALU FMA throughput of this GPU (TFLOP/s), for roofline denominators of
- * ALU-bound kernels: a short in-register FMA loop timed with CUDA events. */
-int msmg_probe_alu_peaks(double* fp64_tflops, double* fp32_tflops, msmg_stream stream);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,7 @@ STATUS = {
     -3: "MSMG_ERR_BAD_KAPPA", -4: "MSMG_ERR_SINGLE_BLOCK", -5: "MSMG_ERR_BREAKDOWN",
     -6: "MSMG_ERR_EIG_NOT_CONVERGED", -7: "MSMG_ERR_WORKSPACE", -8: "MSMG_ERR_CUDA",
     -9: "MSMG_ERR_NOT_FACTORIZABLE", -10: "MSMG_ERR_UNSUPPORTED",
+    -11: "MSMG_ERR_DEVICE_TIMEOUT",
 }
 
 
@@ -99,7 +100,6 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_get_setup_info": (I, [P, C.POINTER(msmg_setup_info)]),
         "msmg_destroy": (None, [P]),
         "msmg_status_string": (C.c_char_p, [I]),
-        "msmg_probe_alu_peaks": (I, [C.POINTER(D), C.POINTER(D), P]),
         "msmg_time_kernels": (I, [P, I, I, C.POINTER(D), I, P]),
         "msmg_solve_batched": (I, [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), C.POINTER(I), D, I, I, P,
                                    C.POINTER(msmg_solve_info)]),
@@ -133,7 +133,7 @@ def exported_symbols():
     return ["msmg_workspace_size", "msmg_setup", "msmg_solve", "msmg_apply_A", "msmg_apply_precond",
             "msmg_dot_scratch_bytes", "msmg_dot", "msmg_export_basis", "msmg_import_bases",
             "msmg_export_operator", "msmg_export_faces", "msmg_get_setup_info", "msmg_destroy",
-            "msmg_status_string", "msmg_probe_alu_peaks", "msmg_time_kernels", "msmg_dot_noalloc",
+            "msmg_status_string", "msmg_time_kernels", "msmg_dot_noalloc",
             "msmg_solve_batched", "msmg_max_batch_rhs", "msmg_autotune", "msmg_set_tuning",
             "msmg_net_workspace_size", "msmg_net_create",
             "msmg_net_destroy", "msmg_net_param_count", "msmg_net_param_offsets", "msmg_net_get_params",
@@ -292,14 +292,27 @@ def msmg_apply_precond(ctx: int, r: torch.Tensor, z: torch.Tensor, stream=None) 
     _check(load_library().msmg_apply_precond(ctx, _ptr(r, torch.float64), _ptr(z, torch.float64), _stream(stream)))
 
 
+def _same_vectors(a: torch.Tensor, b: torch.Tensor) -> None:
+    """Both operands of a dot product: same length, same CUDA device (checked
+    before anything reaches the library, which reads n values of each)."""
+    if a.numel() != b.numel():
+        raise ValueError(f"dot operands differ in length: {a.numel()} vs {b.numel()}")
+    if a.device != b.device:
+        raise ValueError(f"dot operands on different devices: {a.device} vs {b.device}")
+
+
 def msmg_dot(a: torch.Tensor, b: torch.Tensor, scratch: torch.Tensor | None = None, stream=None) -> float:
+    _same_vectors(a, b)
     lib = load_library()
     n = a.numel()
-    if scratch is None:
-        scratch = torch.empty(lib.msmg_dot_scratch_bytes(n), dtype=torch.uint8, device=a.device)
-    out = C.c_double(0.0)
-    _check(lib.msmg_dot(_ptr(a, torch.float64), _ptr(b, torch.float64), n, _ptr(scratch), C.byref(out),
-                        _stream(stream)))
+    with torch.cuda.device(a.device):
+        if scratch is None:
+            scratch = torch.empty(lib.msmg_dot_scratch_bytes(n), dtype=torch.uint8, device=a.device)
+        elif scratch.device != a.device:
+            raise ValueError("scratch must be on the operands' device")
+        out = C.c_double(0.0)
+        _check(lib.msmg_dot(_ptr(a, torch.float64), _ptr(b, torch.float64), n, _ptr(scratch), C.byref(out),
+                            _stream(stream)))
     return out.value
 
 
@@ -309,9 +322,11 @@ DOT_NOALLOC_MAX_N = 16777216
 def msmg_dot_noalloc(a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
     """msmg_dot without a scratch buffer: the library's fixed device array holds the
     partial sums (for callers that cannot allocate device memory; see include/msmg.h)."""
+    _same_vectors(a, b)
     out = C.c_double(0.0)
-    _check(load_library().msmg_dot_noalloc(_ptr(a, torch.float64), _ptr(b, torch.float64), a.numel(),
-                                           C.byref(out), _stream(stream)))
+    with torch.cuda.device(a.device):
+        _check(load_library().msmg_dot_noalloc(_ptr(a, torch.float64), _ptr(b, torch.float64), a.numel(),
+                                               C.byref(out), _stream(stream)))
     return out.value
 
 
@@ -367,12 +382,6 @@ def msmg_time_kernels(ctx: int, reps: int = 20, stream=None, n_rhs: int = 1) -> 
     out = (C.c_double * 7)()
     _check(load_library().msmg_time_kernels(ctx, n_rhs, reps, out, 7, _stream(stream)))
     return list(out)
-
-
-def msmg_probe_alu_peaks(stream=None) -> tuple[float, float]:
-    a, b = C.c_double(0), C.c_double(0)
-    _check(load_library().msmg_probe_alu_peaks(C.byref(a), C.byref(b), _stream(stream)))
-    return a.value, b.value
 
 
 # ----------------------------------------------------------------- learned warm start

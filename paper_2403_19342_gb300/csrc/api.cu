@@ -374,8 +374,8 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   // residual norms and restart mask
   MSMG_CUDA_TRY(cudaMallocHost(&c->hsc, (size_t)3 * n_rhs * sizeof(PcgScalars)));
   MSMG_CUDA_TRY(cudaMallocHost(&c->hres, (size_t)2 * n_rhs * sizeof(double)));
-  MSMG_CUDA_TRY(cudaMallocHost(&c->hmask, (size_t)(n_rhs + 1) * sizeof(int)));
-  c->hmask[n_rhs] = 0;
+  MSMG_CUDA_TRY(cudaMallocHost(&c->hmask, (size_t)(n_rhs + 2) * sizeof(int)));
+  c->hmask[n_rhs] = c->hmask[n_rhs + 1] = 0;
   cudaEventRecord(c->ev0, s);
   LevelShape sh;
   shapes(grid, opts, sh);
@@ -541,11 +541,16 @@ int msmg_apply_precond(msmg_ctx* c, const double* r, double* z, msmg_stream stre
   if (!c || !r || !z) return MSMG_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   c->sb.R = 1;
+  MSMG_CUDA_TRY(cudaMemsetAsync(c->flags + 6, 0, sizeof(int), s));
   launch_nat_to_blk(c, r, c->sb.r, s);
   apply_vcycle_fp64_out(c, s);
   launch_blk_to_nat(c, c->sb.z, z, s);
   MSMG_CUDA_TRY(cudaGetLastError());
-  return 0;
+  // a bounded wait inside the V-cycle that gave up leaves its error word set
+  int err = 0;
+  MSMG_CUDA_TRY(cudaMemcpyAsync(&err, c->flags + 6, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return err ? MSMG_ERR_DEVICE_TIMEOUT : 0;
 }
 
 size_t msmg_dot_scratch_bytes(int64_t n) {
@@ -663,6 +668,7 @@ const char* msmg_status_string(int s) {
     case MSMG_ERR_CUDA: return cudaGetErrorString(g_last_cuda);
     case MSMG_ERR_NOT_FACTORIZABLE: return "smoother or coarsest factorisation failed";
     case MSMG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MSMG_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait gave up (data never arrived)";
     default: return "unknown status";
   }
 }

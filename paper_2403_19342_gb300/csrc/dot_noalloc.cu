@@ -4,7 +4,6 @@
 // caller-provided buffer.  For callers that cannot allocate device memory.
 #include "msmg_internal.cuh"
 #include "reduce.cuh"
-#include <mutex>
 
 namespace msmg {
 
@@ -30,25 +29,14 @@ __global__ void k_dot_noalloc(const double* __restrict__ a, const double* __rest
   grid_reduce<1>(v, red, [=] __device__(double* t) { *out = t[0]; });
 }
 
-// Device address of the array, looked up once per device with that device current.
-static std::mutex g_mu;
-static double* g_addr[64];
-static bool g_ready[64];
-
+// Device address of the array on the current device.  Looked up on every call
+// (the lookup does not synchronise): a cached address would go stale if the
+// caller reset the device, after which the module is loaded again.
 static int scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
-  if (dev < 0 || dev >= 64) return MSMG_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ready[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_dot_scratch);
-    if (e != cudaSuccess || !p) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
-    g_addr[dev] = static_cast<double*>(p);
-    g_ready[dev] = true;
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_dot_scratch);
+  if (e != cudaSuccess || !p) { set_last_cuda_error(e); return MSMG_ERR_CUDA; }
+  *out = static_cast<double*>(p);
   return 0;
 }
 

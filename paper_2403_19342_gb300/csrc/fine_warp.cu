@@ -130,6 +130,24 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   return false;
 }
 
+// Completion of a warp's bulk copies, the same answer in every lane.  When the
+// bounded wait gives up, the error word is set (whatever path launched the
+// kernel), the right-hand side is marked as broken down, and the copies get a
+// second bounded wait before the warp skips its element: it then uses none of
+// the staged data.
+__device__ __forceinline__ bool bulk_landed(bool bulk, unsigned bar, PcgScalars* sc, int* err) {
+  const bool ok = __all_sync(0xffffffffu, !bulk || mbar_wait(bar, 0));
+  if (!ok) {
+    if ((threadIdx.x & 31) == 0) {
+      atomicExch(err, 1);
+      if (sc) sc->done = 2;
+    }
+    mbar_wait(bar, 0);
+  }
+  __syncwarp();
+  return ok;
+}
+
 // one element's chunk of an array; 16-byte copies when the chunk allows it
 template <typename V, typename G>
 __device__ __forceinline__ void w_cp_array(V* dst, const V* __restrict__ src, const G& g, int lane) {
@@ -289,6 +307,8 @@ __device__ __forceinline__ bool w_stage_T_bulk(const WStage<V>& s, const V* __re
       bulk_g2s(s.t2, T + 2 * n + E.base, bytes, bar);
       bulk_g2s(s.dinv, invd + E.base, bytes, bar);
     }
+    // the other lanes poll the barrier only after lane 0 initialised it
+    __syncwarp();
   } else {
     w_cp_array(s.t0, T + E.base, g, lane);
     w_cp_array(s.t1, T + n + E.base, g, lane);
@@ -458,7 +478,7 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
                                                            const V* __restrict__ T, const V* __restrict__ invd,
                                                            V* __restrict__ rv, V* __restrict__ u, int64_t n, G g,
                                                            int64_t m, const int* __restrict__ nbr, int update,
-                                                           RedSlot red, PcgScalars* sc, int R) {
+                                                           RedSlot red, PcgScalars* sc, int* err, int R) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -516,20 +536,22 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
       }
     }
     cp_async_wait_all();
-    if (bulk && !mbar_wait(bar, 0) && sc) sc->done = 2;   // copies never landed: stop the solve
-    __syncwarp();
+    do {   // left early when the staged data never landed
+    if (!bulk_landed(bulk, bar, sc, err)) break;
     w_ic0_s(s, g, lane, tab);
 #pragma unroll 4
     for (int i = 0; i < (g.nb + 31) / 32; ++i) {
       const int c = lane + 32 * i;
       if (c < g.nb) u[base + c] = s.y[c];
     }
+    } while (0);
   }
   if (update) {
     double v[1] = {acc};
     grid_reduce_r<1>(v, red, bi, [=] __device__(double* t) {
       sc->rr = t[0];
       sc->iter += 1;
+      if (sc->done != 0) return;   // a warp of this launch already stopped the solve
       if (!isfinite(t[0])) sc->done = 2;
       else if (t[0] <= sc->tol2) sc->done = 1;
       else if (sc->iter >= sc->max_iter) sc->done = 3;
@@ -870,7 +892,7 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
                                                             const V* __restrict__ ec, int L, int64_t nc,
                                                             double* __restrict__ z, const double* __restrict__ qv,
                                                             int64_t n, G g, int64_t m, const int* __restrict__ nbr,
-                                                            RedSlot red, PcgScalars* sc, int R) {
+                                                            RedSlot red, PcgScalars* sc, int* err, int R) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -899,8 +921,8 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
     w_cp_halo(s.ut, u, E, g, lane);
     const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, true);
     cp_async_wait_all();
-    if (bulk && !mbar_wait(bar, 0) && sc) sc->done = 2;   // copies never landed: stop the solve
-    __syncwarp();
+    do {   // left early when the staged data never landed
+    if (!bulk_landed(bulk, bar, sc, err)) break;
     if (FUSE) {
       w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
       __syncwarp();
@@ -942,6 +964,7 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
       v[0] = fma(rr[i], zc, v[0]);
       v[1] = fma(zc, qq[i], v[1]);
     }
+    } while (0);
   } else if (act) {
     const WElem E = w_elem(e, nbr, g);
     const int64_t base = E.base;
@@ -949,8 +972,8 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
     w_cp_halo(s.ut, u, E, g, lane);
     const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, true);
     cp_async_wait_all();
-    if (bulk && !mbar_wait(bar, 0) && sc) sc->done = 2;   // copies never landed: stop the solve
-    __syncwarp();
+    do {   // left early when the staged data never landed
+    if (!bulk_landed(bulk, bar, sc, err)) break;
     if (FUSE) {
       w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
       __syncwarp();
@@ -967,6 +990,7 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
         if (qv) v[1] = fma(zc, qv[base + c], v[1]);
       }
     }
+    } while (0);
   }
   if (sc) {
     grid_reduce_r<2>(v, red, bi, [=] __device__(double* t) {
@@ -1154,7 +1178,7 @@ static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* 
   constexpr int W = stage_warps<kStagePre, V>();
   k_pre<V, G><<<fine_wgrid(c, W), W * 32, wsmem<kStagePre, V>(g), s>>>(
       B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv, (V*)B.vu[1], c->n, g, c->fine.m, c->fine.nbr, update, c->red, sc,
-      B.R);
+      c->flags + 6, B.R);
 }
 
 template <typename V, typename BT, typename G>
@@ -1174,11 +1198,11 @@ static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, const doub
   if (fuse)
     k_post<V, BT, G, true><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
-        c->fine.m, c->fine.nbr, c->red, sc, B.R);
+        c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R);
   else
     k_post<V, BT, G, false><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
-        c->fine.m, c->fine.nbr, c->red, sc, B.R);
+        c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R);
 }
 
 template <typename V, typename BT, typename G>

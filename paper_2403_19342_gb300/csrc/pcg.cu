@@ -414,7 +414,8 @@ struct PcgRun {
     launches += 2;
     MSMG_CUDA_TRY(cudaMemcpyAsync(hsc_last(), B.sc, (size_t)R * sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     MSMG_CUDA_TRY(cudaMemcpyAsync(c->hres, B.dres, (size_t)2 * R * sizeof(double), cudaMemcpyDeviceToHost, s));
-    MSMG_CUDA_TRY(cudaMemcpyAsync(c->hmask + c->max_rhs, c->flags + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // error words: [5] cooperative coarse cycle not launched, [6] a bounded wait gave up
+    MSMG_CUDA_TRY(cudaMemcpyAsync(c->hmask + c->max_rhs, c->flags + 5, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     MSMG_CUDA_TRY(cudaEventRecord(c->poll_evs[2], s));
     return 0;
   }
@@ -424,6 +425,7 @@ struct PcgRun {
       set_last_cuda_error(cudaErrorLaunchFailure);   // the cooperative coarse cycle did not run
       return MSMG_ERR_CUDA;
     }
+    if (c->hmask[c->max_rhs + 1]) return MSMG_ERR_DEVICE_TIMEOUT;   // staged data never landed
     const PcgScalars* h = hsc_last();
     int worst = MSMG_OK;
     for (int r = 0; r < R; ++r) {
@@ -503,6 +505,7 @@ static int begin_batch(CtxSolve& J, double rtol, int max_iter, int flags, cudaSt
   c->sb.R = J.R;
   J.stage_launches = 0;
   MSMG_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  MSMG_CUDA_TRY(cudaMemsetAsync(c->flags + 6, 0, sizeof(int), s));
   int st = stage_in(c, J.rhs + (int64_t)J.next * c->n, J.x + (int64_t)J.next * c->n, J.R, host, x0, s,
                     &J.stage_launches);
   if (st) return st;

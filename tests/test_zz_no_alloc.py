@@ -39,3 +39,13 @@ def test_noalloc_dot_rejects_oversize(pkg):
         pkg.msmg_dot_noalloc(a, a)
     assert e.value.status == -1
     assert pkg.msmg_dot_noalloc(a[:0], a[:0]) == 0.0
+
+
+def test_noalloc_dot_rejects_mismatched_operands(pkg):
+    # a shorter b would be read past its end: refused before any launch
+    a = torch.zeros(1000, dtype=torch.float64, device="cuda")
+    b = torch.zeros(999, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        pkg.msmg_dot_noalloc(a, b)
+    with pytest.raises(ValueError):
+        pkg.msmg_dot(a, b)
