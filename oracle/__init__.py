@@ -33,13 +33,13 @@ the paper prints, to library routines on special cases and to brute force.
 from .tpfa import (as_components, normalized_permeability, trace_weight,
                    face_transmissibilities, assemble, apply_A, interior_face_mask)
 from .spectral import element_cells, level1_eigenpairs, coarse_eigenpairs
-from .hierarchy import Options, Hierarchy, setup, BlockIC0
+from .hierarchy import Options, Hierarchy, setup, BlockIC0, BlockIC0Dense, ic0_dense, sibling_pattern
 from .solver import vcycle, pcg, solve, PCGResult
 
 __all__ = [
     "as_components", "normalized_permeability", "trace_weight",
     "face_transmissibilities", "assemble", "apply_A", "interior_face_mask",
     "element_cells", "level1_eigenpairs", "coarse_eigenpairs",
-    "Options", "Hierarchy", "setup", "BlockIC0",
+    "Options", "Hierarchy", "setup", "BlockIC0", "BlockIC0Dense", "ic0_dense", "sibling_pattern",
     "vcycle", "pcg", "solve", "PCGResult",
 ]

@@ -152,32 +152,66 @@ class BlockCholesky:
         return out
 
 
-class BlockIC0Dense:
-    """Coarse-level IC(0) option: pattern-restricted incomplete Cholesky of each
-    dense block A[idx, idx], the pattern being the block's nonzeros."""
+def ic0_dense(blk: np.ndarray, pat: np.ndarray) -> np.ndarray:
+    """Incomplete Cholesky with no fill of one dense symmetric block: the
+    right-looking Cholesky factorisation in which every update that would land
+    outside the pattern ``pat`` (boolean, symmetric, true on the diagonal) is
+    dropped.  Returns the lower factor L (zero off the pattern); raises
+    FloatingPointError on a pivot that is not positive."""
+    n = blk.shape[0]
+    W = np.tril(np.array(blk, dtype=np.float64)) * np.tril(pat)
+    for k in range(n):
+        if not W[k, k] > 0:
+            raise FloatingPointError("IC(0) pivot is not positive")
+        W[k, k] = np.sqrt(W[k, k])
+        for i in range(k + 1, n):
+            if pat[i, k]:
+                W[i, k] /= W[k, k]
+        for j in range(k + 1, n):
+            if not pat[j, k]:
+                continue
+            for i in range(j, n):
+                if pat[i, k] and pat[i, j]:
+                    W[i, j] -= W[i, k] * W[j, k]
+    return W
 
-    def __init__(self, A: sp.spmatrix, dofs: np.ndarray):
+
+def sibling_pattern(ratio, L: int) -> np.ndarray:
+    """Structural pattern of one parent's diagonal block of a coarse operator
+    A_l (l >= 2): the parent's children, lexicographic inside the parent (x
+    fastest) with L coordinates each, couple only to themselves and to their
+    face neighbours (A_l is a block 7-point stencil, Section 3), so the block
+    (child a, child b) is in the pattern when a == b or a, b share a face."""
+    rx, ry, rz = ratio
+    nch = rx * ry * rz
+    cz, cy, cx = np.unravel_index(np.arange(nch), (rz, ry, rx))
+    dist = np.abs(cx[:, None] - cx[None, :]) + np.abs(cy[:, None] - cy[None, :]) + np.abs(cz[:, None] - cz[None, :])
+    return np.kron(dist <= 1, np.ones((L, L), dtype=bool))
+
+
+class BlockIC0Dense:
+    """Coarse-level IC(0) smoother (Section 5 names incomplete Cholesky for
+    M_c): block Jacobi over the parents, each parent's diagonal block
+    A[idx, idx] factorised by ``ic0_dense`` on ``pattern`` (one boolean matrix
+    shared by all parents; by default each block's nonzero entries).  A parent
+    whose incomplete factorisation meets a pivot that is not positive is
+    factorised exactly instead (dense Cholesky; A_l is not an M-matrix, so IC(0)
+    can break down) and its index is listed in ``fallback``."""
+
+    def __init__(self, A: sp.spmatrix, dofs: np.ndarray, pattern: np.ndarray | None = None):
         A = sp.csr_matrix(A)
         self.dofs = dofs
         self.factors = []
-        for idx in dofs:
+        self.fallback = []
+        for P, idx in enumerate(dofs):
             blk = A[idx][:, idx].toarray()
-            pat = blk != 0.0
-            n = blk.shape[0]
-            W = np.tril(blk)
-            for k in range(n):
-                if W[k, k] <= 0:
-                    raise FloatingPointError("coarse IC(0) pivot is not positive")
-                W[k, k] = np.sqrt(W[k, k])
-                for i in range(k + 1, n):
-                    if pat[i, k]:
-                        W[i, k] /= W[k, k]
-                for j in range(k + 1, n):
-                    if not pat[j, k]:
-                        continue
-                    for i in range(j, n):
-                        if pat[i, k] and pat[i, j]:
-                            W[i, j] -= W[i, k] * W[j, k]
+            blk = 0.5 * (blk + blk.T)
+            pat = pattern if pattern is not None else blk != 0.0
+            try:
+                W = ic0_dense(blk, pat)
+            except FloatingPointError:
+                W = np.linalg.cholesky(blk)
+                self.fallback.append(P)
             self.factors.append(W)
 
     def solve(self, r: np.ndarray) -> np.ndarray:
@@ -276,7 +310,7 @@ def setup(kappa, h, opts: Options) -> Hierarchy:
         if opts.coarse_smoother == "chol":
             M.append(BlockCholesky(A[l - 1], pd))
         else:
-            M.append(BlockIC0Dense(A[l - 1], pd))
+            M.append(BlockIC0Dense(A[l - 1], pd, sibling_pattern(opts.ratio[l - 2], basis[l - 2].shape[1])))
 
     # coarsest: Moore-Penrose pseudo-inverse (Algorithm 1, A_cc^dagger)
     Ac = A[-1].toarray()

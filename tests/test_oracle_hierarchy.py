@@ -240,3 +240,75 @@ def test_coarse_ic0_option_runs():
 def test_single_element_level_is_rejected():
     with pytest.raises(ValueError):
         make(shape=(8, 8, 8), box=(4, 4, 4), L=(4, 4))
+
+
+# ------------------------------------------------------------------ coarse IC(0) (Section 5: incomplete Cholesky for M_c)
+def test_ic0_dense_hand_worked_3x3():
+    # one structural zero at (2, 1): the fill -l21 l31 / l22 = -1/2 that exact
+    # Cholesky would put there is dropped, so l33 = sqrt(6 - 1) instead of sqrt(4.75)
+    A = np.array([[4.0, 2.0, 2.0], [2.0, 5.0, 0.0], [2.0, 0.0, 6.0]])
+    L = oracle.ic0_dense(A, A != 0)
+    ref = np.array([[2.0, 0.0, 0.0], [1.0, 2.0, 0.0], [1.0, 0.0, np.sqrt(5.0)]])
+    np.testing.assert_allclose(L, ref, rtol=0, atol=1e-15)
+
+
+def test_ic0_dense_full_pattern_is_cholesky():
+    import scipy.linalg as sla
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((12, 12))
+    A = X @ X.T + 12 * np.eye(12)
+    L = oracle.ic0_dense(A, np.ones_like(A, dtype=bool))
+    np.testing.assert_allclose(L, sla.cholesky(A, lower=True), rtol=1e-13, atol=1e-13)
+
+
+def test_ic0_dense_matches_A_on_its_pattern():
+    # 2-D five-point matrix on a 4 x 4 grid: exact Cholesky fills the band, IC(0) keeps the
+    # pattern; L L^T equals A on the pattern (the defining property) and differs off it
+    rng = np.random.default_rng(5)
+    m = 4
+    n = m * m
+    A = np.zeros((n, n))
+    for i in range(n):
+        x, y = i % m, i // m
+        for j, ok in ((i + 1, x + 1 < m), (i + m, y + 1 < m)):
+            if ok:
+                t = rng.uniform(0.5, 2.0)
+                A[i, j] = A[j, i] = -t
+                A[i, i] += t
+                A[j, j] += t
+    A += np.diag(rng.uniform(0.1, 0.3, n))
+    pat = A != 0
+    L = oracle.ic0_dense(A, pat)
+    assert np.all(L[~np.tril(pat)] == 0.0)
+    LLt = L @ L.T
+    np.testing.assert_allclose(LLt[pat], A[pat], rtol=0, atol=1e-13 * np.abs(A).max())
+    assert np.abs(LLt[~pat]).max() > 1e-3              # the dropped fill
+    assert not np.allclose(L, np.linalg.cholesky(A))
+
+
+def test_block_ic0_falls_back_to_cholesky_on_breakdown():
+    import scipy.sparse as sps
+    # Kershaw's 4 x 4 SPD matrix: IC(0) on its nonzero pattern meets a negative pivot
+    K = np.array([[3.0, -2.0, 0.0, 2.0], [-2.0, 3.0, -2.0, 0.0], [0.0, -2.0, 3.0, -2.0], [2.0, 0.0, -2.0, 3.0]])
+    assert np.linalg.eigvalsh(K).min() > 0
+    with pytest.raises(FloatingPointError):
+        oracle.ic0_dense(K, K != 0)
+    good = np.diag([2.0, 3.0, 4.0, 5.0]) + np.diag([-0.5] * 3, 1) + np.diag([-0.5] * 3, -1)
+    A = sps.block_diag([good, K]).tocsr()
+    M = oracle.BlockIC0Dense(A, np.array([[0, 1, 2, 3], [4, 5, 6, 7]]))
+    assert M.fallback == [1]
+    np.testing.assert_allclose(M.factors[1], np.linalg.cholesky(K), rtol=1e-14)
+    r = np.arange(1.0, 9.0)
+    z = M.solve(r)
+    np.testing.assert_allclose(K @ z[4:], r[4:], rtol=1e-12)        # exact on the fallback block
+    np.testing.assert_allclose(good @ z[:4], r[:4], rtol=1e-12)     # tridiagonal: IC(0) is exact
+
+
+def test_sibling_pattern():
+    P = oracle.sibling_pattern((2, 2, 2), 1)
+    # child 0 of a 2 x 2 x 2 parent shares faces with children 1 (x), 2 (y), 4 (z)
+    assert list(np.flatnonzero(P[0])) == [0, 1, 2, 4]
+    assert list(np.flatnonzero(P[7])) == [3, 5, 6, 7]
+    assert (P == P.T).all() and P.sum() == 8 * 4
+    P3 = oracle.sibling_pattern((2, 1, 1), 3)
+    assert P3.shape == (6, 6) and P3.all()

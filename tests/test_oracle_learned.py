@@ -93,3 +93,30 @@ def test_output_weight_is_normalised_sqrt_S():
     S = np.exp(rng.normal(0, 2, size=(3, 64)))
     w = learned.out_weight(learned.features(S))
     np.testing.assert_allclose(w, np.sqrt(S / S.sum(axis=1, keepdims=True)), rtol=1e-12)
+
+
+def test_forward_hand_computed():
+    # 2 -> 2 -> 2 -> 2 network with small integer weights (exact in BF16), worked by hand:
+    #   x = (1, 1):  h1 = relu((3, 0) + (0.5, -3)) = (3.5, 0)
+    #                h2 = relu((3.5, 7) + (-1, 1)) = (2.5, 8)
+    #                o  = (5 - 8, 8) + (1, -2)     = (-2, 6)
+    #                w  = (1/sqrt 2, 1/sqrt 2)      (equal inputs: equal S)
+    #   x = (0, 1):  h1 = (2.5, 0), h2 = (1.5, 6), o = (-2, 4),
+    #                w  = sqrt((e^-8, 1) / (1 + e^-8))
+    W1 = np.array([[1.0, -1.0], [2.0, 1.0]])
+    b1 = np.array([0.5, -3.0])
+    W2 = np.array([[1.0, 2.0], [3.0, -1.0]])
+    b2 = np.array([-1.0, 1.0])
+    W3 = np.array([[2.0, 0.0], [-1.0, 1.0]])
+    b3 = np.array([1.0, -2.0])
+    params = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+    dims, w_off, b_off = (2, 2, 2, 2), [0, 6, 12], [4, 10, 16]
+    Ws, bs = learned.unpack(params, dims, w_off, b_off)
+    x = np.array([[1.0, 1.0], [0.0, 1.0]])
+    h1, h2, y = learned.forward(Ws, bs, x)
+    np.testing.assert_array_equal(h1, [[3.5, 0.0], [2.5, 0.0]])
+    np.testing.assert_array_equal(h2, [[2.5, 8.0], [1.5, 6.0]])
+    e8 = np.exp(-8.0)
+    ref = np.array([[-2.0 / np.sqrt(2.0), 6.0 / np.sqrt(2.0)],
+                    [-2.0 * np.sqrt(e8 / (1.0 + e8)), 4.0 * np.sqrt(1.0 / (1.0 + e8))]])
+    np.testing.assert_allclose(y, ref, rtol=1e-15, atol=0)
