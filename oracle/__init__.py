@@ -13,7 +13,9 @@ reordering beyond what the definition states:
 * ``tpfa``       -- normalised permeability, harmonic-average face
                     coefficients and the cell-centred pressure matrix
                     A = B M_t^{-1} B^T in its two-point-flux form (Section 2.2,
-                    Eq. (discrete varia), Fig. (kappa edge)).
+                    Eq. (discrete varia), Fig. (kappa edge)); the velocity
+                    recovered from the pressure (Eq. (velocity)) and its
+                    discrete divergence.
 * ``spectral``   -- the level-1 local generalised eigenproblem (Eq. (spepb))
                     and the level-l>=2 local problem posed in the coarse space
                     (Eq. (spectral cc)); restriction matrices R_l.
@@ -31,14 +33,14 @@ Pins (tests marked ``not gpu``) tie each function to closed forms, to values
 the paper prints, to library routines on special cases and to brute force.
 """
 from .tpfa import (as_components, normalized_permeability, trace_weight,
-                   face_transmissibilities, assemble, apply_A, interior_face_mask)
+                   face_transmissibilities, assemble, apply_A, interior_face_mask, velocity, divergence)
 from .spectral import element_cells, level1_eigenpairs, coarse_eigenpairs
 from .hierarchy import Options, Hierarchy, setup, BlockIC0, BlockIC0Dense, ic0_dense, sibling_pattern
 from .solver import vcycle, pcg, solve, PCGResult
 
 __all__ = [
     "as_components", "normalized_permeability", "trace_weight",
-    "face_transmissibilities", "assemble", "apply_A", "interior_face_mask",
+    "face_transmissibilities", "assemble", "apply_A", "interior_face_mask", "velocity", "divergence",
     "element_cells", "level1_eigenpairs", "coarse_eigenpairs",
     "Options", "Hierarchy", "setup", "BlockIC0", "BlockIC0Dense", "ic0_dense", "sibling_pattern",
     "vcycle", "pcg", "solve", "PCGResult",

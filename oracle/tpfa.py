@@ -112,3 +112,41 @@ def assemble(T: np.ndarray) -> sp.csr_matrix:
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(n, n))
     return A.tocsr()
+
+
+def velocity(T: np.ndarray, p, h) -> np.ndarray:
+    """Velocity recovered from the pressure (Section 2.2: v = M_t^{-1} B^T p,
+    written out in Eq. (velocity)): on the face between cell i and its +d
+    neighbour j, v = -kappa_e (p_j - p_i) / h_d, where kappa_e / h_d^2 is the
+    face coefficient T_e.  Returns (3, nz, ny, nx): component d at cell c is the
+    velocity on c's +d face; zero on boundary faces (no flow)."""
+    _, nz, ny, nx = T.shape
+    pp = np.asarray(p, dtype=np.float64).reshape(nz, ny, nx)
+    v = np.zeros_like(T)
+    kx = T[0][:, :, :-1] * h[0] * h[0]
+    v[0][:, :, :-1] = -kx * (pp[:, :, 1:] - pp[:, :, :-1]) / h[0]
+    ky = T[1][:, :-1, :] * h[1] * h[1]
+    v[1][:, :-1, :] = -ky * (pp[:, 1:, :] - pp[:, :-1, :]) / h[1]
+    kz = T[2][:-1, :, :] * h[2] * h[2]
+    v[2][:-1, :, :] = -kz * (pp[1:, :, :] - pp[:-1, :, :]) / h[2]
+    return v
+
+
+def divergence(v: np.ndarray, h) -> np.ndarray:
+    """Discrete divergence of a face velocity field (the cell balance stated
+    after Eq. (discrete varia), divided by the cell volume): for each cell,
+    sum over d of (v on its +d face - v on its -d face) / h_d; the -d face of
+    a cell is the +d face of its -d neighbour, and boundary faces carry zero."""
+    _, nz, ny, nx = v.shape
+    out = np.zeros((nz, ny, nx))
+    for d in range(3):
+        vp = v[d]
+        vm = np.zeros_like(vp)
+        if d == 0:
+            vm[:, :, 1:] = vp[:, :, :-1]
+        elif d == 1:
+            vm[:, 1:, :] = vp[:, :-1, :]
+        else:
+            vm[1:, :, :] = vp[:-1, :, :]
+        out += (vp - vm) / h[d]
+    return out

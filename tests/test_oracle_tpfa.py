@@ -125,3 +125,46 @@ def test_matrix_free_apply_closed_form_and_assembled(shape):
     ref = oracle.assemble(T) @ p.ravel()
     np.testing.assert_allclose(q.ravel(), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
     assert abs(q.sum()) < 1e-12 * np.abs(q).max()          # A 1 = 0 implies 1^T A p = 0
+
+
+# ------------------------------------------------------------------ velocity recovery (Eq. (velocity))
+def test_velocity_two_cells_by_hand():
+    # kappa^x = (1, 3) on a 2 x 1 x 1 grid, h = (1/2, 1, 1): normalised 4 and 12, harmonic
+    # face coefficient 2 / (1/4 + 1/12) = 6, kappa_e = 6 h^2 = 1.5; p = (1, 3):
+    # v = -1.5 (3 - 1) / (1/2) = -6 on the interior face, 0 on the boundary
+    kap = np.array([[[1.0, 3.0]]])
+    h = (0.5, 1.0, 1.0)
+    T = oracle.face_transmissibilities(kap, h)
+    v = oracle.velocity(T, np.array([1.0, 3.0]), h)
+    np.testing.assert_allclose(v[0].ravel(), [-6.0, 0.0], rtol=1e-15)
+    assert not v[1].any() and not v[2].any()
+    # divergence: cell 0 loses -6 through +x (-6 / 0.5 = -12), cell 1 gains it
+    np.testing.assert_allclose(oracle.divergence(v, h).ravel(), [-12.0, 12.0], rtol=1e-15)
+
+
+def test_velocity_of_linear_pressure_is_darcy_flux():
+    # homogeneous kappa = 5, p = x at the cell centres: v_x = -kappa dp/dx = -5 on interior
+    # x faces, 0 on the x boundary faces, v_y = v_z = 0
+    shape = (3, 4, 6)
+    h = (1 / 6, 1 / 4, 1 / 3)
+    T = oracle.face_transmissibilities(np.full(shape, 5.0), h)
+    x = (np.arange(6) + 0.5) * h[0]
+    p = np.broadcast_to(x[None, None, :], shape)
+    v = oracle.velocity(T, p, h)
+    np.testing.assert_allclose(v[0][:, :, :-1], -5.0, rtol=1e-13)
+    assert not v[0][:, :, -1].any() and not v[1].any() and not v[2].any()
+
+
+def test_divergence_of_velocity_is_A_p_and_conserves_mass():
+    # div v = A p (the assembled matrix of Eq. (discrete varia), an independent route), and
+    # with no-flow boundaries the cell balances sum to zero
+    rng = np.random.default_rng(7)
+    shape = (5, 4, 6)
+    h = (1 / 6, 1 / 4, 1 / 5)
+    kap = np.exp(rng.normal(0, 2, size=(3,) + shape))
+    T = oracle.face_transmissibilities(kap, h)
+    p = rng.standard_normal(shape)
+    div = oracle.divergence(oracle.velocity(T, p, h), h)
+    Ap = oracle.assemble(T) @ p.ravel()
+    np.testing.assert_allclose(div.ravel(), Ap, rtol=0, atol=1e-11 * np.abs(Ap).max())
+    assert abs(div.sum()) < 1e-10 * np.abs(div).sum()
