@@ -11,6 +11,53 @@ import numpy as np
 from .hierarchy import Hierarchy
 
 
+class _Level1FP32:
+    """Level 1 of the hierarchy with its data rounded to FP32: the fine
+    operator, the basis Phi (as R_1 and R_1^T) and the IC(0) factor.  Products
+    with FP32 operands stay in FP32 (NumPy and SciPy keep the operand type)."""
+
+    def __init__(self, H: Hierarchy):
+        from .hierarchy import BlockIC0
+        self.A = H.A[0].astype(np.float32)
+        self.R = H.R[0].astype(np.float32).tocsr()
+        self.RT = self.R.T.tocsr()
+        M = H.M[0]
+        M32 = BlockIC0.__new__(BlockIC0)
+        M32.__dict__.update(M.__dict__)
+        M32.L = {k: v.astype(np.float32) for k, v in M.L.items()}
+        self.M = M32
+
+
+def _level1_fp32(H: Hierarchy) -> _Level1FP32:
+    cache = getattr(H, "_fp32_level1", None)
+    if cache is None:
+        cache = _Level1FP32(H)
+        H._fp32_level1 = cache
+    return cache
+
+
+def vcycle_mixed(H: Hierarchy, f: np.ndarray) -> np.ndarray:
+    """The V-cycle of ``vcycle`` with level 1 in single precision, the split of
+    the mixed form: the right-hand side rounded to FP32; pre-smoothing,
+    residual, restriction, prolongation and post-smoothing on level 1 with FP32
+    data and FP32 arithmetic; the restricted residual widened to FP64; every
+    coarse level and the coarsest pseudo-inverse in FP64; the coarse correction
+    rounded to FP32 for the prolongation; the result widened to FP64.  The
+    order of the steps is that of ``vcycle`` (Algorithm 1)."""
+    L1 = _level1_fp32(H)
+    f32 = np.asarray(f, dtype=np.float64).astype(np.float32)
+    nu = H.opts.nu[0]
+    u = np.zeros_like(f32)
+    for _ in range(nu):
+        u = u + L1.M.solve(f32 - L1.A @ u)
+    rc = (L1.R @ (f32 - L1.A @ u)).astype(np.float64)
+    e = vcycle(H, rc, 2) if H.opts.n_levels > 2 else H.coarsest_pinv @ rc
+    u = u + L1.RT @ e.astype(np.float32)
+    for _ in range(nu):
+        u = u + L1.M.solve(f32 - L1.A @ u)
+    return u.astype(np.float64)
+
+
 def vcycle(H: Hierarchy, f: np.ndarray, level: int = 1) -> np.ndarray:
     """One application of the multigrid preconditioner on level ``level``
     (Algorithm 1, applied recursively: the map r_c -> e_c of Algorithm 1 is
@@ -50,13 +97,17 @@ class PCGResult:
 
 
 def pcg(A, b: np.ndarray, precond=None, rtol: float = 1e-8, max_iter: int = 1000,
-        x0: np.ndarray | None = None) -> PCGResult:
+        x0: np.ndarray | None = None, flexible: bool = False) -> PCGResult:
     """Preconditioned conjugate gradients (Hestenes-Stiefel recurrences) for the
     singular consistent system A x = b of Eq. (p).
 
     The mean of b is removed first (compatibility condition, Section 2.1) and
     the returned x has zero mean (uniqueness condition, Section 2.1).  Stops
-    when ||b - A x_k||_2 <= rtol ||b||_2 on the recurrence residual."""
+    when ||b - A x_k||_2 <= rtol ||b||_2 on the recurrence residual.  With
+    ``flexible`` the direction update takes the Polak-Ribiere coefficient
+    beta = z_{k+1}^T (r_{k+1} - r_k) / z_k^T r_k, which tolerates a
+    preconditioner that is not exactly the same linear map every time (the
+    mixed form's rounded V-cycle)."""
     b = np.asarray(b, dtype=np.float64)
     mean = float(b.mean())
     b = b - mean
@@ -86,12 +137,18 @@ def pcg(A, b: np.ndarray, precond=None, rtol: float = 1e-8, max_iter: int = 1000
             break
         z = apply_p(r)
         rz_new = float(r @ z)
-        beta = rz_new / rz
+        if flexible:
+            beta = float(z @ (-alpha * q)) / rz      # z_{k+1}^T (r_{k+1} - r_k) / z_k^T r_k
+        else:
+            beta = rz_new / rz
         p = z + beta * p
         rz = rz_new
     return PCGResult(x - x.mean(), k, converged, res, mean)
 
 
-def solve(H: Hierarchy, b: np.ndarray, rtol: float = 1e-8, max_iter: int = 1000) -> PCGResult:
-    """PCG on the fine system preconditioned by one V-cycle per iteration."""
-    return pcg(H.A[0], np.asarray(b, dtype=np.float64).ravel(), lambda r: vcycle(H, r), rtol, max_iter)
+def solve(H: Hierarchy, b: np.ndarray, rtol: float = 1e-8, max_iter: int = 1000, mixed: bool = False) -> PCGResult:
+    """PCG on the fine system preconditioned by one V-cycle per iteration; with
+    ``mixed`` the V-cycle's level 1 runs in FP32 (``vcycle_mixed``) and the PCG
+    takes the flexible beta."""
+    pre = (lambda r: vcycle_mixed(H, r)) if mixed else (lambda r: vcycle(H, r))
+    return pcg(H.A[0], np.asarray(b, dtype=np.float64).ravel(), pre, rtol, max_iter, flexible=mixed)

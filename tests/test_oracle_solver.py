@@ -124,3 +124,50 @@ def test_more_coarse_vectors_fewer_iterations():
         b[0], b[-1] = 1.0, -1.0
         its.append(oracle.solve(H, b, 1e-8).iterations)
     assert its[0] >= its[1] >= its[2]
+
+
+# ------------------------------------------------------------------ the mixed form's V-cycle and flexible PCG
+def _small_hierarchy(contrast=1e2, seed=3):
+    import fields
+    N = 16
+    kap = fields.grf_lognormal((N, N, N), seed=seed, contrast=contrast)
+    opts = oracle.Options(n_levels=3, block=(4, 4, 4), ratio=[(2, 2, 2)], n_eig=[4, 4], nu=[1, 1])
+    return oracle.setup(kap, (1 / N,) * 3, opts)
+
+
+def test_mixed_vcycle_is_the_vcycle_in_single_precision():
+    H = _small_hierarchy()
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(H.dims[0])
+    r -= r.mean()
+    z64 = oracle.vcycle(H, r)
+    z32 = oracle.vcycle_mixed(H, r)
+    d = np.linalg.norm(z32 - z64) / np.linalg.norm(z64)
+    # level 1 really runs in FP32 (differs from FP64 by rounding), and only by rounding:
+    # unit roundoff 6e-8 times the growth through the smoother at contrast 1e2
+    assert 1e-9 < d < 1e-4, d
+    assert z32.dtype == np.float64
+
+
+def test_flexible_pcg_equals_standard_with_a_fixed_preconditioner():
+    # with an exactly repeatable (linear, symmetric) preconditioner the Polak-Ribiere beta
+    # equals the Fletcher-Reeves one in exact arithmetic: same iterations, same iterates
+    H = _small_hierarchy()
+    b = np.zeros(H.dims[0])
+    b[0], b[-1] = 1.0, -1.0
+    std = oracle.pcg(H.A[0], b, lambda r: oracle.vcycle(H, r), rtol=1e-10)
+    flx = oracle.pcg(H.A[0], b, lambda r: oracle.vcycle(H, r), rtol=1e-10, flexible=True)
+    assert abs(std.iterations - flx.iterations) <= 1
+    k = min(std.iterations, flx.iterations)
+    np.testing.assert_allclose(flx.residuals[:k], std.residuals[:k], rtol=1e-6)
+    assert np.linalg.norm(flx.x - std.x) <= 1e-8 * np.linalg.norm(std.x)
+
+
+def test_mixed_solve_reaches_the_tolerance():
+    H = _small_hierarchy(contrast=1e3)
+    b = np.zeros(H.dims[0])
+    b[0], b[-1] = 1.0, -1.0
+    res = oracle.solve(H, b, rtol=1e-8, mixed=True)
+    assert res.converged
+    bm = b - b.mean()
+    assert np.linalg.norm(bm - H.A[0] @ res.x) <= 2e-8 * np.linalg.norm(bm)
