@@ -46,6 +46,8 @@ typedef struct msmg_net msmg_net;                /* opaque: learned warm-start n
 /* status codes */
 #define MSMG_OK                      0
 #define MSMG_NOT_CONVERGED           1   /* warning: max_iter reached            */
+#define MSMG_COARSE_IC_FALLBACK      2   /* warning: a coarse IC(0) factor broke  */
+                                         /* down; that parent uses its exact block */
 #define MSMG_ERR_INVALID_ARG        -1
 #define MSMG_ERR_NOT_DIVISIBLE      -2   /* element sizes do not tile the grid   */
 #define MSMG_ERR_BAD_KAPPA          -3   /* non-positive or non-finite kappa     */
@@ -63,6 +65,11 @@ typedef struct msmg_net msmg_net;                /* opaque: learned warm-start n
 #define MSMG_MIXED  1   /* FP32 fine-level V-cycle and bases, FP64 coarse levels,       */
                         /* coarsest solve and outer PCG; the level-1 eigensolve runs in */
                         /* FP32 to a residual near FP32's reach, then FP64 to eig_tol   */
+
+/* coarse-level smoothers (block Jacobi over the parents of each level l >= 2) */
+#define MSMG_BLOCK_CHOL 0   /* exact inverse of each parent's diagonal block of A_l       */
+#define MSMG_BLOCK_IC0  1   /* incomplete Cholesky of it (Section 5): no fill outside the  */
+                            /* block pattern of the children's face adjacency             */
 
 /* kappa element types */
 #define MSMG_F64 0
@@ -99,6 +106,11 @@ typedef struct {
                                        /* level-1 element's cells and n_vec equals n_eig[0] - 1:     */
                                        /* its guesses seed the level-1 subspace iteration (elements  */
                                        /* of more than 96 cells), which still runs to eig_tol        */
+    int coarse_smoother;               /* MSMG_BLOCK_CHOL (default) or MSMG_BLOCK_IC0: the factor of */
+                                       /* each parent's diagonal block on levels >= 2 (Section 5);  */
+                                       /* with MSMG_BLOCK_IC0 a parent whose incomplete factor meets */
+                                       /* a pivot <= 0 uses its exact block and msmg_setup returns   */
+                                       /* the warning MSMG_COARSE_IC_FALLBACK                        */
 } msmg_options;
 
 typedef struct {
@@ -303,6 +315,24 @@ int msmg_import_bases(msmg_ctx* ctx, const double* const* bases, msmg_stream str
  * out: device, dim(W_l)^2 values, row-major.  Intended for small grids.
  */
 int msmg_export_operator(msmg_ctx* ctx, int level, double* out, msmg_stream stream);
+
+/*
+ * Velocity recovery (Section 2.2): v = M_t^{-1} B^T p, the two-point flux of Eq. (velocity)
+ * on every face, v_f = -kappa_f (p_j - p_i) / h_d = -T_f h_d (p_j - p_i) for the face between
+ * cell i and its +d neighbour j (T_f the harmonic-average face coefficient of Fig. (kappa
+ * edge)), zero on boundary faces (no flow); and the discrete mass balance of every cell,
+ * div_i = sum_d (v_{i+e_d/2} - v_{i-e_d/2}) / h_d against b_i = f_i - mean(f) (the
+ * conservation identity that follows Eq. (discrete varia), in three directions).
+ *   p        device, n FP64 pressures, natural order (for instance msmg_solve's x)
+ *   f        device, n FP64 sources, natural order (msmg_solve's rhs; its mean is removed
+ *            here as the solve removes it)
+ *   v        device, 3 x n FP64, natural order: v[d][cell] = velocity on the cell's +d face
+ *   balance  host, 2 doubles (may be NULL): ||div - b||_2 and ||b||_2; their ratio equals the
+ *            solve's relative residual ||b - A p|| / ||b||.  With balance the call
+ *            synchronises the stream.
+ * Uses the context's reduction scratch: not concurrently with a solve on the same context.
+ */
+int msmg_velocity(msmg_ctx* ctx, const double* p, const double* f, double* v, double* balance, msmg_stream stream);
 
 /* Face coefficients T[d][cell] (d = x, y, z; face between cell and its +d neighbour,
  * zero on the boundary), FP64, natural order: device, 3 x (nx*ny*nz). */

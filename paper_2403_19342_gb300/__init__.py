@@ -27,8 +27,10 @@ FP64, MIXED = 0, 1
 F64, F32 = 0, 1
 FLAG_X0, FLAG_HOST_IO, FLAG_NO_GRAPH = 1, 2, 4
 
+BLOCK_CHOL, BLOCK_IC0 = 0, 1
+
 STATUS = {
-    0: "MSMG_OK", 1: "MSMG_NOT_CONVERGED", -1: "MSMG_ERR_INVALID_ARG", -2: "MSMG_ERR_NOT_DIVISIBLE",
+    0: "MSMG_OK", 1: "MSMG_NOT_CONVERGED", 2: "MSMG_COARSE_IC_FALLBACK", -1: "MSMG_ERR_INVALID_ARG", -2: "MSMG_ERR_NOT_DIVISIBLE",
     -3: "MSMG_ERR_BAD_KAPPA", -4: "MSMG_ERR_SINGLE_BLOCK", -5: "MSMG_ERR_BREAKDOWN",
     -6: "MSMG_ERR_EIG_NOT_CONVERGED", -7: "MSMG_ERR_WORKSPACE", -8: "MSMG_ERR_CUDA",
     -9: "MSMG_ERR_NOT_FACTORIZABLE", -10: "MSMG_ERR_UNSUPPORTED",
@@ -51,7 +53,7 @@ class msmg_options(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("block", C.c_int * 3), ("ratio", (C.c_int * 3) * MAX_LEVELS),
                 ("n_eig", C.c_int * MAX_LEVELS), ("nu", C.c_int * MAX_LEVELS), ("precision", C.c_int),
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int), ("autotune", C.c_int),
-                ("warm_start", C.c_void_p)]
+                ("warm_start", C.c_void_p), ("coarse_smoother", C.c_int)]
 
 
 class msmg_setup_info(C.Structure):
@@ -119,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_learning_data": (I, [P, P, P, P]),
         "msmg_dot_noalloc": (I, [P, P, I64, C.POINTER(D), P]),
         "msmg_check_conversions": (I, [P, P, I64, P, P, P]),
+        "msmg_velocity": (I, [P, P, P, P, C.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -138,7 +141,7 @@ def exported_symbols():
             "msmg_net_workspace_size", "msmg_net_create",
             "msmg_net_destroy", "msmg_net_param_count", "msmg_net_param_offsets", "msmg_net_get_params",
             "msmg_net_set_params", "msmg_net_forward", "msmg_net_gradients", "msmg_net_train_step",
-            "msmg_learning_data", "msmg_check_conversions"]
+            "msmg_learning_data", "msmg_check_conversions", "msmg_velocity"]
 
 
 def _check(status: int) -> int:
@@ -176,6 +179,7 @@ class Options:
     eig_max_iter: int = 0
     autotune: bool = False             # time the V-cycle variants at set-up (msmg_autotune)
     warm_start: object = None          # a WarmStartNet (or its handle) seeds the level-1 eigensolves
+    coarse_smoother: int = BLOCK_CHOL  # BLOCK_CHOL (exact parent blocks) or BLOCK_IC0 (Section 5)
 
     def to_c(self) -> msmg_options:
         o = msmg_options()
@@ -196,6 +200,7 @@ class Options:
         o.autotune = 1 if self.autotune else 0
         ws = self.warm_start
         o.warm_start = (ws.handle if hasattr(ws, "handle") else ws) or None
+        o.coarse_smoother = self.coarse_smoother
         return o
 
 
@@ -357,6 +362,17 @@ def msmg_import_bases(ctx: int, bases: list, stream=None) -> int:
 
 def msmg_export_operator(ctx: int, level: int, out: torch.Tensor, stream=None) -> None:
     _check(load_library().msmg_export_operator(ctx, level, _ptr(out, torch.float64), _stream(stream)))
+
+
+def msmg_velocity(ctx: int, p: torch.Tensor, f: torch.Tensor, v: torch.Tensor, stream=None) -> tuple[float, float]:
+    """Face velocities v[3][nz][ny][nx] from the pressure p (Eq. (velocity)) and the mass
+    balance (||div v - b||_2, ||b||_2), b = f - mean(f)."""
+    if p.numel() * 3 != v.numel() or f.numel() != p.numel():
+        raise ValueError("p, f: n values each; v: 3 n values")
+    bal = (C.c_double * 2)()
+    _check(load_library().msmg_velocity(ctx, _ptr(p, torch.float64), _ptr(f, torch.float64), _ptr(v, torch.float64),
+                                        bal, _stream(stream)))
+    return bal[0], bal[1]
 
 
 def msmg_export_faces(ctx: int, out: torch.Tensor, stream=None) -> None:
@@ -610,6 +626,13 @@ class Solver:
         y = torch.empty((m, L - 1, nb), dtype=torch.float32, device="cuda")
         msmg_learning_data(self.ctx, x, y, self.stream)
         return x, y
+
+    def velocity(self, p: torch.Tensor, f: torch.Tensor):
+        """(v [3, nz, ny, nx], mass balance (||div v - b||, ||b||)) of a pressure field."""
+        v = torch.empty((3,) + self.shape, dtype=torch.float64, device="cuda")
+        bal = msmg_velocity(self.ctx, p.to(torch.float64).contiguous(), f.to(torch.float64).contiguous(), v,
+                            self.stream)
+        return v, bal
 
     def export_faces(self) -> torch.Tensor:
         out = torch.empty((3,) + self.shape, dtype=torch.float64, device="cuda")

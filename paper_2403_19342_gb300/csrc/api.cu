@@ -62,6 +62,7 @@ int validate(const msmg_grid* g, const msmg_options* o) {
   if (!(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0)) return MSMG_ERR_INVALID_ARG;
   if (o->n_levels < 2 || o->n_levels > kMaxLevels) return MSMG_ERR_INVALID_ARG;
   if (o->precision != MSMG_FP64 && o->precision != MSMG_MIXED) return MSMG_ERR_INVALID_ARG;
+  if (o->coarse_smoother != MSMG_BLOCK_CHOL && o->coarse_smoother != MSMG_BLOCK_IC0) return MSMG_ERR_INVALID_ARG;
   LevelShape sh;
   int st = shapes(g, o, sh);
   if (st) return st;
@@ -235,7 +236,8 @@ static void build_tables(const msmg_ctx* c, const LevelShape& sh, std::vector<st
 
 static int check_flags(msmg_ctx* c, cudaStream_t s) {
   int h[8];
-  double d[4];   // [0] eig residual max, [1] factorisation failure, [2] max T, [3] max 1/T
+  double d[9];   // [0] eig residual max, [1] factorisation failure, [2] max T, [3] max 1/T,
+                 // [8] a coarse IC(0) factor fell back to the exact block
   MSMG_CUDA_TRY(cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, s));
   MSMG_CUDA_TRY(cudaMemcpyAsync(d, c->dtmp, sizeof(d), cudaMemcpyDeviceToHost, s));
   MSMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -247,6 +249,7 @@ static int check_flags(msmg_ctx* c, cudaStream_t s) {
   c->info.eig_iterations_max = h[3];
   c->info.eig_iterations_total = h[4];
   if (h[2]) return MSMG_ERR_EIG_NOT_CONVERGED;
+  if (d[8] != 0.0) return MSMG_COARSE_IC_FALLBACK;
   return 0;
 }
 
@@ -658,6 +661,7 @@ const char* msmg_status_string(int s) {
   switch (s) {
     case MSMG_OK: return "ok";
     case MSMG_NOT_CONVERGED: return "not converged within max_iter";
+    case MSMG_COARSE_IC_FALLBACK: return "a coarse IC(0) factor broke down; its parent uses the exact block";
     case MSMG_ERR_INVALID_ARG: return "invalid argument";
     case MSMG_ERR_NOT_DIVISIBLE: return "element sizes do not tile the grid";
     case MSMG_ERR_BAD_KAPPA: return "permeability not positive and finite";

@@ -182,8 +182,52 @@ __global__ void k_galerkin1(const double* __restrict__ T, const double* __restri
 }
 
 // ------------------------------------------------------------------ coarse levels
+// Incomplete Cholesky with no fill (Section 5: incomplete Cholesky for the
+// coarse smoother) of a parent's diagonal block A (nP x nP, shared memory) into
+// the lower factor Lf.  The pattern is structural: A_l is a block 7-point
+// stencil, so the block (child a, child b), L x L, is in it when the children
+// (lexicographic inside the parent, rx x ry x rz) are equal or share a face.
+// Right-looking order: pivot k, column k scaled, then the updates of the
+// trailing pattern entries.  Returns false (every thread) on a pivot that is
+// not positive.  flag: one shared int of scratch.
+__device__ __forceinline__ bool sib_pat(int i, int j, int L, int rx, int ry) {
+  const int a = i / L, b = j / L;
+  const int ax = a % rx, ay = (a / rx) % ry, az = a / (rx * ry);
+  const int bx = b % rx, by = (b / rx) % ry, bz = b / (rx * ry);
+  return abs(ax - bx) + abs(ay - by) + abs(az - bz) <= 1;
+}
+__device__ bool ic0_factor(const double* A, double* Lf, int nP, int L, int rx, int ry, double* flag) {
+  for (int idx = threadIdx.x; idx < nP * nP; idx += blockDim.x) {
+    const int i = idx / nP, j = idx % nP;
+    Lf[idx] = (j <= i && sib_pat(i, j, L, rx, ry)) ? A[idx] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < nP; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = Lf[k * nP + k];
+      flag[0] = d > 0.0 ? 0.0 : 1.0;
+      Lf[k * nP + k] = d > 0.0 ? sqrt(d) : d;
+    }
+    __syncthreads();
+    if (flag[0] != 0.0) return false;
+    const double dk = Lf[k * nP + k];
+    for (int i = k + 1 + threadIdx.x; i < nP; i += blockDim.x)
+      if (sib_pat(i, k, L, rx, ry)) Lf[i * nP + k] /= dk;
+    __syncthreads();
+    const int m = nP - k - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+      if (j > i) continue;
+      if (sib_pat(j, k, L, rx, ry) && sib_pat(i, k, L, rx, ry) && sib_pat(i, j, L, rx, ry))
+        Lf[i * nP + j] -= Lf[i * nP + k] * Lf[j * nP + k];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // One CTA per parent P of level l.  nP <= 96.
-__global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, int given) {
+__global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, int given, int ic0) {
   extern __shared__ double sm[];
   const int nP = lv.nP, L = lv.L, L2 = L * L, Ln = lv.Lnext, Ln2 = Ln * Ln;
   double* A = sm;                 // parent's diagonal block of A_l
@@ -295,7 +339,21 @@ __global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, in
     }
   }
   __syncthreads();
-  // smoother: inverse of the parent's diagonal block
+  // smoother: the inverse of the parent's diagonal block (exact block Jacobi), or
+  // of L L^T with L its incomplete Cholesky factor (IC(0) block Jacobi)
+  if (ic0 && ic0_factor(A, N, nP, L, lv.rx, lv.ry, cs)) {
+    // A <- L L^T (then inverted like the exact block)
+    for (int idx = threadIdx.x; idx < nP * nP; idx += blockDim.x) {
+      const int i = idx / nP, j = idx % nP;
+      const int kmax = i < j ? i : j;
+      double acc = 0.0;
+      for (int k = 0; k <= kmax; ++k) acc += N[i * nP + k] * N[j * nP + k];
+      A[idx] = acc;
+    }
+    __syncthreads();
+  } else if (ic0 && threadIdx.x == 0) {
+    atomic_max_pos(&stats[8], 1.0);   // this parent fell back to its exact block
+  }
   gj_inverse(A, nP, cs, V);
   for (int idx = threadIdx.x; idx < nP * nP; idx += blockDim.x) {
     const double v = A[idx];
@@ -500,7 +558,7 @@ int launch_coarse_setup(msmg_ctx* c, int l, cudaStream_t s) {
   if (lv.nP > 96) return MSMG_ERR_UNSUPPORTED;
   const size_t sm = jac_smem(lv.nP, 3);
   cudaFuncSetAttribute(k_coarse_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 0);
+  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 0, c->opts.coarse_smoother == MSMG_BLOCK_IC0);
   k_coarse_galerkin_off<<<(unsigned)lv.mP, 128, 0, s>>>(lv, nx);
   return 0;
 }
@@ -512,7 +570,7 @@ int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s) {
   if (lv.nP > 96) return MSMG_ERR_UNSUPPORTED;
   const size_t sm = jac_smem(lv.nP, 3);
   cudaFuncSetAttribute(k_coarse_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 1);
+  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 1, c->opts.coarse_smoother == MSMG_BLOCK_IC0);
   k_coarse_galerkin_off<<<(unsigned)lv.mP, 128, 0, s>>>(lv, nx);
   return 0;
 }
