@@ -36,12 +36,12 @@ from .tpfa import (as_components, normalized_permeability, trace_weight,
                    face_transmissibilities, assemble, apply_A, interior_face_mask, velocity, divergence)
 from .spectral import element_cells, level1_eigenpairs, coarse_eigenpairs
 from .hierarchy import Options, Hierarchy, setup, BlockIC0, BlockIC0Dense, ic0_dense, sibling_pattern
-from .solver import vcycle, vcycle_mixed, pcg, solve, PCGResult
+from .solver import vcycle, vcycle_mixed, vcycle_two_grid, coarse_pinv, pcg, solve, PCGResult
 
 __all__ = [
     "as_components", "normalized_permeability", "trace_weight",
     "face_transmissibilities", "assemble", "apply_A", "interior_face_mask", "velocity", "divergence",
     "element_cells", "level1_eigenpairs", "coarse_eigenpairs",
     "Options", "Hierarchy", "setup", "BlockIC0", "BlockIC0Dense", "ic0_dense", "sibling_pattern",
-    "vcycle", "vcycle_mixed", "pcg", "solve", "PCGResult",
+    "vcycle", "vcycle_mixed", "vcycle_two_grid", "coarse_pinv", "pcg", "solve", "PCGResult",
 ]

@@ -87,6 +87,36 @@ def vcycle(H: Hierarchy, f: np.ndarray, level: int = 1) -> np.ndarray:
     return u
 
 
+def coarse_pinv(H: Hierarchy) -> np.ndarray:
+    """Dense Moore-Penrose pseudo-inverse of A_2 = R_1 A R_1^T (singular, with
+    the null vector of Section 3's remark), cached on the hierarchy."""
+    P = getattr(H, "_coarse_pinv", None)
+    if P is None:
+        Ac = H.A[1].toarray()
+        P = np.linalg.pinv(0.5 * (Ac + Ac.T), rcond=1e-13, hermitian=True)
+        H._coarse_pinv = P
+    return P
+
+
+def vcycle_two_grid(H: Hierarchy, f: np.ndarray) -> np.ndarray:
+    """The exact two-grid preconditioner P_TG of Eq. (B_TG): Algorithm 1's fine
+    steps with the coarse correction e_c = A_c^dagger r_c solved exactly (A_c =
+    A_2), in place of the recursive cycle B_c^{-1} of Eq. (B_c).  Starting from
+    u = 0: pre-smoothing, restriction, exact coarse solve, prolongation,
+    post-smoothing."""
+    A, M, R = H.A[0], H.M[0], H.R[0]
+    nu = H.opts.nu[0]
+    u = np.zeros_like(f)
+    for _ in range(nu):
+        u = u + M.solve(f - A @ u)
+    rc = R @ (f - A @ u)
+    e = coarse_pinv(H) @ rc
+    u = u + R.T @ e
+    for _ in range(nu):
+        u = u + M.solve(f - A @ u)
+    return u
+
+
 @dataclass
 class PCGResult:
     x: np.ndarray
@@ -146,9 +176,14 @@ def pcg(A, b: np.ndarray, precond=None, rtol: float = 1e-8, max_iter: int = 1000
     return PCGResult(x - x.mean(), k, converged, res, mean)
 
 
-def solve(H: Hierarchy, b: np.ndarray, rtol: float = 1e-8, max_iter: int = 1000, mixed: bool = False) -> PCGResult:
+def solve(H: Hierarchy, b: np.ndarray, rtol: float = 1e-8, max_iter: int = 1000, mixed: bool = False,
+          two_grid: bool = False) -> PCGResult:
     """PCG on the fine system preconditioned by one V-cycle per iteration; with
     ``mixed`` the V-cycle's level 1 runs in FP32 (``vcycle_mixed``) and the PCG
-    takes the flexible beta."""
-    pre = (lambda r: vcycle_mixed(H, r)) if mixed else (lambda r: vcycle(H, r))
+    takes the flexible beta; with ``two_grid`` the preconditioner is the exact
+    two-grid P_TG (``vcycle_two_grid``)."""
+    if two_grid:
+        pre = lambda r: vcycle_two_grid(H, r)
+    else:
+        pre = (lambda r: vcycle_mixed(H, r)) if mixed else (lambda r: vcycle(H, r))
     return pcg(H.A[0], np.asarray(b, dtype=np.float64).ravel(), pre, rtol, max_iter, flexible=mixed)

@@ -171,3 +171,42 @@ def test_mixed_solve_reaches_the_tolerance():
     assert res.converged
     bm = b - b.mean()
     assert np.linalg.norm(bm - H.A[0] @ res.x) <= 2e-8 * np.linalg.norm(bm)
+
+
+# ------------------------------------------------------------------ exact two-grid P_TG (Eq. (B_TG))
+def test_two_grid_matches_closed_form():
+    # Eq. (B_TG): P_TG^{-1} = M^-T + M^-1 - M^-T A M^-1 + (I - M^-T A) Rc^T Ac^+ Rc (I - A M^-1),
+    # with Ac^+ the pseudo-inverse of the singular coarse operator, here from an SVD
+    H = make()
+    n = H.dims[0]
+    A, Ac, Rc = H.A[0].toarray(), H.A[1].toarray(), H.R[0].toarray()
+    U, sv, Vt = np.linalg.svd(Ac)
+    keep = sv > 1e-12 * sv[0]
+    Acp = (Vt[keep].T / sv[keep]) @ U[:, keep].T
+    Mi = dense_op(H.M[0].solve, n)
+    I = np.eye(n)
+    P = Mi.T + Mi - Mi.T @ A @ Mi + (I - Mi.T @ A) @ Rc.T @ Acp @ Rc @ (I - A @ Mi)
+    V = dense_op(lambda r: oracle.vcycle_two_grid(H, r), n)
+    np.testing.assert_allclose(V, P, atol=1e-9 * np.abs(P).max())
+
+
+def test_two_grid_spectrum_top_is_one():
+    # Section 4 (after Eq. (B_TG)): lambda_max(P_TG^{-1} A) = 1, and lambda_min > 0 on range(A)
+    H = make()
+    n = H.dims[0]
+    A = H.A[0].toarray()
+    V = dense_op(lambda r: oracle.vcycle_two_grid(H, r), n)
+    Q = np.linalg.qr(np.c_[np.ones(n), np.eye(n)[:, :n - 1]])[0][:, 1:]
+    Vr, Ar = Q.T @ V @ Q, Q.T @ A @ Q
+    C = np.linalg.cholesky(0.5 * (Vr + Vr.T))
+    w = np.linalg.eigvalsh(C.T @ Ar @ C)
+    assert abs(w[-1] - 1.0) < 1e-9
+    assert w[0] > 1e-6
+
+
+def test_two_grid_equals_vcycle_with_two_levels():
+    # with two levels the V-cycle's coarse step already is the exact pseudo-inverse
+    H = make(n_levels=2, L=(3,))
+    r = np.random.default_rng(2).standard_normal(H.dims[0])
+    r -= r.mean()
+    np.testing.assert_allclose(oracle.vcycle_two_grid(H, r), oracle.vcycle(H, r), rtol=1e-10, atol=1e-12)
