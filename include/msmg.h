@@ -111,6 +111,13 @@ typedef struct {
                                        /* with MSMG_BLOCK_IC0 a parent whose incomplete factor meets */
                                        /* a pivot <= 0 uses its exact block and msmg_setup returns   */
                                        /* the warning MSMG_COARSE_IC_FALLBACK                        */
+    int two_grid;                      /* 0: the V-cycle, P_ITG of Eq. (B_ITG) (default); 1: the     */
+                                       /* exact two-grid preconditioner P_TG of Eq. (B_TG): the      */
+                                       /* coarse correction solves A_2 e_c = r_c by an inner PCG on  */
+                                       /* level 2 preconditioned by the coarse cycle from level 2,    */
+                                       /* one cooperative launch per application (n_levels >= 3)    */
+    double inner_rtol;                 /* P_TG: inner relative residual (0: 1e-10)                   */
+    int inner_max_iter;                /* P_TG: inner iteration cap per application (0: 200)         */
 } msmg_options;
 
 typedef struct {
@@ -143,6 +150,7 @@ typedef struct {
     double true_rel_residual;          /* recomputed from x at exit                      */
     double rhs_mean;                   /* mean removed from the right-hand side          */
     double solve_ms;                   /* device time of the solve                       */
+    int64_t inner_iterations;          /* P_TG: inner iterations summed over the solve    */
     int64_t kernel_launches;           /* library kernels launched by the solve          */
 } msmg_solve_info;
 

@@ -53,7 +53,8 @@ class msmg_options(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("block", C.c_int * 3), ("ratio", (C.c_int * 3) * MAX_LEVELS),
                 ("n_eig", C.c_int * MAX_LEVELS), ("nu", C.c_int * MAX_LEVELS), ("precision", C.c_int),
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int), ("autotune", C.c_int),
-                ("warm_start", C.c_void_p), ("coarse_smoother", C.c_int)]
+                ("warm_start", C.c_void_p), ("coarse_smoother", C.c_int), ("two_grid", C.c_int),
+                ("inner_rtol", C.c_double), ("inner_max_iter", C.c_int)]
 
 
 class msmg_setup_info(C.Structure):
@@ -71,7 +72,7 @@ class msmg_net_desc(C.Structure):
 class msmg_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
                 ("true_rel_residual", C.c_double), ("rhs_mean", C.c_double), ("solve_ms", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("inner_iterations", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
 _lib = None
@@ -180,6 +181,9 @@ class Options:
     autotune: bool = False             # time the V-cycle variants at set-up (msmg_autotune)
     warm_start: object = None          # a WarmStartNet (or its handle) seeds the level-1 eigensolves
     coarse_smoother: int = BLOCK_CHOL  # BLOCK_CHOL (exact parent blocks) or BLOCK_IC0 (Section 5)
+    two_grid: bool = False             # exact two-grid P_TG (Eq. (B_TG)) instead of the V-cycle
+    inner_rtol: float = 0.0            # P_TG inner tolerance (0: library default 1e-10)
+    inner_max_iter: int = 0            # P_TG inner iteration cap (0: library default 200)
 
     def to_c(self) -> msmg_options:
         o = msmg_options()
@@ -201,6 +205,9 @@ class Options:
         ws = self.warm_start
         o.warm_start = (ws.handle if hasattr(ws, "handle") else ws) or None
         o.coarse_smoother = self.coarse_smoother
+        o.two_grid = 1 if self.two_grid else 0
+        o.inner_rtol = self.inner_rtol
+        o.inner_max_iter = self.inner_max_iter
         return o
 
 
@@ -251,7 +258,7 @@ def msmg_solve(ctx: int, rhs: torch.Tensor, x: torch.Tensor, rtol: float, max_it
 def _info_dict(i) -> dict:
     return dict(iterations=i.iterations, converged=bool(i.converged), rel_residual=i.rel_residual,
                 true_rel_residual=i.true_rel_residual, rhs_mean=i.rhs_mean, solve_ms=i.solve_ms,
-                kernel_launches=i.kernel_launches)
+                inner_iterations=i.inner_iterations, kernel_launches=i.kernel_launches)
 
 
 def msmg_solve_batched(ctxs: list, rhs: list, x: list, rtol: float, max_iter: int, flags: int = 0,

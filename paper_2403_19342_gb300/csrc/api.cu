@@ -63,6 +63,9 @@ int validate(const msmg_grid* g, const msmg_options* o) {
   if (o->n_levels < 2 || o->n_levels > kMaxLevels) return MSMG_ERR_INVALID_ARG;
   if (o->precision != MSMG_FP64 && o->precision != MSMG_MIXED) return MSMG_ERR_INVALID_ARG;
   if (o->coarse_smoother != MSMG_BLOCK_CHOL && o->coarse_smoother != MSMG_BLOCK_IC0) return MSMG_ERR_INVALID_ARG;
+  if (o->two_grid != 0 && o->two_grid != 1) return MSMG_ERR_INVALID_ARG;
+  if (o->two_grid && o->n_levels < 3) return MSMG_ERR_INVALID_ARG;   // two levels: the V-cycle is P_TG
+  if (!(o->inner_rtol >= 0) || o->inner_max_iter < 0) return MSMG_ERR_INVALID_ARG;
   LevelShape sh;
   int st = shapes(g, o, sh);
   if (st) return st;
@@ -93,6 +96,8 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   const int nL = o->n_levels;
   c->grid = *g;
   c->opts = *o;
+  if (c->opts.inner_rtol <= 0) c->opts.inner_rtol = 1e-10;
+  if (c->opts.inner_max_iter <= 0) c->opts.inner_max_iter = 200;
   c->nL = nL;
   c->n = (int64_t)g->nx * g->ny * g->nz;
   c->max_rhs = n_rhs < 1 ? 1 : n_rhs;
@@ -188,6 +193,15 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   B.sc = ar.take<PcgScalars>(R);
   B.dres = ar.take<double>(2 * R);
   B.dmask = ar.take<int>(R);
+  if (o->two_grid) {
+    const int64_t n2 = c->lev[2].n * R;
+    B.ix = ar.take<double>(n2);
+    B.ip0 = ar.take<double>(n2);
+    B.ip1 = ar.take<double>(n2);
+    B.iq = ar.take<double>(n2);
+    B.ipart = ar.take<double>((size_t)1024 * R * 2);
+    B.iiters = ar.take<int>(R);
+  }
   B.n_rhs = R;
   B.R = 1;
   return 0;
@@ -305,6 +319,7 @@ static int build_from_bases(msmg_ctx* c, bool given, cudaStream_t s) {
   launch_mixed_copies(c, s);
   prepare_fine_kernels(c);
   prepare_coarse_kernels(c);
+  if (c->opts.two_grid && !c->inner_grid) return MSMG_ERR_UNSUPPORTED;   // needs the cooperative form
   return 0;
 }
 
@@ -604,6 +619,7 @@ int msmg_import_bases(msmg_ctx* c, const double* const* bases, msmg_stream strea
   launch_mixed_copies(c, s);
   prepare_fine_kernels(c);
   prepare_coarse_kernels(c);
+  if (c->opts.two_grid && !c->inner_grid) return MSMG_ERR_UNSUPPORTED;
   return check_flags(c, s);
 }
 

@@ -66,8 +66,17 @@ struct LevelData {
   const S *Ad, *Ao, *Minv, *Psi;
 };
 
+// Loads of f and u: through the read-only path when they were written by an
+// earlier launch (per-level kernels), coherent when an earlier phase of the same
+// launch wrote them (the fused forms, the inner two-grid solve).
+template <bool NC, typename S>
+__device__ __forceinline__ S ld_vec(const S* p) {
+  if constexpr (NC) return __ldg(p);
+  else return *p;
+}
+
 // r_i = f_i - (A_l u)_i for the rows i of one parent's children (thread t: row t).
-template <int LT, typename S>
+template <int LT, typename S, bool NC = true>
 __device__ __forceinline__ S coarse_residual_row(const CoarseLevel& lv, const LevelData<S>& D, int64_t P, int t,
                                                  const S* __restrict__ f, const S* __restrict__ u) {
   const int L = LT ? LT : lv.L;
@@ -76,15 +85,15 @@ __device__ __forceinline__ S coarse_residual_row(const CoarseLevel& lv, const Le
   const int L2 = L * L;
   const S* ad = D.Ad + a * L2 + (size_t)k * L;
   const S* ua = u + a * L;
-  S acc = __ldg(f + a * L + k);
+  S acc = ld_vec<NC>(f + a * L + k);
   int nb[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) nb[q] = __ldg(lv.nbr + a * 6 + q);
   if (LT) {
 #pragma unroll
-    for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ad + mm) * __ldg(ua + mm);
+    for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ad + mm) * ld_vec<NC>(ua + mm);
   } else {
-    for (int mm = 0; mm < L; ++mm) acc -= __ldg(ad + mm) * __ldg(ua + mm);
+    for (int mm = 0; mm < L; ++mm) acc -= __ldg(ad + mm) * ld_vec<NC>(ua + mm);
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -94,9 +103,9 @@ __device__ __forceinline__ S coarse_residual_row(const CoarseLevel& lv, const Le
       const S* ub = u + (int64_t)bp * L;
       if (LT) {
 #pragma unroll
-        for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + mm) * __ldg(ub + mm);
+        for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + mm) * ld_vec<NC>(ub + mm);
       } else {
-        for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + mm) * __ldg(ub + mm);
+        for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + mm) * ld_vec<NC>(ub + mm);
       }
     }
     const int bm = nb[2 * d];       // -d neighbour: A_l[a, bm] = Ao[bm][d]^T
@@ -105,9 +114,9 @@ __device__ __forceinline__ S coarse_residual_row(const CoarseLevel& lv, const Le
       const S* ub = u + (int64_t)bm * L;
       if (LT) {
 #pragma unroll
-        for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + (size_t)mm * LT) * __ldg(ub + mm);
+        for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + (size_t)mm * LT) * ld_vec<NC>(ub + mm);
       } else {
-        for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + (size_t)mm * L) * __ldg(ub + mm);
+        for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + (size_t)mm * L) * ld_vec<NC>(ub + mm);
       }
     }
   }
@@ -312,18 +321,29 @@ struct GridBarrier {
   }
 };
 
+// Per right-hand-side stop flags the fused forms read: the PCG scalars' done
+// words (stride between records in ints) or any other int array.
+struct DoneFlags {
+  const int* p;
+  int stride;
+  __device__ __forceinline__ bool operator()(int r) const { return p && p[(size_t)r * stride]; }
+};
+__host__ __device__ inline DoneFlags done_of(const PcgScalars* sc) {
+  return DoneFlags{sc ? &sc->done : nullptr, (int)(sizeof(PcgScalars) / sizeof(int))};
+}
+
 // item i of the level's R * mP (right-hand side, parent) pairs
 struct TailItem {
   int r;
   int64_t P;
   bool live;
 };
-__device__ __forceinline__ TailItem tail_item(int64_t i, int64_t mP, int r0, int r1, const PcgScalars* sc) {
+__device__ __forceinline__ TailItem tail_item(int64_t i, int64_t mP, int r0, int r1, DoneFlags dn) {
   TailItem it;
   it.live = i < (int64_t)(r1 - r0) * mP;
   it.r = it.live ? r0 + (int)(i / mP) : r0;
   it.P = it.live ? i % mP : 0;
-  if (it.live && sc && sc[it.r].done) it.live = false;
+  if (it.live && dn(it.r)) it.live = false;
   return it;
 }
 
@@ -343,7 +363,7 @@ __host__ __device__ inline int tail_group_doubles(int nP, int Ln, int gw) {
 
 template <int LT, typename Bar>
 __device__ void tail_level_down(const TailArgs& A, int l, int r0, int r1, int cta, int ncta, double* sm,
-                                const PcgScalars* sc, Bar bar) {
+                                DoneFlags sc, Bar bar) {
   const CoarseLevel& lv = A.lv[l];
   const LevelData<double> D{lv.Ad, lv.Ao, lv.Minv, lv.Psi};
   const int nP = lv.nP, Ln = lv.Lnext;
@@ -375,7 +395,7 @@ __device__ void tail_level_down(const TailArgs& A, int l, int r0, int r1, int ct
     const double* f = A.f[l] + (int64_t)it.r * lv.n;
     const double* u = A.u[l] + (int64_t)it.r * lv.n;
     double* fn = A.f[l + 1] + (int64_t)it.r * lv.mP * Ln;
-    const double rt = (live && t < nP) ? coarse_residual_row<LT>(lv, D, it.P, t, f, u) : 0.0;
+    const double rt = (live && t < nP) ? coarse_residual_row<LT, double, false>(lv, D, it.P, t, f, u) : 0.0;
     double* red = fs + nP;
     for (int j = 0; j < Ln; ++j) {
       double v = (live && t < nP) ? __ldg(D.Psi + ((size_t)it.P * Ln + j) * nP + t) * rt : 0.0;
@@ -395,7 +415,7 @@ __device__ void tail_level_down(const TailArgs& A, int l, int r0, int r1, int ct
 
 template <int LT, typename Bar>
 __device__ void tail_level_up(const TailArgs& A, int l, int r0, int r1, int cta, int ncta, double* sm,
-                              const PcgScalars* sc, Bar bar) {
+                              DoneFlags sc, Bar bar) {
   const CoarseLevel& lv = A.lv[l];
   const LevelData<double> D{lv.Ad, lv.Ao, lv.Minv, lv.Psi};
   const int nP = lv.nP, Ln = lv.Lnext;
@@ -430,7 +450,7 @@ __device__ void tail_level_up(const TailArgs& A, int l, int r0, int r1, int cta,
     double* w = A.w[l] + (int64_t)it.r * lv.n;
     float* o32 = (l == 2 && A.out32) ? A.out32 + (int64_t)it.r * lv.n : nullptr;
     if (live) group_cp(Mi, D.Minv + (size_t)it.P * nP * nP, nP * nP, t, gw * 32);
-    if (live && t < nP) rs[t] = coarse_residual_row<LT>(lv, D, it.P, t, f, u);
+    if (live && t < nP) rs[t] = coarse_residual_row<LT, double, false>(lv, D, it.P, t, f, u);
     cp_wait();
     __syncthreads();
     if (live && t < nP) {
@@ -446,7 +466,7 @@ __device__ void tail_level_up(const TailArgs& A, int l, int r0, int r1, int cta,
 // coarsest: u = A^dagger f, one warp per (right-hand side, row), the same
 // arithmetic as k_dense_gemv
 template <typename Bar>
-__device__ void tail_coarsest(const TailArgs& A, int r0, int r1, int cta, int ncta, const PcgScalars* sc, Bar bar) {
+__device__ void tail_coarsest(const TailArgs& A, int r0, int r1, int cta, int ncta, DoneFlags sc, Bar bar) {
   const CoarseLevel& lc = A.lv[A.nL];
   const int64_t n = lc.n;
   const int lane = threadIdx.x & 31;
@@ -455,7 +475,7 @@ __device__ void tail_coarsest(const TailArgs& A, int r0, int r1, int cta, int nc
   for (int64_t i = (int64_t)cta * (kTailThreads / 32) + (threadIdx.x >> 5); i < items; i += nw) {
     const int r = r0 + (int)(i / n);
     const int64_t row = i % n;
-    if (sc && sc[r].done) continue;
+    if (sc(r)) continue;
     const double* x = A.f[A.nL] + (int64_t)r * n;
     double* y = A.u[A.nL] + (int64_t)r * n;
     const double* a = lc.pinv + row * n;
@@ -478,7 +498,7 @@ __device__ void tail_coarsest(const TailArgs& A, int r0, int r1, int cta, int nc
 }
 
 template <int LT, typename Bar>
-__device__ void tail_run(const TailArgs& A, int r0, int r1, int cta, int ncta, const PcgScalars* sc, Bar bar) {
+__device__ void tail_run(const TailArgs& A, int r0, int r1, int cta, int ncta, DoneFlags sc, Bar bar) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double* sm = reinterpret_cast<double*>(smraw);
   for (int l = A.l0; l < A.nL; ++l) tail_level_down<LT>(A, l, r0, r1, cta, ncta, sm, sc, bar);
@@ -492,7 +512,7 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(TailArgs A, const 
   const int ncta = (int)cg::this_cluster().num_blocks();
   const int cta = (int)cg::this_cluster().block_rank();
   const int r = (int)(blockIdx.x / (unsigned)ncta) % R;
-  tail_run<LT>(A, r, r + 1, cta, ncta, sc, ClusterBarrier{});
+  tail_run<LT>(A, r, r + 1, cta, ncta, done_of(sc), ClusterBarrier{});
 }
 
 // one cooperative grid for every right-hand side
@@ -504,7 +524,247 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_coop(TailArgs A, const 
     if (threadIdx.x == 0) atomicExch(A.err, 1);
     return;
   }
-  tail_run<LT>(A, 0, R, (int)blockIdx.x, (int)gridDim.x, sc, GridBarrier{});
+  tail_run<LT>(A, 0, R, (int)blockIdx.x, (int)gridDim.x, done_of(sc), GridBarrier{});
+}
+
+// ------------------------------------------------------------------ exact two-grid (P_TG)
+// Eq. (B_TG) puts the exact A_c^dagger where the V-cycle has the recursive
+// coarse cycle B_c^{-1} of Eq. (B_c).  A_2 e_c = r_c is solved here by PCG on
+// level 2, preconditioned by the coarse cycle from level 2 down (the device code
+// of the fused grid form), to ||r|| <= inner_rtol ||r_c||, in one cooperative
+// launch that iterates on the device until every right-hand side has converged.
+// The result is projected orthogonal to the null vector z of A_2 (the
+// minimum-norm solution, as the pseudo-inverse gives).
+//
+// Work split: CTA k owns the level-2 rows [k chunk, (k+1) chunk) of every
+// right-hand side; warp w takes the right-hand sides r = w (mod 8) and its lanes
+// the rows.  Sums: lanes -> warp shuffle -> one partial per (CTA, right-hand
+// side) -> grid barrier -> every CTA adds the partials in CTA order with the same
+// fixed tree, so all CTAs hold the same scalars and take the same decisions.
+struct InnerArgs {
+  double* x;        // [R][n2] solution of A_2 x = r_c
+  double* p0;       // [R][n2] search directions, alternating between iterations
+  double* p1;
+  double* q;        // [R][n2] A_2 p
+  double* part;     // [ncta][R][2] per-CTA partial sums
+  int* iters;       // [R] inner iterations, accumulated over the calls of a solve
+  float* out32;     // FP32 copy of the solution (mixed form) or null
+  double rtol2;
+  int max_iter;
+};
+
+// (A_2 v)_i, i = (element a, coordinate k); v(j) returns the vector's entry j
+template <int LT, typename Vf>
+__device__ __forceinline__ double coarse_apply_row(const CoarseLevel& lv, int64_t a, int k, Vf v) {
+  const int L = LT ? LT : lv.L;
+  const int L2 = L * L;
+  double acc = 0.0;
+  const double* ad = lv.Ad + a * L2 + (size_t)k * L;
+  for (int mm = 0; mm < L; ++mm) acc = fma(ad[mm], v(a * L + mm), acc);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int bp = lv.nbr[a * 6 + 2 * d + 1];
+    if (bp >= 0) {
+      const double* ao = lv.Ao + ((size_t)a * 3 + d) * L2 + (size_t)k * L;
+      for (int mm = 0; mm < L; ++mm) acc = fma(ao[mm], v((int64_t)bp * L + mm), acc);
+    }
+    const int bm = lv.nbr[a * 6 + 2 * d];
+    if (bm >= 0) {
+      const double* ao = lv.Ao + ((size_t)bm * 3 + d) * L2 + k;
+      for (int mm = 0; mm < L; ++mm) acc = fma(ao[(size_t)mm * L], v((int64_t)bm * L + mm), acc);
+    }
+  }
+  return acc;
+}
+
+// sum over the CTAs of partial ``slot`` of right-hand side r (every lane gets it)
+__device__ __forceinline__ double inner_total(const double* part, int ncta, int R, int r, int slot, int lane) {
+  double v = 0.0;
+  for (int k = lane; k < ncta; k += 32) v += __ldcg(part + ((size_t)k * R + r) * 2 + slot);
+  return warp_sum(v);
+}
+
+template <int LT>
+__global__ void __launch_bounds__(kTailThreads) k_inner_pcg(TailArgs A, InnerArgs I, const PcgScalars* osc, int R) {
+  if (!cg::this_grid().is_valid()) {   // the grid barrier needs a cooperative launch
+    if (threadIdx.x == 0) atomicExch(A.err, 1);
+    return;
+  }
+  const GridBarrier bar{};
+  const int cta = (int)blockIdx.x, ncta = (int)gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = kTailThreads / 32;
+  const CoarseLevel& lv = A.lv[2];
+  const int L = LT ? LT : lv.L;
+  const int64_t n2 = lv.n;
+  const int64_t chunk = (n2 + ncta - 1) / ncta;
+  const int64_t row0 = (int64_t)cta * chunk;
+  const int64_t row1 = row0 + chunk < n2 ? row0 + chunk : n2;
+  __shared__ int s_done[MSMG_MAX_BATCH_RHS];
+  __shared__ int s_it[MSMG_MAX_BATCH_RHS];
+  __shared__ double s_tol2[MSMG_MAX_BATCH_RHS], s_rz[MSMG_MAX_BATCH_RHS], s_beta[MSMG_MAX_BATCH_RHS],
+      s_alpha[MSMG_MAX_BATCH_RHS];
+  double* const rv = A.f[2];        // the residual, r_c on entry
+  const double* const z = A.w[2];   // the coarse cycle's output
+  // The pseudo-inverse acts on the part of r_c in the range of A_2: r_c is
+  // orthogonal to A_2's null vector z0 in exact arithmetic (z0 represents the
+  // constant), but rounding (FP32 in the mixed form) leaves a component along
+  // it, which would make the inner system inconsistent.  Remove it, set x = 0,
+  // and take ||r_c||^2.
+  for (int r = warp; r < R; r += NW) {
+    double v0 = 0.0, v1 = 0.0;
+    for (int64_t i = row0 + lane; i < row1; i += 32) {
+      const double zi = lv.z[i];
+      v0 = fma(zi, rv[(int64_t)r * n2 + i], v0);
+      v1 = fma(zi, zi, v1);
+    }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+      I.part[((size_t)cta * R + r) * 2] = v0;
+      I.part[((size_t)cta * R + r) * 2 + 1] = v1;
+    }
+  }
+  bar();
+  for (int r = warp; r < R; r += NW) {
+    const double zr = inner_total(I.part, ncta, R, r, 0, lane);
+    const double zz = inner_total(I.part, ncta, R, r, 1, lane);
+    const double cz = zz > 0.0 ? zr / zz : 0.0;
+    double v = 0.0;
+    for (int64_t i = row0 + lane; i < row1; i += 32) {
+      const double t = fma(-cz, lv.z[i], rv[(int64_t)r * n2 + i]);
+      rv[(int64_t)r * n2 + i] = t;
+      I.x[(int64_t)r * n2 + i] = 0.0;
+      v = fma(t, t, v);
+    }
+    v = warp_sum(v);
+    s_tol2[r] = v;   // this warp's own partial, written below once every CTA has read slot 0
+  }
+  bar();   // every CTA has read the null-vector sums
+  for (int r = warp; r < R; r += NW)
+    if (lane == 0) I.part[((size_t)cta * R + r) * 2] = s_tol2[r];
+  bar();
+  for (int r = warp; r < R; r += NW) {
+    const double t = inner_total(I.part, ncta, R, r, 0, lane);
+    if (lane == 0) {
+      s_done[r] = ((osc && osc[r].done) || !(t > 0.0)) ? 1 : 0;
+      s_tol2[r] = I.rtol2 * t;
+      s_rz[r] = 0.0;
+      s_it[r] = 0;
+    }
+  }
+  __syncthreads();
+  const DoneFlags dn{s_done, 1};
+  for (int it = 0; it < I.max_iter; ++it) {
+    bool any = false;
+    for (int r = 0; r < R; ++r) any |= !s_done[r];
+    if (!any) break;
+    // z = B_2^{-1} r (its grid barriers also separate the r.r reads above from
+    // the next partial sums written below): the coarse cycle from level 2 (Algorithm 1 below level 1)
+    tail_run<LT>(A, 0, R, cta, ncta, dn, bar);
+    // r.z
+    for (int r = warp; r < R; r += NW) {
+      if (s_done[r]) continue;
+      double v = 0.0;
+      for (int64_t i = row0 + lane; i < row1; i += 32) v = fma(rv[(int64_t)r * n2 + i], z[(int64_t)r * n2 + i], v);
+      v = warp_sum(v);
+      if (lane == 0) I.part[((size_t)cta * R + r) * 2] = v;
+    }
+    bar();
+    for (int r = warp; r < R; r += NW) {
+      if (s_done[r]) continue;
+      const double rz = inner_total(I.part, ncta, R, r, 0, lane);
+      if (lane == 0) {
+        s_beta[r] = (it > 0 && s_rz[r] != 0.0) ? rz / s_rz[r] : 0.0;
+        s_rz[r] = rz;
+        ++s_it[r];
+      }
+    }
+    __syncthreads();
+    // p = z + beta p_prev and q = A_2 p (neighbour entries of p formed on the fly
+    // from z and p_prev, which are complete), p.q
+    const double* pp = (it & 1) ? I.p0 : I.p1;
+    double* pc = (it & 1) ? I.p1 : I.p0;
+    for (int r = warp; r < R; r += NW) {
+      if (s_done[r]) continue;
+      const double beta = s_beta[r];
+      const int64_t off = (int64_t)r * n2;
+      auto pv = [&](int64_t j) { return it > 0 ? fma(beta, pp[off + j], z[off + j]) : z[off + j]; };
+      double v = 0.0;
+      for (int64_t i = row0 + lane; i < row1; i += 32) {
+        const double pi = pv(i);
+        const double qi = coarse_apply_row<LT>(lv, i / L, (int)(i % L), pv);
+        pc[off + i] = pi;
+        I.q[off + i] = qi;
+        v = fma(pi, qi, v);
+      }
+      v = warp_sum(v);
+      if (lane == 0) I.part[((size_t)cta * R + r) * 2 + 1] = v;
+    }
+    bar();
+    for (int r = warp; r < R; r += NW) {
+      if (s_done[r]) continue;
+      const double pq = inner_total(I.part, ncta, R, r, 1, lane);
+      if (lane == 0) {
+        const double al = s_rz[r] / pq;
+        s_alpha[r] = al;
+        if (!(pq > 0.0) || !isfinite(al)) s_done[r] = 2;   // breakdown: keep the iterate
+      }
+    }
+    __syncthreads();
+    // x += alpha p, r -= alpha q, r.r
+    for (int r = warp; r < R; r += NW) {
+      if (s_done[r]) continue;
+      const double al = s_alpha[r];
+      const int64_t off = (int64_t)r * n2;
+      double v = 0.0;
+      for (int64_t i = row0 + lane; i < row1; i += 32) {
+        I.x[off + i] = fma(al, pc[off + i], I.x[off + i]);
+        const double ri = fma(-al, I.q[off + i], rv[off + i]);
+        rv[off + i] = ri;
+        v = fma(ri, ri, v);
+      }
+      v = warp_sum(v);
+      if (lane == 0) I.part[((size_t)cta * R + r) * 2] = v;
+    }
+    bar();
+    for (int r = warp; r < R; r += NW) {
+      if (s_done[r]) continue;
+      const double rr = inner_total(I.part, ncta, R, r, 0, lane);
+      if (lane == 0 && rr <= s_tol2[r]) s_done[r] = 1;
+    }
+    __syncthreads();
+  }
+  // minimum-norm solution: x -= (z0.x / z0.z0) z0, z0 the null vector of A_2
+  bar();   // every CTA has read the last partial sums
+  for (int r = warp; r < R; r += NW) {
+    if (osc && osc[r].done) continue;
+    double v0 = 0.0, v1 = 0.0;
+    for (int64_t i = row0 + lane; i < row1; i += 32) {
+      const double zi = lv.z[i];
+      v0 = fma(zi, I.x[(int64_t)r * n2 + i], v0);
+      v1 = fma(zi, zi, v1);
+    }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+      I.part[((size_t)cta * R + r) * 2] = v0;
+      I.part[((size_t)cta * R + r) * 2 + 1] = v1;
+    }
+  }
+  bar();
+  for (int r = warp; r < R; r += NW) {
+    if (osc && osc[r].done) continue;
+    const double zx = inner_total(I.part, ncta, R, r, 0, lane);
+    const double zz = inner_total(I.part, ncta, R, r, 1, lane);
+    const double cz = zz > 0.0 ? zx / zz : 0.0;
+    for (int64_t i = row0 + lane; i < row1; i += 32) {
+      const double xi = fma(-cz, lv.z[i], I.x[(int64_t)r * n2 + i]);
+      I.x[(int64_t)r * n2 + i] = xi;
+      if (I.out32) I.out32[(int64_t)r * n2 + i] = (float)xi;
+    }
+    if (cta == 0 && lane == 0) I.iters[r] += s_it[r];
+  }
 }
 
 static inline unsigned coarse_threads(const CoarseLevel& lv) { return coarse_threads_d(lv.nP, lv.Lnext); }
@@ -554,6 +814,7 @@ static void prepare_t(msmg_ctx* c) {
 constexpr int64_t kTailMaxParents = 256;
 constexpr int64_t kTailMaxCoarsest = 1536;
 constexpr int64_t kCoopMaxCoarsest = 4096;
+constexpr int kInnerMaxCtas = 1024;   // CTAs of the exact two-grid solve (partials are sized for it)
 
 // shared memory and the common compile-time L of levels l0 .. nL-1 (0: runtime)
 static bool tail_shape(const msmg_ctx* c, int l0, int* lt_out, size_t* sm_out) {
@@ -695,11 +956,65 @@ static int launch_coop(msmg_ctx* c, int l0, PcgScalars* sc, cudaStream_t s) {
   return 0;
 }
 
+template <int LT>
+static void inner_prepare_lt(msmg_ctx* c) {
+  c->inner_grid = 0;
+  int coop = 0, dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop || nsm < 1) return;
+  cudaFuncSetAttribute(k_inner_pcg<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->coop_smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_inner_pcg<LT>, kTailThreads, c->coop_smem) !=
+          cudaSuccess || per < 1) {
+    cudaGetLastError();
+    return;
+  }
+  int g = nsm * (per < 2 ? per : 2);
+  if (g > kInnerMaxCtas) g = kInnerMaxCtas;
+  c->inner_grid = g;
+}
+
+// Exact two-grid: the level-2 solve as one cooperative launch.  Returns the
+// level-2 correction (FP64; its FP32 copy is written too in the mixed form).
+static const double* launch_inner(msmg_ctx* c, PcgScalars* sc, cudaStream_t s) {
+  TailArgs A = tail_args(c, 2);
+  A.out32 = nullptr;
+  const int R = c->sb.R;
+  InnerArgs I;
+  I.x = c->sb.ix;
+  I.p0 = c->sb.ip0;
+  I.p1 = c->sb.ip1;
+  I.q = c->sb.iq;
+  I.part = c->sb.ipart;
+  I.iters = c->sb.iiters;
+  I.out32 = c->sb.ec32;
+  I.rtol2 = c->opts.inner_rtol * c->opts.inner_rtol;
+  I.max_iter = c->opts.inner_max_iter;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)c->inner_grid);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = c->coop_smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaSuccess;
+  with_L(c->coop_lt, [&](auto LC) { e = cudaLaunchKernelEx(&cfg, k_inner_pcg<decltype(LC)::value>, A, I, (const PcgScalars*)sc, R); });
+  if (e != cudaSuccess) set_last_cuda_error(e);
+  return c->sb.ix;
+}
+
 // Shared-memory limits of the coarse kernels and the fused forms (set once per
 // context, never during capture).
 void prepare_coarse_kernels(msmg_ctx* c) {
   prepare_t<double>(c);
   tail_prepare(c);
+  c->inner_grid = 0;
+  if (c->opts.two_grid && c->nL >= 3 && c->coop_smem)
+    with_L(c->coop_lt, [&](auto LC) { inner_prepare_lt<decltype(LC)::value>(c); });
   for (int k = 0; k < 2; ++k) {
     if (c->tune_tail[k] == 3 && !(c->coop_grid && c->tail_l0)) c->tune_tail[k] = c->coop_grid ? 2 : 0;
     if (c->tune_tail[k] == 2 && !c->coop_grid) c->tune_tail[k] = c->tail_l0 ? 1 : 0;
@@ -761,7 +1076,7 @@ static const S* coarse_cycle_t(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t 
 // Returns the level-2 correction in the V-cycle precision: FP64, or its FP32
 // copy in the mixed form.
 const void* coarse_cycle(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t s) {
-  const double* e = coarse_cycle_t<double>(c, l, sc, s);
+  const double* e = (l == 2 && c->opts.two_grid) ? launch_inner(c, sc, s) : coarse_cycle_t<double>(c, l, sc, s);
   return c->sb.ec32 ? (const void*)c->sb.ec32 : (const void*)e;
 }
 

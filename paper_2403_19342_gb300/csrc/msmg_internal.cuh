@@ -157,14 +157,18 @@ struct SolveBuffers {
   float* ec32;                  // FP32 copy of the level-2 correction (mixed form), else nullptr
   // V-cycle work on every level: f (right side), u (iterate), w (scratch); level 1 in
   // the V-cycle precision, levels >= 2 in FP64
-  void* vf[kMaxLevels];
-  void* vu[kMaxLevels];
-  void* vw[kMaxLevels];
+  void* vf[kMaxLevels + 1];     // indexed by level, 1 .. n_levels
+  void* vu[kMaxLevels + 1];
+  void* vw[kMaxLevels + 1];
   PcgScalars* sc;               // [n_rhs]
   int n_rhs;                    // capacity: every vector above holds n_rhs copies
   int R;                        // right-hand sides of the batch in flight (<= n_rhs)
   double* dres;                 // [n_rhs][2] true-residual norms, mean sums
   int* dmask;                   // [n_rhs] restart mask
+  // exact two-grid (level-2 inner PCG), null otherwise: level-2 vectors x, p (two),
+  // q; per-CTA partial sums; inner iteration counts
+  double *ix, *ip0, *ip1, *iq, *ipart;
+  int* iiters;
 };
 
 }  // namespace msmg
@@ -175,7 +179,7 @@ struct msmg_ctx {
   int nL;                                       // n_levels
   int64_t n;                                    // fine cells
   msmg::FineLevel fine;
-  msmg::CoarseLevel lev[msmg::kMaxLevels];      // lev[l] for l = 2 .. nL (index by level)
+  msmg::CoarseLevel lev[msmg::kMaxLevels + 1];  // lev[l] for l = 2 .. nL (index by level)
   msmg::SolveBuffers sb;
   msmg::RedSlot red;                            // reduction scratch
   double* dtmp;                                 // setup scratch (dense coarsest work etc.)
@@ -204,6 +208,7 @@ struct msmg_ctx {
   int tail_lt;                                  // compile-time L of the tail levels (0: runtime)
   size_t tail_smem;
   int coop_grid;                                // CTAs of the cooperative coarse cycle (0: unavailable)
+  int inner_grid;                               // CTAs of the exact two-grid inner solve (0: unavailable)
   int coop_lt;
   size_t coop_smem;
 };

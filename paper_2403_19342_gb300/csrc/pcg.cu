@@ -506,6 +506,7 @@ static int begin_batch(CtxSolve& J, double rtol, int max_iter, int flags, cudaSt
   J.stage_launches = 0;
   MSMG_CUDA_TRY(cudaEventRecord(c->ev0, s));
   MSMG_CUDA_TRY(cudaMemsetAsync(c->flags + 6, 0, sizeof(int), s));
+  if (c->sb.iiters) MSMG_CUDA_TRY(cudaMemsetAsync(c->sb.iiters, 0, (size_t)J.R * sizeof(int), s));
   int st = stage_in(c, J.rhs + (int64_t)J.next * c->n, J.x + (int64_t)J.next * c->n, J.R, host, x0, s,
                     &J.stage_launches);
   if (st) return st;
@@ -532,10 +533,14 @@ static int end_batch(CtxSolve& J, int flags, cudaStream_t s, msmg_solve_info* in
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   msmg_solve_info* I = info ? info + J.next : nullptr;
   const int res = J.run.finish(I);
+  int inner[MSMG_MAX_BATCH_RHS] = {};
+  if (I && c->sb.iiters)
+    MSMG_CUDA_TRY(cudaMemcpy(inner, c->sb.iiters, (size_t)J.R * sizeof(int), cudaMemcpyDeviceToHost));
   if (I)
     for (int r = 0; r < J.R; ++r) {
       I[r].kernel_launches += J.stage_launches;
       I[r].solve_ms = ms;
+      I[r].inner_iterations = inner[r];
     }
   if (res < 0) return res;
   if (res > J.worst) J.worst = res;
