@@ -34,14 +34,16 @@ the paper prints, to library routines on special cases and to brute force.
 """
 from .tpfa import (as_components, normalized_permeability, trace_weight,
                    face_transmissibilities, assemble, apply_A, interior_face_mask, velocity, divergence)
-from .spectral import element_cells, level1_eigenpairs, coarse_eigenpairs
-from .hierarchy import Options, Hierarchy, setup, BlockIC0, BlockIC0Dense, ic0_dense, sibling_pattern
+from .spectral import element_cells, level1_eigenpairs, coarse_eigenpairs, coarse_eigenpairs_kept
+from .hierarchy import (Options, Hierarchy, setup, BlockIC0, BlockIC0Dense, ic0_dense, sibling_pattern,
+                        kept_count, ragged_pattern)
 from .solver import vcycle, vcycle_mixed, vcycle_two_grid, coarse_pinv, pcg, solve, PCGResult
 
 __all__ = [
     "as_components", "normalized_permeability", "trace_weight",
     "face_transmissibilities", "assemble", "apply_A", "interior_face_mask", "velocity", "divergence",
-    "element_cells", "level1_eigenpairs", "coarse_eigenpairs",
+    "element_cells", "level1_eigenpairs", "coarse_eigenpairs", "coarse_eigenpairs_kept",
     "Options", "Hierarchy", "setup", "BlockIC0", "BlockIC0Dense", "ic0_dense", "sibling_pattern",
+    "kept_count", "ragged_pattern",
     "vcycle", "vcycle_mixed", "vcycle_two_grid", "coarse_pinv", "pcg", "solve", "PCGResult",
 ]

@@ -31,7 +31,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from .tpfa import (assemble, face_transmissibilities, interior_face_mask, trace_weight)
-from .spectral import coarse_eigenpairs, element_cells, level1_eigenpairs
+from .spectral import coarse_eigenpairs, coarse_eigenpairs_kept, element_cells, level1_eigenpairs
 
 
 @dataclass
@@ -44,6 +44,14 @@ class Options:
     n_eig: list = field(default_factory=lambda: [4, 4])       # L_1 .. L_{n_levels-1}
     nu: list = field(default_factory=lambda: [1, 1])          # sweeps on levels 1 .. n_levels-1
     coarse_smoother: str = "chol"            # "chol" (exact block Cholesky) or "ic0"
+    # Strategy 2 of Section 5: eig_threshold[l-1] > 0 keeps, on every element of E_l, the
+    # candidate eigenvectors (n_eig[l-1] of them) whose eigenvalues lie below the threshold
+    # (B_c, B_cc), at least one; 0 (or a short list) keeps all n_eig[l-1] (Strategy 1)
+    eig_threshold: list = field(default_factory=list)
+
+    def threshold(self, l: int) -> float:
+        """B for the local problems on the elements of E_l (0: Strategy 1)."""
+        return float(self.eig_threshold[l - 1]) if l - 1 < len(self.eig_threshold) else 0.0
 
     def check(self):
         if self.n_levels < 2:
@@ -152,6 +160,28 @@ class BlockCholesky:
         return out
 
 
+def kept_count(lam_candidates: np.ndarray, B: float) -> int:
+    """Number of local eigenvectors kept (Section 5): all candidates under
+    Strategy 1 (B = 0); under Strategy 2 those with eigenvalue below B, at
+    least one (the constant, eigenvalue 0, is always among them)."""
+    if B <= 0:
+        return int(len(lam_candidates))
+    return max(1, int(np.count_nonzero(np.asarray(lam_candidates) < B)))
+
+
+def ragged_pattern(ratio, counts_children) -> np.ndarray:
+    """sibling_pattern for children carrying different numbers of coordinates
+    (Strategy 2): the dofs of child a and child b couple when a == b or the
+    two share a face."""
+    rx, ry, rz = ratio
+    nch = rx * ry * rz
+    cz, cy, cx = np.unravel_index(np.arange(nch), (rz, ry, rx))
+    owner = np.repeat(np.arange(nch), counts_children)
+    dist = np.abs(cx[owner][:, None] - cx[owner][None, :]) + np.abs(cy[owner][:, None] - cy[owner][None, :]) \
+        + np.abs(cz[owner][:, None] - cz[owner][None, :])
+    return dist <= 1
+
+
 def ic0_dense(blk: np.ndarray, pat: np.ndarray) -> np.ndarray:
     """Incomplete Cholesky with no fill of one dense symmetric block: the
     right-looking Cholesky factorisation in which every update that would land
@@ -206,7 +236,10 @@ class BlockIC0Dense:
         for P, idx in enumerate(dofs):
             blk = A[idx][:, idx].toarray()
             blk = 0.5 * (blk + blk.T)
-            pat = pattern if pattern is not None else blk != 0.0
+            if pattern is None:
+                pat = blk != 0.0
+            else:
+                pat = pattern[P] if isinstance(pattern, list) else pattern
             try:
                 W = ic0_dense(blk, pat)
             except FloatingPointError:
@@ -238,6 +271,7 @@ class Hierarchy:
     parent_dofs: list                    # parent_dofs[l-1] (m_l, nP) for l >= 2; None for l = 1
     coarsest_pinv: np.ndarray            # dense A_L^dagger
     null_vectors: list                   # null vector of A_l in level-l coordinates
+    counts: list = field(default_factory=list)  # counts[l-1][e]: vectors kept on element e of E_l
 
     @property
     def dims(self):
@@ -254,16 +288,23 @@ def setup(kappa, h, opts: Options) -> Hierarchy:
     A1 = assemble(T)
     nL = opts.n_levels
 
-    # level 1 -> 2: Eq. (spepb) on the elements of E_1
+    # level 1 -> 2: Eq. (spepb) on the elements of E_1; the candidates' unused slots
+    # (Strategy 2) are zero rows of the padded basis array and no rows of R_1
     lam1, Phi, cells = level1_eigenpairs(T, S, opts.block, opts.n_eig[0])
     m1, L1, nb = Phi.shape
-    rows = (np.arange(m1)[:, None] * L1 + np.arange(L1)[None, :]).repeat(nb, axis=1).ravel()
-    cols = np.repeat(cells[:, None, :], L1, axis=1).ravel()
-    R1 = sp.csr_matrix((Phi.ravel(), (rows, cols)), shape=(m1 * L1, A1.shape[0]))
+    cnt = np.array([kept_count(lam1[e], opts.threshold(1)) for e in range(m1)])
+    keep = np.arange(L1)[None, :] < cnt[:, None]
+    Phi = np.where(keep[:, :, None], Phi, 0.0)
+    off = np.concatenate([[0], np.cumsum(cnt)])
+    row_of = off[:-1, None] + np.arange(L1)[None, :]
+    rows = np.repeat(row_of[keep][:, None], nb, axis=1).ravel()
+    cols = cells[np.nonzero(keep)[0]].ravel()
+    R1 = sp.csr_matrix((Phi[keep].ravel(), (rows, cols)), shape=(int(off[-1]), A1.shape[0]))
     A = [A1, (R1 @ A1 @ R1.T).tocsr()]
     R = [R1]
     lam = [lam1]
     basis = [Phi]
+    counts = [cnt]
     grids = [(shape[0] // opts.block[2], shape[1] // opts.block[1], shape[2] // opts.block[0])]
     parent_dofs = [None]
     B = R1.T.tocsr()                          # composed basis of W_2 in fine coordinates
@@ -279,19 +320,36 @@ def setup(kappa, h, opts: Options) -> Hierarchy:
             raise ValueError("ratio does not divide the element grid")
         children = element_cells(g, r)         # (mP, r^3) indices into E_{l-1}
         Lprev = basis[-1].shape[1]
-        pd = (children[:, :, None] * Lprev + np.arange(Lprev)[None, None, :]).reshape(children.shape[0], -1)
+        cprev = counts[-1]                     # coordinates carried by each element of E_{l-1}
+        oprev = np.concatenate([[0], np.cumsum(cprev)])
+        pd = [np.concatenate([oprev[c] + np.arange(cprev[c]) for c in ch]) for ch in children]
+        if np.all(cprev == Lprev):
+            pd = np.array(pd)
         fine_box = [fine_box[d] * r[d] for d in range(3)]
         An = assemble(T * interior_face_mask(shape, fine_box))
         An_coarse = (B.T @ An @ B).tocsr()
-        lamP, Psi = coarse_eigenpairs(An_coarse, pd, opts.n_eig[l - 1])
-        mP, Ll, nP = Psi.shape
-        rows = (np.arange(mP)[:, None] * Ll + np.arange(Ll)[None, :]).repeat(nP, axis=1).ravel()
-        cols = np.repeat(pd[:, None, :], Ll, axis=1).ravel()
-        Rl = sp.csr_matrix((Psi.ravel(), (rows, cols)), shape=(mP * Ll, A[-1].shape[0]))
+        Ll = opts.n_eig[l - 1]
+        lam_c, vecs = coarse_eigenpairs_kept(An_coarse, list(pd), Ll, opts.threshold(l))
+        mP, nch = children.shape
+        cnt = np.array([v.shape[0] for v in vecs])
+        off = np.concatenate([[0], np.cumsum(cnt)])
+        rows = np.concatenate([np.repeat(off[P] + np.arange(cnt[P]), len(pd[P])) for P in range(mP)])
+        cols = np.concatenate([np.tile(pd[P], cnt[P]) for P in range(mP)])
+        vals = np.concatenate([vecs[P].ravel() for P in range(mP)])
+        Rl = sp.csr_matrix((vals, (rows, cols)), shape=(int(off[-1]), A[-1].shape[0]))
+        # padded arrays (the layout of the library's exports): slot ci * Lprev + k of a
+        # parent holds coordinate k of its child ci; unused slots and rows are zero
+        Psi = np.zeros((mP, Ll, nch * Lprev))
+        lamP = np.full((mP, Ll), np.inf)
+        for P in range(mP):
+            slots = np.concatenate([ci * Lprev + np.arange(cprev[c]) for ci, c in enumerate(children[P])])
+            Psi[P, :cnt[P]][:, slots] = vecs[P]
+            lamP[P, :len(lam_c[P])] = lam_c[P]
         A.append((Rl @ A[-1] @ Rl.T).tocsr())
         R.append(Rl)
         lam.append(lamP)
         basis.append(Psi)
+        counts.append(cnt)
         grids.append((g[0] // r[2], g[1] // r[1], g[2] // r[0]))
         parent_dofs.append(pd)
         B = (B @ Rl.T).tocsr()
@@ -309,12 +367,16 @@ def setup(kappa, h, opts: Options) -> Hierarchy:
         pd = parent_dofs[l - 1]
         if opts.coarse_smoother == "chol":
             M.append(BlockCholesky(A[l - 1], pd))
-        else:
+        elif isinstance(pd, np.ndarray):
             M.append(BlockIC0Dense(A[l - 1], pd, sibling_pattern(opts.ratio[l - 2], basis[l - 2].shape[1])))
+        else:
+            ch = element_cells(grids[l - 2], opts.ratio[l - 2])
+            pats = [ragged_pattern(opts.ratio[l - 2], counts[l - 2][c]) for c in ch]
+            M.append(BlockIC0Dense(A[l - 1], pd, pats))
 
     # coarsest: Moore-Penrose pseudo-inverse (Algorithm 1, A_cc^dagger)
     Ac = A[-1].toarray()
     Ac = 0.5 * (Ac + Ac.T)
     pinv = np.linalg.pinv(Ac, rcond=1e-13, hermitian=True)
     return Hierarchy(opts, tuple(shape), tuple(h), T, S, A, R, M, lam, basis, grids,
-                     parent_dofs, pinv, z)
+                     parent_dofs, pinv, z, counts)

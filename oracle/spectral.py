@@ -88,3 +88,25 @@ def coarse_eigenpairs(An_coarse: sp.spmatrix, parent_dofs: np.ndarray, L: int):
         lam[P] = w[:L]
         Psi[P] = V[:, :L].T
     return lam, Psi
+
+
+def coarse_eigenpairs_kept(An_coarse: sp.spmatrix, parent_dofs: list, L: int, B: float):
+    """Eq. (spectral cc) on every level-l element whose coordinates
+    ``parent_dofs[P]`` may differ in number (Strategy 2 below), with the
+    selection of Section 5: the ``L`` smallest eigenpairs are the candidates
+    (fewer if the local space is smaller), of which Strategy 1 (B = 0) keeps
+    all and Strategy 2 keeps those with eigenvalue below B, at least one.
+    Returns (lam [mP] arrays of the candidates' eigenvalues, vecs [mP] arrays
+    (kept, len(parent_dofs[P])) of the kept eigenvectors as rows)."""
+    from .hierarchy import kept_count
+    An_coarse = sp.csr_matrix(An_coarse)
+    lam, vecs = [], []
+    for idx in parent_dofs:
+        N = An_coarse[idx][:, idx].toarray()
+        N = 0.5 * (N + N.T)
+        w, V = np.linalg.eigh(N)
+        nc = min(L, len(idx))
+        c = kept_count(w[:nc], B)
+        lam.append(w[:nc])
+        vecs.append(V[:, :c].T)
+    return lam, vecs

@@ -312,3 +312,95 @@ def test_sibling_pattern():
     assert (P == P.T).all() and P.sum() == 8 * 4
     P3 = oracle.sibling_pattern((2, 1, 1), 3)
     assert P3.shape == (6, 6) and P3.all()
+
+
+# ------------------------------------------------------------------ Strategy 2 (Section 5: thresholds B_c, B_cc)
+def _inertia_below(Am: np.ndarray, Sm: np.ndarray, B: float) -> int:
+    """Eigenvalues of A x = lambda S x below B, by Sylvester's law of inertia: the
+    negative eigenvalues of D in the LDL^T factorisation of A - B S."""
+    import scipy.linalg as sla
+    _, D, _ = sla.ldl(Am - B * Sm, lower=True)
+    return int(np.count_nonzero(np.linalg.eigvalsh(D) < 0))
+
+
+def _strategy2(B1, B2, n_levels=3, shape=(8, 8, 16), L=(6, 8), seed=3, sigma=2.0):
+    rng = np.random.default_rng(seed)
+    kap = np.exp(rng.normal(0, sigma, size=shape))
+    h = (1.0 / shape[2], 1.0 / shape[1], 1.0 / shape[0])
+    opts = oracle.Options(n_levels=n_levels, block=(2, 2, 2), ratio=[(2, 2, 2)] * (n_levels - 2), n_eig=list(L),
+                          nu=[1] * (n_levels - 1), eig_threshold=[B1, B2][:n_levels - 1])
+    return oracle.setup(kap, h, opts)
+
+
+def test_strategy2_level1_counts_by_inertia():
+    B = 0.35
+    H = _strategy2(B, 0.0)
+    An = oracle.assemble(H.T * oracle.interior_face_mask(H.shape, (2, 2, 2))).tocsr()
+    cells = oracle.element_cells(H.shape, (2, 2, 2))
+    s = H.S.ravel()
+    for e in range(cells.shape[0]):
+        idx = cells[e]
+        c = _inertia_below(An[idx][:, idx].toarray(), np.diag(s[idx]), B)
+        assert H.counts[0][e] == min(max(c, 1), 6)
+        assert np.all(H.basis[0][e, H.counts[0][e]:] == 0.0)
+    assert H.dims[1] == H.counts[0].sum()
+    assert 1 < H.counts[0].min() < H.counts[0].max() <= 6         # ragged in this field
+
+
+def test_strategy2_homogeneous_ladder():
+    # kappa = 1 on 4^3 elements of a 8^3 grid: the local spectrum is the ladder of Section 5.2,
+    # lambda = (1/3) sum_d 2 (1 - cos(pi k_d / 4)) / ... ; the first distinct values have
+    # multiplicities 1, 3, 3, 1: a threshold between the 2nd and 3rd distinct value keeps 4
+    shape = (8, 8, 8)
+    h = (1 / 8,) * 3
+    lam_all, _, _ = oracle.level1_eigenpairs(oracle.face_transmissibilities(np.ones(shape), h),
+                                             oracle.trace_weight(np.ones(shape), h), (4, 4, 4), 12)
+    d = np.unique(np.round(lam_all[0], 10))
+    for B, expect in (((d[1] + d[2]) / 2, 4), ((d[2] + d[3]) / 2, 7), ((d[3] + d[4]) / 2, 8)):
+        opts = oracle.Options(n_levels=2, block=(4, 4, 4), ratio=[], n_eig=[12], nu=[1], eig_threshold=[B])
+        H = oracle.setup(np.ones(shape), h, opts)
+        assert list(H.counts[0]) == [expect] * 8
+
+
+def test_strategy2_huge_threshold_is_strategy1():
+    # Table (second approach), last row: B = 1e12 keeps every candidate
+    H2 = _strategy2(1e12, 1e12)
+    H1 = _strategy2(0.0, 0.0)
+    assert H2.dims == H1.dims
+    for l in range(3):
+        assert abs(H2.A[l] - H1.A[l]).max() == 0.0
+
+
+@pytest.mark.parametrize("n_levels", [3, 4])
+def test_strategy2_ragged_hierarchy_invariants(n_levels):
+    H = _strategy2(0.35, 0.05, n_levels=n_levels, shape=(8, 16, 16) if n_levels == 4 else (8, 8, 16),
+                   L=(6, 8, 4) if n_levels == 4 else (6, 8))
+    n = H.dims[0]
+    # W_{l+1} coordinates: one per kept vector; Psi rows orthonormal (Eq. (spectral cc), right matrix I)
+    for l in range(2, n_levels):
+        assert H.dims[l] == H.counts[l - 1].sum()
+        Rl = H.R[l - 1].toarray()
+        np.testing.assert_allclose(Rl @ Rl.T, np.eye(Rl.shape[0]), atol=1e-12)
+    assert len(set(H.counts[1].tolist())) > 1                    # the level-2 spaces are ragged
+    # the composed basis is S-orthonormal and the constant stays in every space
+    Bc = np.eye(n)
+    for Rm in H.R:
+        Bc = Bc @ Rm.T.toarray()
+    np.testing.assert_allclose(Bc.T @ (H.S.ravel()[:, None] * Bc), np.eye(Bc.shape[1]), atol=1e-10)
+    for l in range(1, n_levels):
+        np.testing.assert_allclose(H.A[l] @ H.null_vectors[l], 0.0, atol=1e-9 * abs(H.A[l]).max())
+    # the preconditioner keeps its spectrum in (0, 1] on range(A) (Section 4)
+    A = H.A[0].toarray()
+    V = np.column_stack([oracle.vcycle(H, np.eye(n)[:, j]) for j in range(n)])
+    Q = np.linalg.qr(np.c_[np.ones(n), np.eye(n)[:, :n - 1]])[0][:, 1:]
+    Vr, Ar = Q.T @ V @ Q, Q.T @ A @ Q
+    C = np.linalg.cholesky(0.5 * (Vr + Vr.T))
+    w = np.linalg.eigvalsh(C.T @ Ar @ C)
+    assert w[-1] <= 1.0 + 1e-9 and w[0] > 1e-6
+
+
+def test_ragged_pattern_uniform_equals_sibling_pattern():
+    P = oracle.ragged_pattern((2, 2, 2), np.full(8, 3))
+    assert (P == oracle.sibling_pattern((2, 2, 2), 3)).all()
+    Q = oracle.ragged_pattern((2, 1, 1), np.array([1, 2]))
+    assert Q.shape == (3, 3) and Q.all()
