@@ -118,11 +118,20 @@ typedef struct {
                                        /* one cooperative launch per application (n_levels >= 3)    */
     double inner_rtol;                 /* P_TG: inner relative residual (0: 1e-10)                   */
     int inner_max_iter;                /* P_TG: inner iteration cap per application (0: 200)         */
+    double eig_threshold[MSMG_MAX_LEVELS]; /* Strategy 2 (Section 5): eig_threshold[i] > 0 keeps, on   */
+                                       /* every element of level i+1, the candidate eigenvectors     */
+                                       /* (n_eig[i] of them) with eigenvalue below it, at least one  */
+                                       /* (B_c for i = 0, B_cc beyond); 0 keeps all n_eig[i]          */
+                                       /* (Strategy 1).  The arrays keep n_eig[i] slots per element: */
+                                       /* an unused slot holds a zero basis vector and, one level     */
+                                       /* up, a decoupled unknown that stays zero                     */
 } msmg_options;
 
 typedef struct {
     int n_levels;
     int64_t dims[MSMG_MAX_LEVELS];     /* dim W_l, l = 1 .. n_levels                     */
+    int64_t dims_kept[MSMG_MAX_LEVELS];/* dim W_l counting the kept vectors only (Strategy */
+                                       /* 2); equal to dims under Strategy 1             */
     int64_t elements[MSMG_MAX_LEVELS]; /* number of elements of E_l, l = 1 .. n_levels-1 */
     double setup_ms;                   /* device time of msmg_setup                      */
     double eig_ms;                     /* of which level-1 eigensolves                   */

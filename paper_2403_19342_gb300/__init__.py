@@ -54,11 +54,13 @@ class msmg_options(C.Structure):
                 ("n_eig", C.c_int * MAX_LEVELS), ("nu", C.c_int * MAX_LEVELS), ("precision", C.c_int),
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int), ("autotune", C.c_int),
                 ("warm_start", C.c_void_p), ("coarse_smoother", C.c_int), ("two_grid", C.c_int),
-                ("inner_rtol", C.c_double), ("inner_max_iter", C.c_int)]
+                ("inner_rtol", C.c_double), ("inner_max_iter", C.c_int),
+                ("eig_threshold", C.c_double * MAX_LEVELS)]
 
 
 class msmg_setup_info(C.Structure):
-    _fields_ = [("n_levels", C.c_int), ("dims", C.c_int64 * MAX_LEVELS), ("elements", C.c_int64 * MAX_LEVELS),
+    _fields_ = [("n_levels", C.c_int), ("dims", C.c_int64 * MAX_LEVELS),
+                ("dims_kept", C.c_int64 * MAX_LEVELS), ("elements", C.c_int64 * MAX_LEVELS),
                 ("setup_ms", C.c_double), ("eig_ms", C.c_double), ("eig_iterations_max", C.c_int),
                 ("eig_iterations_total", C.c_int64), ("warm_started", C.c_int), ("face_contrast", C.c_double),
                 ("tuning", C.c_int * 4),
@@ -184,6 +186,7 @@ class Options:
     two_grid: bool = False             # exact two-grid P_TG (Eq. (B_TG)) instead of the V-cycle
     inner_rtol: float = 0.0            # P_TG inner tolerance (0: library default 1e-10)
     inner_max_iter: int = 0            # P_TG inner iteration cap (0: library default 200)
+    eig_threshold: list = field(default_factory=list)   # Strategy 2: B per level (0: keep n_eig)
 
     def to_c(self) -> msmg_options:
         o = msmg_options()
@@ -208,6 +211,8 @@ class Options:
         o.two_grid = 1 if self.two_grid else 0
         o.inner_rtol = self.inner_rtol
         o.inner_max_iter = self.inner_max_iter
+        for i, v in enumerate(self.eig_threshold[:MAX_LEVELS]):
+            o.eig_threshold[i] = v
         return o
 
 
@@ -390,7 +395,8 @@ def msmg_get_setup_info(ctx: int) -> dict:
     i = msmg_setup_info()
     _check(load_library().msmg_get_setup_info(ctx, C.byref(i)))
     nL = i.n_levels
-    return dict(n_levels=nL, dims=list(i.dims[:nL]), elements=list(i.elements[:nL - 1]), setup_ms=i.setup_ms,
+    return dict(n_levels=nL, dims=list(i.dims[:nL]), dims_kept=list(i.dims_kept[:nL]),
+                elements=list(i.elements[:nL - 1]), setup_ms=i.setup_ms,
                 eig_ms=i.eig_ms, eig_iterations_max=i.eig_iterations_max,
                 eig_iterations_total=i.eig_iterations_total, warm_started=bool(i.warm_started),
                 tuning=list(i.tuning), face_contrast=i.face_contrast,

@@ -12,6 +12,7 @@ static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
 void launch_mixed_copies(msmg_ctx* c, cudaStream_t s);
+void launch_kept_sums(msmg_ctx* c, cudaStream_t s);
 void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s);
 int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess, float* block);
 int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream_t s);
@@ -66,6 +67,8 @@ int validate(const msmg_grid* g, const msmg_options* o) {
   if (o->two_grid != 0 && o->two_grid != 1) return MSMG_ERR_INVALID_ARG;
   if (o->two_grid && o->n_levels < 3) return MSMG_ERR_INVALID_ARG;   // two levels: the V-cycle is P_TG
   if (!(o->inner_rtol >= 0) || o->inner_max_iter < 0) return MSMG_ERR_INVALID_ARG;
+  for (int l = 0; l < o->n_levels - 1; ++l)
+    if (!(o->eig_threshold[l] >= 0) || !(o->eig_threshold[l] < 1e300)) return MSMG_ERR_INVALID_ARG;
   LevelShape sh;
   int st = shapes(g, o, sh);
   if (st) return st;
@@ -131,6 +134,7 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   const int64_t nc = c->lev[nL].n;
   // common
   c->flags = ar.take<int>(16);
+  c->kept = ar.take<unsigned long long>(kMaxLevels + 1);
   c->dtmp = ar.take<double>(16 + nc * nc + 3 * nc + 64);
   // every reducing kernel launches at most one CTA per element and right-hand
   // side, or 1216 CTAs per right-hand side for the grid-stride vector kernels
@@ -163,6 +167,7 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
     lv.Ao = ar.take<double>(lv.me * 3 * L2);
     lv.F = ar.take<double>(lv.me * 6 * L2);
     lv.z = ar.take<double>(lv.n);
+    lv.cnt = ar.take<int>(lv.me);
     if (l < nL) {
       lv.Minv = ar.take<double>(lv.mP * lv.nP * lv.nP);
       lv.Psi = ar.take<double>(lv.mP * lv.Lnext * lv.nP);
@@ -258,6 +263,14 @@ static int check_flags(msmg_ctx* c, cudaStream_t s) {
   MSMG_CUDA_TRY(cudaGetLastError());
   if (h[0]) return MSMG_ERR_BAD_KAPPA;
   if (h[1] || d[1] != 0.0) return MSMG_ERR_NOT_FACTORIZABLE;
+  {
+    unsigned long long k[kMaxLevels + 1] = {};
+    launch_kept_sums(c, s);
+    MSMG_CUDA_TRY(cudaMemcpyAsync(k, c->kept, sizeof(k), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+    c->info.dims_kept[0] = c->n;
+    for (int l = 2; l <= c->nL; ++l) c->info.dims_kept[l - 1] = (int64_t)k[l];
+  }
   c->info.eig_residual_max = d[0];
   c->info.face_contrast = d[2] * d[3];
   c->info.eig_iterations_max = h[3];
@@ -309,7 +322,7 @@ static int autotune(msmg_ctx* c, int R, int reps, cudaStream_t s) {
 // Everything that depends on the bases: Galerkin operators, coarse smoothers,
 // coarsest pseudo-inverse, reduced-precision copies.
 static int build_from_bases(msmg_ctx* c, bool given, cudaStream_t s) {
-  launch_level1_galerkin(c, s);
+  launch_level1_galerkin(c, s, !given);
   for (int l = 2; l <= c->nL - 1; ++l) {
     int st = given ? launch_coarse_setup_given(c, l, s) : launch_coarse_setup(c, l, s);
     if (st) return st;
@@ -609,7 +622,7 @@ int msmg_import_bases(msmg_ctx* c, const double* const* bases, msmg_stream strea
   }
   MSMG_CUDA_TRY(cudaMemsetAsync(c->dtmp, 0, 16 * sizeof(double), s));
   // level-by-level: each level's operator is needed before the next level's set-up
-  launch_level1_galerkin(c, s);
+  launch_level1_galerkin(c, s, false);
   for (int l = 2; l <= c->nL - 1; ++l) {
     int st = launch_coarse_setup_given(c, l, s);
     if (st) return st;

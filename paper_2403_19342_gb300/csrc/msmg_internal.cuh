@@ -137,6 +137,9 @@ struct CoarseLevel {            // level l >= 2 (W_l)
   double* Ao;                   // [me][3][L][L] A_l[a, a+e_d], d = x, y, z
   double* F;                    // [me][6][L][L] face terms (setup only)
   double* z;                    // [n] null vector of A_l
+  int* cnt;                     // [me] coordinates each element keeps (Strategy 2; L otherwise):
+                                //      slots k >= cnt are decoupled unit-diagonal unknowns that
+                                //      stay zero (their basis rows one level down are zero)
   // smoother / restriction towards level l+1 (absent at the coarsest level)
   int rx, ry, rz, nchild;       // children per parent (ratio of E_l over E_{l-1})
   int64_t mP;                   // parents (elements of E_l)
@@ -209,6 +212,7 @@ struct msmg_ctx {
   size_t tail_smem;
   int coop_grid;                                // CTAs of the cooperative coarse cycle (0: unavailable)
   int inner_grid;                               // CTAs of the exact two-grid inner solve (0: unavailable)
+  unsigned long long* kept;                     // [kMaxLevels + 1] sum of cnt per level (device)
   int coop_lt;
   size_t coop_smem;
 };
@@ -229,7 +233,7 @@ void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s, int 
 
 // ---------------------------------------------------------------- setup
 int launch_level1_eigen(msmg_ctx* c, cudaStream_t s);
-void launch_level1_galerkin(msmg_ctx* c, cudaStream_t s);
+void launch_level1_galerkin(msmg_ctx* c, cudaStream_t s, bool threshold);
 int launch_coarse_setup(msmg_ctx* c, int l, cudaStream_t s);
 int launch_coarsest(msmg_ctx* c, cudaStream_t s);
 void launch_basis_export(msmg_ctx* c, int level, double* basis, double* lam, bool import, cudaStream_t s);

@@ -89,13 +89,50 @@ __global__ void k_eig_l1_jacobi(const double* __restrict__ T, const double* __re
   if (threadIdx.x == 0) atomic_max_pos(&stats[0], res);
 }
 
+// ------------------------------------------------------------------ level-1 counts (Strategy 2)
+// With a threshold B > 0 (B_c, Section 5) each element keeps its candidates with
+// eigenvalue below B, at least one (the candidates come in ascending order), and
+// the other slots become zero rows of Phi.  The count is then the number of
+// leading nonzero rows (which also reads the counts of imported bases).  One
+// warp per element.
+__global__ void k_level1_counts(double* __restrict__ Phi, const double* __restrict__ lam, int64_t m, int L, int nb,
+                                double B, int* __restrict__ cnt) {
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (e >= m) return;
+  double* Pe = Phi + e * (int64_t)L * nb;
+  if (B > 0.0) {
+    int c = 0;
+    for (int k = 0; k < L; ++k) c += lam[e * L + k] < B ? 1 : 0;
+    if (c < 1) c = 1;
+    for (int idx = c * nb + lane; idx < L * nb; idx += 32) Pe[idx] = 0.0;
+    __syncwarp();
+  }
+  int last = 0;
+  for (int k = 0; k < L; ++k) {
+    bool nz = false;
+    for (int i = lane; i < nb; i += 32) nz |= Pe[k * nb + i] != 0.0;
+    if (__any_sync(0xffffffffu, nz)) last = k + 1;
+  }
+  if (lane == 0) cnt[e] = last;
+}
+
+__global__ void k_kept_sum(const int* __restrict__ cnt, int64_t m, unsigned long long* out) {
+  unsigned long long v = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    v += (unsigned long long)cnt[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
 // ------------------------------------------------------------------ level 1 Galerkin
 // One CTA per element a.  Outputs: Ad[a] = Phi_a^T A_aa Phi_a, Ao[a][d] = A_2[a, a+e_d],
 // F[a][f] = Phi_a^T diag(T on face f) Phi_a, z[a] = Phi_a^T S 1.
 __global__ void k_galerkin1(const double* __restrict__ T, const double* __restrict__ S, int64_t n, int bx, int by,
                             int bz, int64_t m, const int* __restrict__ nbr, int L, const double* __restrict__ Phi,
                             double* __restrict__ Ad, double* __restrict__ Ao, double* __restrict__ F,
-                            double* __restrict__ z) {
+                            double* __restrict__ z, const int* __restrict__ cnt) {
   extern __shared__ double sm[];
   const int nb = bx * by * bz;
   double* Ph = sm;            // [L][nb]
@@ -139,7 +176,8 @@ __global__ void k_galerkin1(const double* __restrict__ T, const double* __restri
       if (k > mm) continue;
       double acc = 0.0, acc2 = 0.0;
       for (int c = 0; c < nb; ++c) { acc += Ph[k * nb + c] * W[mm * nb + c]; acc2 += Ph[mm * nb + c] * W[k * nb + c]; }
-      const double v = 0.5 * (acc + acc2);
+      double v = 0.5 * (acc + acc2);
+      if (k == mm && k >= cnt[a]) v = 1.0;   // unused slot (Strategy 2): a decoupled unknown
       Ad[a * L2 + k * L + mm] = v;
       Ad[a * L2 + mm * L + k] = v;
     } else if (o < 7 * L2) {
@@ -227,7 +265,14 @@ __device__ bool ic0_factor(const double* A, double* Lf, int nP, int L, int rx, i
 }
 
 // One CTA per parent P of level l.  nP <= 96.
-__global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, int given, int ic0) {
+//
+// Strategy 2 (Section 5): a child's unused slots (k >= lv.cnt[child]) are
+// decoupled unit-diagonal unknowns; the local eigenproblem is posed on the kept
+// coordinates only (compacted), and with a threshold B > 0 (B_cc) the parent
+// keeps its candidates with eigenvalue below B, at least one; its other rows of
+// Psi are zero and its count goes to nx.cnt.  With given (imported) bases the
+// count is the number of leading nonzero rows of Psi.
+__global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, int given, int ic0, double B) {
   extern __shared__ double sm[];
   const int nP = lv.nP, L = lv.L, L2 = L * L, Ln = lv.Lnext, Ln2 = Ln * Ln;
   double* A = sm;                 // parent's diagonal block of A_l
@@ -237,6 +282,9 @@ __global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, in
   double* red = cs + nP + 2;
   int* pr = reinterpret_cast<int*>(red + 72);
   int* order = pr + nP + 2;
+  int* ridx = order + nP + 2;     // [nP] kept coordinates of the parent, in order
+  int* cidx = ridx + nP;          // [nP] compact index of each coordinate (-1: unused slot)
+  __shared__ int s_nr, s_cnt;
   const int64_t P = blockIdx.x;
   const int rx = lv.rx, ry = lv.ry;
   // assemble A_P
@@ -275,18 +323,53 @@ __global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, in
     }
   }
   __syncthreads();
-  if (!given) {
-    jacobi_eig(N, V, nP, cs, pr, red, 40, 1e-15);
-    sort_diag(N, nP, order);
-    for (int j = threadIdx.x; j < Ln; j += blockDim.x) lv.lamP[P * Ln + j] = N[order[j] * nP + order[j]];
-    __syncthreads();
-    // Psi (rows = eigenvectors)
-    for (int idx = threadIdx.x; idx < Ln * nP; idx += blockDim.x) {
-      const int j = idx / nP, i = idx % nP;
-      lv.Psi[(P * Ln + j) * nP + i] = V[i * nP + order[j]];
+  if (threadIdx.x == 0) {
+    int nr = 0;
+    for (int i = 0; i < nP; ++i) {
+      const bool kept = (i % L) < lv.cnt[P * lv.nchild + i / L];
+      cidx[i] = kept ? nr : -1;
+      if (kept) ridx[nr++] = i;
     }
+    s_nr = nr;
   }
   __syncthreads();
+  const int nR = s_nr;
+  if (!given) {
+    // the local problem on the kept coordinates (all of them under Strategy 1)
+    for (int idx = threadIdx.x; idx < nR * nR; idx += blockDim.x)
+      V[idx] = N[ridx[idx / nR] * nP + ridx[idx % nR]];
+    __syncthreads();
+    jacobi_eig(V, N, nR, cs, pr, red, 40, 1e-15);
+    sort_diag(V, nR, order);
+    const int nc = Ln < nR ? Ln : nR;
+    if (threadIdx.x == 0) {
+      int cn = nc;
+      if (B > 0.0) {
+        cn = 0;
+        for (int j = 0; j < nc; ++j) cn += V[order[j] * nR + order[j]] < B ? 1 : 0;
+        if (cn < 1) cn = 1;
+      }
+      s_cnt = cn;
+    }
+    for (int j = threadIdx.x; j < Ln; j += blockDim.x)
+      lv.lamP[P * Ln + j] = j < nc ? V[order[j] * nR + order[j]] : INFINITY;
+    __syncthreads();
+    const int cn = s_cnt;
+    // Psi (rows = eigenvectors), zero in unused rows and slots
+    for (int idx = threadIdx.x; idx < Ln * nP; idx += blockDim.x) {
+      const int j = idx / nP, i = idx % nP;
+      lv.Psi[(P * Ln + j) * nP + i] = (j < cn && cidx[i] >= 0) ? N[cidx[i] * nR + order[j]] : 0.0;
+    }
+  } else if (threadIdx.x == 0) {
+    int last = 0;
+    for (int j = 0; j < Ln; ++j)
+      for (int i = 0; i < nP; ++i)
+        if (lv.Psi[(P * Ln + j) * nP + i] != 0.0) { last = j + 1; break; }
+    s_cnt = last;
+  }
+  __syncthreads();
+  const int cntP = s_cnt;
+  if (threadIdx.x == 0) nx.cnt[P] = cntP;
   for (int idx = threadIdx.x; idx < Ln * nP; idx += blockDim.x) {
     const int j = idx / nP, i = idx % nP;
     N[j * nP + i] = lv.Psi[(P * Ln + j) * nP + i];
@@ -307,7 +390,8 @@ __global__ void k_coarse_setup(CoarseLevel lv, CoarseLevel nx, double* stats, in
       if (j > jj) continue;
       double acc = 0.0, acc2 = 0.0;
       for (int i = 0; i < nP; ++i) { acc += N[j * nP + i] * V[i * Ln + jj]; acc2 += N[jj * nP + i] * V[i * Ln + j]; }
-      const double v = 0.5 * (acc + acc2);
+      double v = 0.5 * (acc + acc2);
+      if (j == jj && j >= cntP) v = 1.0;   // unused slot (Strategy 2): a decoupled unknown
       nx.Ad[P * Ln2 + j * Ln + jj] = v;
       nx.Ad[P * Ln2 + jj * Ln + j] = v;
     } else if (o < 7 * Ln2) {
@@ -529,7 +613,7 @@ __global__ void k_operator_export(CoarseLevel lv, double* __restrict__ out) {
 // ------------------------------------------------------------------ host launchers
 static size_t jac_smem(int n, int extra_mats) {
   return (size_t)extra_mats * n * n * sizeof(double) + (size_t)(2 * n + 4 + 72) * sizeof(double) +
-         (size_t)(2 * n + 4) * sizeof(int) + 64;
+         (size_t)(4 * n + 4) * sizeof(int) + 64;
 }
 
 int launch_level1_eigen(msmg_ctx* c, cudaStream_t s) {
@@ -542,14 +626,16 @@ int launch_level1_eigen(msmg_ctx* c, cudaStream_t s) {
   return 0;
 }
 
-void launch_level1_galerkin(msmg_ctx* c, cudaStream_t s) {
+void launch_level1_galerkin(msmg_ctx* c, cudaStream_t s, bool threshold) {
   FineLevel& f = c->fine;
   CoarseLevel& l2 = c->lev[2];
+  const double B = threshold ? c->opts.eig_threshold[0] : 0.0;
+  k_level1_counts<<<(unsigned)((f.m + 7) / 8), 256, 0, s>>>(f.Phi, f.lam, f.m, f.L, f.nb, B, l2.cnt);
   const size_t sm = (size_t)(2 * f.L * f.nb + 3 * f.nb) * sizeof(double);
   cudaFuncSetAttribute(k_galerkin1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const unsigned thr = f.nb >= 256 ? 256 : (unsigned)((f.nb + 31) / 32 * 32 < 64 ? 64 : (f.nb + 31) / 32 * 32);
   k_galerkin1<<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, f.nbr, f.L, f.Phi, l2.Ad, l2.Ao,
-                                             l2.F, l2.z);
+                                             l2.F, l2.z, l2.cnt);
 }
 
 int launch_coarse_setup(msmg_ctx* c, int l, cudaStream_t s) {
@@ -558,7 +644,8 @@ int launch_coarse_setup(msmg_ctx* c, int l, cudaStream_t s) {
   if (lv.nP > 96) return MSMG_ERR_UNSUPPORTED;
   const size_t sm = jac_smem(lv.nP, 3);
   cudaFuncSetAttribute(k_coarse_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 0, c->opts.coarse_smoother == MSMG_BLOCK_IC0);
+  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 0, c->opts.coarse_smoother == MSMG_BLOCK_IC0,
+                                                  c->opts.eig_threshold[l - 1]);
   k_coarse_galerkin_off<<<(unsigned)lv.mP, 128, 0, s>>>(lv, nx);
   return 0;
 }
@@ -570,7 +657,8 @@ int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s) {
   if (lv.nP > 96) return MSMG_ERR_UNSUPPORTED;
   const size_t sm = jac_smem(lv.nP, 3);
   cudaFuncSetAttribute(k_coarse_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 1, c->opts.coarse_smoother == MSMG_BLOCK_IC0);
+  k_coarse_setup<<<(unsigned)lv.mP, 256, sm, s>>>(lv, nx, c->dtmp, 1, c->opts.coarse_smoother == MSMG_BLOCK_IC0,
+                                                  0.0);
   k_coarse_galerkin_off<<<(unsigned)lv.mP, 128, 0, s>>>(lv, nx);
   return 0;
 }
@@ -618,4 +706,17 @@ void launch_operator_export(msmg_ctx* c, int level, double* out, cudaStream_t s)
   k_operator_export<<<(unsigned)lv.me, 64, 0, s>>>(lv, out);
 }
 
+}  // namespace msmg
+
+namespace msmg {
+// dims_kept: the number of kept coordinates of every coarse level
+void launch_kept_sums(msmg_ctx* c, cudaStream_t s) {
+  cudaMemsetAsync(c->kept, 0, (kMaxLevels + 1) * sizeof(unsigned long long), s);
+  for (int l = 2; l <= c->nL; ++l) {
+    const CoarseLevel& lv = c->lev[l];
+    unsigned g = (unsigned)((lv.me + 255) / 256);
+    if (g > 1024) g = 1024;
+    k_kept_sum<<<g, 256, 0, s>>>(lv.cnt, lv.me, c->kept + l);
+  }
+}
 }  // namespace msmg
