@@ -13,7 +13,8 @@ flushed (256 MiB write) before every timed step.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batched [--steps K] [--warmup W]
   python bench.py --workload layered [--steps K] [--warmup W]
-  python bench.py --workload scale [--steps K] [--warmup W]
+  python bench.py --workload scale [--steps K] [--warmup W] [--hierarchy stated]
+  python bench.py --workload strategy2 [--steps K] [--warmup W]
 
 The default line also carries ``batched_rhs``: the same workload with 16
 zero-mean random right-hand sides solved in one call (one launch sequence for
@@ -242,10 +243,11 @@ def replica_value(world: int, units_per_rank: float, ms_per_step_local: float) -
 CROP = 64
 
 
-def oracle_sample(steps: int = 1):
+def oracle_sample(steps: int = 1, keep: bool = False):
     """The FP64 oracle as it stands on a bounded sample of the workload: the
     64^3 corner crop of the same field, same hierarchy parameters, same RHS
-    pattern; setup excluded from the metric."""
+    pattern; setup excluded from the metric.  With keep, the record also holds
+    the crop, its right-hand side and the oracle's hierarchy."""
     import oracle
     kappa = field()[:CROP, :CROP, :CROP].copy()
     f = rhs(kappa.shape).ravel()
@@ -261,10 +263,74 @@ def oracle_sample(steps: int = 1):
         its.append(res.iterations)
     n = kappa.size
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": n / float(np.mean(times)), "unit": "DOF/s", "cores": cores, "kind": "oracle",
-            "sample": f"{CROP}^3 corner crop of the same field and hierarchy, full PCG solve to rtol 1e-8 "
-                      f"({its[0]} iterations); oracle setup {t1 - t0:.1f} s excluded like the GPU setup",
-            "setup_s": t1 - t0, "solve_s": float(np.mean(times)), "iterations": its[0]}
+    rec = {"value": n / float(np.mean(times)), "unit": "DOF/s", "cores": cores, "kind": "oracle",
+           "sample": f"{CROP}^3 corner crop of the same field and hierarchy, full PCG solve to rtol 1e-8 "
+                     f"({its[0]} iterations); oracle setup {t1 - t0:.1f} s excluded like the GPU setup",
+           "setup_s": t1 - t0, "solve_s": float(np.mean(times)), "iterations": its[0]}
+    if keep:
+        rec.update(kappa=kappa, f=f, H=H)
+    return rec
+
+
+def error_vs_oracle(pkg, rec) -> dict:
+    """Error of each GPU form against the FP64 oracle, stated per result: the 64^3
+    crop solved by the GPU (its own bases, rtol 1e-8) and by the oracle to rtol
+    1e-12 (the reference solution; both zero-mean)."""
+    import oracle
+    import torch
+    kappa, f, H = rec["kappa"], rec["f"], rec["H"]
+    ref = None
+    for tol in (1e-11, 1e-10):          # tighter solves meet rounding (p^T A p <= 0) at contrast 1e6
+        try:
+            ref = oracle.solve(H, f, rtol=tol)
+            break
+        except FloatingPointError:
+            continue
+    if ref is None:
+        return {"unavailable": "the oracle's reference solve broke down at rtol 1e-10"}
+    out = {"sample": f"{CROP}^3 corner crop, hierarchy of the workload; oracle solution to rtol {tol:g} "
+                     f"({ref.iterations} iterations); GPU solves to rtol 1e-8 with their own bases",
+           "metric": "||x_gpu - x_oracle||_2 / ||x_oracle||_2"}
+    for form, prec in (("fp64", pkg.FP64), ("mixed", pkg.MIXED)):
+        S = pkg.Solver(torch.tensor(kappa, device="cuda"),
+                       pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec,
+                                   eig_tol=1e-8), h=(1.0 / N_GRID,) * 3)
+        x, info, _ = S.solve(torch.tensor(f.reshape(kappa.shape), device="cuda"), rtol=RTOL)
+        xe = x.cpu().numpy().ravel()
+        out[form] = {"error": float(np.linalg.norm(xe - ref.x) / np.linalg.norm(ref.x)),
+                     "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"]}
+        S.close()
+    return out
+
+
+def two_grid_record(pkg, kappa, f_dev, args, world, flush, stream, forms) -> dict:
+    """The exact two-grid preconditioner P_TG (Eq. (B_TG)) on the same workload: the
+    level-2 system solved by the inner PCG to 1e-10 every outer iteration, against
+    the V-cycle (P_ITG) of the main measurement."""
+    import torch
+    out = {"inner_rtol": 1e-10}
+    for form, prec in (("fp64", pkg.FP64), ("mixed", pkg.MIXED)):
+        S = pkg.Solver(kappa, pkg.Options(n_levels=N_LEVELS, block=BLOCK, ratio=RATIO, n_eig=N_EIG, precision=prec,
+                                          eig_tol=1e-8, two_grid=True, inner_rtol=1e-10, inner_max_iter=500))
+        x = torch.zeros_like(f_dev)
+        pkg.msmg_solve(S.ctx, f_dev, x, RTOL, 1000, 0)
+        torch.cuda.synchronize()
+        ms, info = [], None
+        for k in range(max(1, min(args.steps, 2))):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st, info = pkg.msmg_solve(S.ctx, f_dev, x, RTOL, 1000, 0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        step = max_over_ranks(world, float(np.mean(ms)))
+        out[form] = {"ms_per_step": step, "iterations": info[0]["iterations"],
+                     "inner_iterations": info[0]["inner_iterations"],
+                     "true_rel_residual": info[0]["true_rel_residual"],
+                     "p_itg_ms_per_step": forms[form]["ms_per_step"], "p_itg_iterations": forms[form]["iterations"]}
+        S.close()
+    return out
 
 
 def run_reference(args, world, rank):
@@ -447,9 +513,11 @@ def run_gpu(args, world, rank, local):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks}
+    line["two_grid"] = two_grid_record(pkg, kappa, f_dev, args, world, flush, stream, forms)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rec = oracle_sample(1)
+        rec = oracle_sample(1, keep=True)
         line["cpu_baseline"] = {k: rec[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["error_vs_oracle"] = error_vs_oracle(pkg, rec)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -581,12 +649,15 @@ def run_layered(args, world, rank, local):
     pkg.load_library()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    L = 12            # the channels cross many elements: 6 eigenvectors leave ~1000 PCG iterations at 128^3
+    # stated: the configuration as specified (6 eigenvectors, 5 levels: coarsest 3072 unknowns);
+    # tuned: 12 eigenvectors and 6 levels (the channels cross many elements: with 6
+    # eigenvectors the 128^3 field needs ~1000 PCG iterations, with 12 ~400)
+    L, nl = (6, 5) if args.hierarchy == "stated" else (12, 6)
     net, train = train_warm_start(pkg, torch, fields, L)
     kappa = torch.tensor(fields.layered_channels((LAYERED_N,) * 3, seed=100), device=dev)
     n = LAYERED_N ** 3
-    base = dict(n_levels=6, block=(8, 8, 8), ratio=[(2, 2, 2)] * 4, n_eig=[L] * 5, precision=pkg.MIXED, eig_tol=1e-8,
-                autotune=True)
+    base = dict(n_levels=nl, block=(8, 8, 8), ratio=[(2, 2, 2)] * (nl - 2), n_eig=[L] * (nl - 1), precision=pkg.MIXED,
+                eig_tol=1e-8, autotune=True)
     recs = {}
     solver = None
     for name, ws in (("cold", None), ("warm", net)):
@@ -620,7 +691,9 @@ def run_layered(args, world, rank, local):
     line = {"metric": METRIC, "value": world * n / (step * 1e-3), "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": LAYERED_WORKLOAD, "form": "mixed, learned warm start",
+            "config": {"workload": LAYERED_WORKLOAD.replace("6 levels (ratio 2), 12 eigenvectors",
+                                                            f"{nl} levels (ratio 2), {L} eigenvectors"),
+                       "hierarchy": args.hierarchy, "form": "mixed, learned warm start",
                        "l2": "flushed before each step (256 MiB write); working set > L2"},
             "iterations": info[0]["iterations"], "true_rel_residual": info[0]["true_rel_residual"],
             "setup": recs, "training": train,
@@ -628,6 +701,84 @@ def run_layered(args, world, rank, local):
             "gpu_launches": int(info[0]["kernel_launches"])}
     solver.close()
     net.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+STRAT2_N = 128
+STRAT2_WORKLOAD = ("128^3 layered field of the 512^3 recipe (85 layers, sinuous channels, contrast U(1e6, 1e8), "
+                   "seed 100); corner source/sink; 8^3 elements, 3 levels (ratio 2, the paper's three-grid setting), "
+                   "12 level-1 eigenvectors; "
+                   "level-2 spaces by Strategy 1 (12 or 24 per parent) or Strategy 2 (B_cc among 24 candidates, "
+                   "at quantiles of the level-2 local spectra; also B_c among the 12 level-1 candidates); "
+                   "PCG rtol 1e-8")
+
+
+def run_strategy2(args, world, rank, local):
+    """Strategy 2 (Section 5) against Strategy 1 on the layered channel field, as
+    the paper compares them: L_c fixed, the coarse-coarse dimension chosen by a
+    threshold B_cc among 24 candidates (the last run also thresholds level 1),
+    mixed form."""
+    import torch
+    import fields
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    _build.build()
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = STRAT2_N
+    n = N ** 3
+    kappa = torch.tensor(fields.layered_channels((N, N, N), seed=100), device=dev)
+    f = torch.tensor(rhs((N, N, N)), device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # three levels: with 24 vectors per level-2 parent a third level's local problems would
+    # have 8 x 24 unknowns, above the 96 of the shared-memory eigensolver
+    base = dict(n_levels=3, block=(8, 8, 8), ratio=[(2, 2, 2)], precision=pkg.MIXED, eig_tol=1e-8, autotune=True)
+
+    def measure(opts, export=False):
+        S = pkg.Solver(kappa, pkg.Options(**base, **opts))
+        x = torch.zeros_like(f)
+        for _ in range(args.warmup):
+            pkg.msmg_solve(S.ctx, f, x, RTOL, 3000, 0)
+        torch.cuda.synchronize()
+        ms, info = [], None
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st, info = pkg.msmg_solve(S.ctx, f, x, RTOL, 3000, 0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        i0 = S.info
+        rec = {"ms_per_step": float(np.mean(ms)), "value": n / (float(np.mean(ms)) * 1e-3),
+               "iterations": info[0]["iterations"], "true_rel_residual": info[0]["true_rel_residual"],
+               "dims": i0["dims"], "dims_kept": i0["dims_kept"], "setup_ms": i0["setup_ms"], "options": opts}
+        lam = (S.export_basis(1)[1].cpu().numpy(), S.export_basis(2)[1].cpu().numpy()) if export else None
+        S.close()
+        return rec, lam
+
+    recs = {}
+    recs["strategy1_Lcc12"], _ = measure(dict(n_eig=[12, 12]))
+    recs["strategy1_Lcc24"], (lam1, lam2) = measure(dict(n_eig=[12, 24]), export=True)
+    lam1, lam2 = lam1.ravel(), lam2.ravel()
+    lam2 = lam2[np.isfinite(lam2)]
+    for name, k1, k2 in (("strategy2_Bcc_mean12", 12, 12), ("strategy2_Bcc_mean8", 12, 8),
+                         ("strategy2_Bc_mean8_Bcc_mean12", 8, 12)):
+        B1 = float(np.quantile(lam1, k1 / 12.0)) if k1 < 12 else 0.0
+        B2 = float(np.quantile(lam2, k2 / 24.0))
+        recs[name], _ = measure(dict(n_eig=[12, 24], eig_threshold=[B1, B2]))
+        recs[name]["B"] = [B1, B2]
+    best = "strategy2_Bcc_mean12"
+    line = {"metric": METRIC, "value": recs[best]["value"], "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": recs[best]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": STRAT2_WORKLOAD, "form": "mixed",
+                                             "l2": "flushed before each step (256 MiB write); working set > L2"},
+            "runs": recs}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -651,8 +802,11 @@ def run_scale(args, world, rank, local):
     dev = torch.device("cuda", local)
     N = SCALE_N
     n = N ** 3
-    opts = pkg.Options(n_levels=7, block=(8, 8, 8), ratio=[(2, 2, 2)] * 5, n_eig=[4] * 6, precision=pkg.MIXED,
-                       eig_tol=1e-8, autotune=True)
+    # stated: 5 levels as specified (coarsest 16^3 elements x 4 = 16384 unknowns, a 2 GiB dense
+    # pseudo-inverse); tuned: 7 levels (coarsest 256 unknowns)
+    nl = 5 if args.hierarchy == "stated" else 7
+    opts = pkg.Options(n_levels=nl, block=(8, 8, 8), ratio=[(2, 2, 2)] * (nl - 2), n_eig=[4] * (nl - 1),
+                       precision=pkg.MIXED, eig_tol=1e-8, autotune=True)
     need = pkg.msmg_workspace_size(pkg.make_grid((N, N, N)), opts.to_c(), 1)
     free, total = torch.cuda.mem_get_info()
     vec_bytes = 2 * 8 * n + 4 * n                       # rhs, x (FP64) and kappa (FP32)
@@ -686,7 +840,8 @@ def run_scale(args, world, rank, local):
     line = {"metric": METRIC, "value": world * n / (step * 1e-3), "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": SCALE_WORKLOAD, "form": "mixed", "l2": "working set far above L2"},
+            "config": {"workload": SCALE_WORKLOAD.replace("7 levels", f"{nl} levels"), "hierarchy": args.hierarchy,
+                       "form": "mixed", "l2": "working set far above L2"},
             "iterations": info[0]["iterations"], "true_rel_residual": info[0]["true_rel_residual"],
             "converged": info[0]["converged"], "setup_ms": info0["setup_ms"], "eig_ms": info0["eig_ms"],
             "eig_iterations_max": info0["eig_iterations_max"], "workspace_gib": need / 2**30,
@@ -729,7 +884,10 @@ def main():
     ap.add_argument("--profile", action="store_true", help="short run for ncu (no timing output)")
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--max-iter", type=int, default=4)
-    ap.add_argument("--workload", default="inclusions", choices=["inclusions", "batched", "layered", "scale"])
+    ap.add_argument("--workload", default="inclusions",
+                    choices=["inclusions", "batched", "layered", "scale", "strategy2"])
+    ap.add_argument("--hierarchy", default="tuned", choices=["tuned", "stated"],
+                    help="layered / scale: the tuned hierarchy or the one the configuration states")
     ap.add_argument("--tuning-cache", default=os.path.join(os.environ.get("TMPDIR", "/tmp"), "msmg_tuning.json"),
                     help="autotune cache (JSON): a later run, e.g. under a profiler, reuses the variants found")
     args = ap.parse_args()
@@ -739,7 +897,8 @@ def main():
                                                                    int(os.environ.get("RANK", "0")), 0)
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    run = {"batched": run_batched, "layered": run_layered, "scale": run_scale}.get(args.workload, run_gpu)
+    run = {"batched": run_batched, "layered": run_layered, "scale": run_scale,
+           "strategy2": run_strategy2}.get(args.workload, run_gpu)
     rc = run(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist

@@ -174,6 +174,8 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
       lv.lamP = ar.take<double>(lv.mP * lv.Lnext);
     } else {
       lv.pinv = ar.take<double>(lv.n * lv.n);
+      lv.nk = lv.n;
+      c->cmaps = ar.take<int>(2 * lv.n);   // launch_coarsest points cmap / cinv here when it packs
     }
   }
   // solve buffers

@@ -247,10 +247,39 @@ __global__ void k_coarse_resid_smooth(CoarseLevel lv, LevelData<S> D, const S* _
   }
 }
 
-// Coarsest level: u = A^dagger f, dense symmetric GEMV, one warp per row.
+// Coarsest level: u = A^dagger f, dense symmetric GEMV, one warp per row.  Under
+// Strategy 2 the pseudo-inverse acts on the kept coordinates only (packed,
+// nk x nk): row p of the padded output reads packed row cinv[p] and gathers x
+// through cmap; unused slots get 0.
+__device__ __forceinline__ double coarsest_row(const double* __restrict__ A, const double* x, int64_t q, int64_t nk,
+                                               const int* __restrict__ cmap, int lane) {
+  const double* a = A + q * nk;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int64_t j = lane;
+  if (cmap) {
+    for (; j + 96 < nk; j += 128) {
+      a0 = fma(__ldg(a + j), x[cmap[j]], a0);
+      a1 = fma(__ldg(a + j + 32), x[cmap[j + 32]], a1);
+      a2 = fma(__ldg(a + j + 64), x[cmap[j + 64]], a2);
+      a3 = fma(__ldg(a + j + 96), x[cmap[j + 96]], a3);
+    }
+    for (; j < nk; j += 32) a0 = fma(__ldg(a + j), x[cmap[j]], a0);
+  } else {
+    for (; j + 96 < nk; j += 128) {
+      a0 = fma(__ldg(a + j), x[j], a0);
+      a1 = fma(__ldg(a + j + 32), x[j + 32], a1);
+      a2 = fma(__ldg(a + j + 64), x[j + 64], a2);
+      a3 = fma(__ldg(a + j + 96), x[j + 96], a3);
+    }
+    for (; j < nk; j += 32) a0 = fma(__ldg(a + j), x[j], a0);
+  }
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
 template <typename S>
 __global__ void k_dense_gemv(const double* __restrict__ A, const S* __restrict__ x, S* __restrict__ y,
-                             float* __restrict__ y32, int64_t n, const PcgScalars* sc, int R) {
+                             float* __restrict__ y32, int64_t n, int64_t nk, const int* __restrict__ cmap,
+                             const int* __restrict__ cinv, const PcgScalars* sc, int R) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -260,17 +289,8 @@ __global__ void k_dense_gemv(const double* __restrict__ A, const S* __restrict__
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)bi.blk * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
-  const double* a = A + row * n;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int64_t j = lane;
-  for (; j + 96 < n; j += 128) {
-    a0 = fma(__ldg(a + j), (double)__ldg(x + j), a0);
-    a1 = fma(__ldg(a + j + 32), (double)__ldg(x + j + 32), a1);
-    a2 = fma(__ldg(a + j + 64), (double)__ldg(x + j + 64), a2);
-    a3 = fma(__ldg(a + j + 96), (double)__ldg(x + j + 96), a3);
-  }
-  for (; j < n; j += 32) a0 = fma(__ldg(a + j), (double)__ldg(x + j), a0);
-  const double acc = warp_sum((a0 + a1) + (a2 + a3));
+  const int64_t q = cinv ? cinv[row] : row;
+  const double acc = q >= 0 ? coarsest_row(A, x, q, nk, cmap, lane) : 0.0;
   if (lane == 0) {
     y[row] = (S)acc;
     if (y32) y32[row] = (float)acc;
@@ -478,17 +498,8 @@ __device__ void tail_coarsest(const TailArgs& A, int r0, int r1, int cta, int nc
     if (sc(r)) continue;
     const double* x = A.f[A.nL] + (int64_t)r * n;
     double* y = A.u[A.nL] + (int64_t)r * n;
-    const double* a = lc.pinv + row * n;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int64_t j = lane;
-    for (; j + 96 < n; j += 128) {
-      a0 = fma(__ldg(a + j), x[j], a0);
-      a1 = fma(__ldg(a + j + 32), x[j + 32], a1);
-      a2 = fma(__ldg(a + j + 64), x[j + 64], a2);
-      a3 = fma(__ldg(a + j + 96), x[j + 96], a3);
-    }
-    for (; j < n; j += 32) a0 = fma(__ldg(a + j), x[j], a0);
-    const double acc = warp_sum((a0 + a1) + (a2 + a3));
+    const int64_t q = lc.cinv ? lc.cinv[row] : row;
+    const double acc = q >= 0 ? coarsest_row(lc.pinv, x, q, lc.nk, lc.cmap, lane) : 0.0;
     if (lane == 0) {
       y[row] = acc;
       if (A.nL == 2 && A.out32) A.out32[(int64_t)r * n + row] = (float)acc;
@@ -1053,7 +1064,8 @@ static const S* coarse_cycle_t(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t 
   }
   if (l == c->nL) {
     const unsigned grid = (unsigned)((lv.n * 32 + 255) / 256 * R);
-    k_dense_gemv<S><<<grid, 256, 0, s>>>(lv.pinv, f, u, l == 2 ? c->sb.ec32 : nullptr, lv.n, sc, R);
+    k_dense_gemv<S><<<grid, 256, 0, s>>>(lv.pinv, f, u, l == 2 ? c->sb.ec32 : nullptr, lv.n, lv.nk, lv.cmap,
+                                         lv.cinv, sc, R);
     return u;
   }
   const LevelData<S> D = level_data<S>(lv);

@@ -149,7 +149,10 @@ struct CoarseLevel {            // level l >= 2 (W_l)
   double* Psi;                  // [mP][Lnext][nP]
   double* lamP;                 // [mP][Lnext]
   // coarsest only
-  double* pinv;                 // [n][n]
+  double* pinv;                 // [nk][nk] pseudo-inverse on the kept coordinates
+  int64_t nk;                   // kept coordinates (n under Strategy 1)
+  int* cmap;                    // [nk] packed -> padded coordinate, null when nk == n
+  int* cinv;                    // [n] padded -> packed coordinate (-1: unused slot), null when nk == n
 };
 
 struct SolveBuffers {
@@ -213,6 +216,7 @@ struct msmg_ctx {
   int coop_grid;                                // CTAs of the cooperative coarse cycle (0: unavailable)
   int inner_grid;                               // CTAs of the exact two-grid inner solve (0: unavailable)
   unsigned long long* kept;                     // [kMaxLevels + 1] sum of cnt per level (device)
+  int* cmaps;                                   // [2 n_L] storage of the coarsest packing maps
   int coop_lt;
   size_t coop_smem;
 };

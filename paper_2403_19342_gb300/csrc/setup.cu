@@ -19,6 +19,7 @@
 #include "reduce.cuh"
 #include "linalg_small.cuh"
 #include <cmath>
+#include <vector>
 
 namespace msmg {
 
@@ -497,6 +498,19 @@ __global__ void k_assemble_dense(CoarseLevel lv, double* __restrict__ out) {
   }
 }
 
+// Strategy 2 packing of the coarsest level: out[i][j] = B[cmap[i]][cmap[j]]
+__global__ void k_pack_dense(const double* __restrict__ B, int64_t n, const int* __restrict__ cmap, int64_t nk,
+                             double* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nk * nk) return;
+  out[idx] = B[(int64_t)cmap[idx / nk] * n + cmap[idx % nk]];
+}
+__global__ void k_pack_vec(const double* __restrict__ z, const int* __restrict__ cmap, int64_t nk,
+                           double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nk) out[i] = z[cmap[i]];
+}
+
 // scal[0] = |z|^2, scal[1] = trace(A)
 __global__ void k_coarsest_scalars(const double* __restrict__ A, const double* __restrict__ z, int64_t n,
                                    double* scal) {
@@ -666,6 +680,29 @@ int launch_coarse_setup_given(msmg_ctx* c, int l, cudaStream_t s) {
 int launch_coarsest(msmg_ctx* c, cudaStream_t s) {
   CoarseLevel& lv = c->lev[c->nL];
   const int64_t n = lv.n;
+  // Strategy 2: the pseudo-inverse is built and applied on the kept coordinates
+  // only (packed), so unused slots cost the dense solve nothing
+  {
+    std::vector<int> cnt((size_t)lv.me), cmap, cinv((size_t)n, -1);
+    MSMG_CUDA_TRY(cudaMemcpyAsync(cnt.data(), lv.cnt, (size_t)lv.me * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int64_t a = 0; a < lv.me; ++a)
+      for (int k = 0; k < cnt[a] && k < lv.L; ++k) {
+        cinv[a * lv.L + k] = (int)cmap.size();
+        cmap.push_back((int)(a * lv.L + k));
+      }
+    lv.nk = (int64_t)cmap.size();
+    if (lv.nk < n) {
+      lv.cmap = c->cmaps;
+      lv.cinv = c->cmaps + n;
+      MSMG_CUDA_TRY(cudaMemcpyAsync(lv.cmap, cmap.data(), cmap.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      MSMG_CUDA_TRY(cudaMemcpyAsync(lv.cinv, cinv.data(), cinv.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      MSMG_CUDA_TRY(cudaStreamSynchronize(s));   // the host maps go out of scope
+    } else {
+      lv.cmap = lv.cinv = nullptr;
+    }
+  }
+  const int64_t nk = lv.nk;
   double* B = c->dtmp + 16;
   double* rowk = B + n * n;
   double* colk = rowk + n;
@@ -673,17 +710,25 @@ int launch_coarsest(msmg_ctx* c, cudaStream_t s) {
   double* scal = c->dtmp + 4;
   MSMG_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)n * n * sizeof(double), s));
   k_assemble_dense<<<(unsigned)lv.me, 64, 0, s>>>(lv, B);
-  k_coarsest_scalars<<<1, 256, 0, s>>>(B, lv.z, n, scal);
-  const unsigned g2 = (unsigned)((n * n + 255) / 256);
-  k_add_null_shift<<<g2, 256, 0, s>>>(B, lv.z, n, scal);
-  const unsigned g1 = (unsigned)((n + 255) / 256);
-  for (int64_t k = 0; k < n; ++k) {
-    k_gj_copy<<<g1, 256, 0, s>>>(B, n, k, rowk, colk);
-    k_gj_update<<<g2, 256, 0, s>>>(B, n, k, rowk, colk, c->dtmp);
+  const double* z = lv.z;
+  if (nk < n) {
+    // packed matrix and null vector (the pinv array is scratch until the end)
+    k_pack_dense<<<(unsigned)((nk * nk + 255) / 256), 256, 0, s>>>(B, n, lv.cmap, nk, lv.pinv);
+    MSMG_CUDA_TRY(cudaMemcpyAsync(B, lv.pinv, (size_t)nk * nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k_pack_vec<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(lv.z, lv.cmap, nk, lv.pinv + nk * nk);
+    z = lv.pinv + nk * nk;
   }
-  k_gemv_z<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(B, lv.z, n, scal, w);
-  k_dot_zw<<<1, 256, 0, s>>>(lv.z, w, n, scal);
-  k_project<<<g2, 256, 0, s>>>(B, lv.z, w, n, scal, lv.pinv);
+  k_coarsest_scalars<<<1, 256, 0, s>>>(B, z, nk, scal);
+  const unsigned g2 = (unsigned)((nk * nk + 255) / 256);
+  k_add_null_shift<<<g2, 256, 0, s>>>(B, z, nk, scal);
+  const unsigned g1 = (unsigned)((nk + 255) / 256);
+  for (int64_t k = 0; k < nk; ++k) {
+    k_gj_copy<<<g1, 256, 0, s>>>(B, nk, k, rowk, colk);
+    k_gj_update<<<g2, 256, 0, s>>>(B, nk, k, rowk, colk, c->dtmp);
+  }
+  k_gemv_z<<<(unsigned)((nk * 32 + 255) / 256), 256, 0, s>>>(B, z, nk, scal, w);
+  k_dot_zw<<<1, 256, 0, s>>>(z, w, nk, scal);
+  k_project<<<g2, 256, 0, s>>>(B, z, w, nk, scal, lv.pinv);
   return 0;
 }
 
