@@ -75,52 +75,72 @@ __device__ __forceinline__ S ld_vec(const S* p) {
   else return *p;
 }
 
-// r_i = f_i - (A_l u)_i for the rows i of one parent's children (thread t: row t).
+// Partial s of r_i = f_i - (A_l u)_i for row t of parent P: s = 0 takes f and
+// the element's own block, s = 1, 2, 3 its x, y, z neighbour blocks (+d, then
+// -d).  The row is (p0 + p1) + (p2 + p3): four threads (per-level kernels) or
+// one thread in turn (fused forms) give the same bits.
 template <int LT, typename S, bool NC = true>
-__device__ __forceinline__ S coarse_residual_row(const CoarseLevel& lv, const LevelData<S>& D, int64_t P, int t,
-                                                 const S* __restrict__ f, const S* __restrict__ u) {
+__device__ __forceinline__ S coarse_residual_part(const CoarseLevel& lv, const LevelData<S>& D, int64_t P, int t,
+                                                  int s, const S* __restrict__ f, const S* __restrict__ u) {
   const int L = LT ? LT : lv.L;
   const int64_t a = P * lv.nchild + t / L;
   const int k = t % L;
   const int L2 = L * L;
-  const S* ad = D.Ad + a * L2 + (size_t)k * L;
-  const S* ua = u + a * L;
-  S acc = ld_vec<NC>(f + a * L + k);
-  int nb[6];
+  if (s == 0) {
+    const S* ad = D.Ad + a * L2 + (size_t)k * L;
+    const S* ua = u + a * L;
+    S acc = ld_vec<NC>(f + a * L + k);
+    if (LT) {
 #pragma unroll
-  for (int q = 0; q < 6; ++q) nb[q] = __ldg(lv.nbr + a * 6 + q);
-  if (LT) {
-#pragma unroll
-    for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ad + mm) * ld_vec<NC>(ua + mm);
-  } else {
-    for (int mm = 0; mm < L; ++mm) acc -= __ldg(ad + mm) * ld_vec<NC>(ua + mm);
-  }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int bp = nb[2 * d + 1];   // +d neighbour: A_l[a, bp] = Ao[a][d]
-    if (bp >= 0) {
-      const S* ao = D.Ao + ((size_t)a * 3 + d) * L2 + (size_t)k * L;
-      const S* ub = u + (int64_t)bp * L;
-      if (LT) {
-#pragma unroll
-        for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + mm) * ld_vec<NC>(ub + mm);
-      } else {
-        for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + mm) * ld_vec<NC>(ub + mm);
-      }
+      for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ad + mm) * ld_vec<NC>(ua + mm);
+    } else {
+      for (int mm = 0; mm < L; ++mm) acc -= __ldg(ad + mm) * ld_vec<NC>(ua + mm);
     }
-    const int bm = nb[2 * d];       // -d neighbour: A_l[a, bm] = Ao[bm][d]^T
-    if (bm >= 0) {
-      const S* ao = D.Ao + ((size_t)bm * 3 + d) * L2 + k;
-      const S* ub = u + (int64_t)bm * L;
-      if (LT) {
+    return acc;
+  }
+  const int d = s - 1;
+  S acc = 0;
+  const int bp = __ldg(lv.nbr + a * 6 + 2 * d + 1);   // +d neighbour: A_l[a, bp] = Ao[a][d]
+  const int bm = __ldg(lv.nbr + a * 6 + 2 * d);       // -d neighbour: A_l[a, bm] = Ao[bm][d]^T
+  if (bp >= 0) {
+    const S* ao = D.Ao + ((size_t)a * 3 + d) * L2 + (size_t)k * L;
+    const S* ub = u + (int64_t)bp * L;
+    if (LT) {
 #pragma unroll
-        for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + (size_t)mm * LT) * ld_vec<NC>(ub + mm);
-      } else {
-        for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + (size_t)mm * L) * ld_vec<NC>(ub + mm);
-      }
+      for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + mm) * ld_vec<NC>(ub + mm);
+    } else {
+      for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + mm) * ld_vec<NC>(ub + mm);
+    }
+  }
+  if (bm >= 0) {
+    const S* ao = D.Ao + ((size_t)bm * 3 + d) * L2 + k;
+    const S* ub = u + (int64_t)bm * L;
+    if (LT) {
+#pragma unroll
+      for (int mm = 0; mm < LT; ++mm) acc -= __ldg(ao + (size_t)mm * LT) * ld_vec<NC>(ub + mm);
+    } else {
+      for (int mm = 0; mm < L; ++mm) acc -= __ldg(ao + (size_t)mm * L) * ld_vec<NC>(ub + mm);
     }
   }
   return acc;
+}
+
+template <int LT, typename S, bool NC = true>
+__device__ __forceinline__ S coarse_residual_row(const CoarseLevel& lv, const LevelData<S>& D, int64_t P, int t,
+                                                 const S* __restrict__ f, const S* __restrict__ u) {
+  const S p0 = coarse_residual_part<LT, S, NC>(lv, D, P, t, 0, f, u);
+  const S p1 = coarse_residual_part<LT, S, NC>(lv, D, P, t, 1, f, u);
+  const S p2 = coarse_residual_part<LT, S, NC>(lv, D, P, t, 2, f, u);
+  const S p3 = coarse_residual_part<LT, S, NC>(lv, D, P, t, 3, f, u);
+  return (p0 + p1) + (p2 + p3);
+}
+
+// (q0 + q1) + (q2 + q3) of the four lanes 4t .. 4t+3 of a warp, in every one of them
+// (IEEE addition commutes, so the four lanes agree bit for bit)
+template <typename S>
+__device__ __forceinline__ S quad_combine(S q) {
+  const S a = q + __shfl_xor_sync(0xffffffffu, q, 1);
+  return a + __shfl_xor_sync(0xffffffffu, a, 2);
 }
 
 // y_t = sum_j M[j][t] x_j from shared memory (M symmetric, so column t = row t)
@@ -138,8 +158,34 @@ __device__ __forceinline__ S smem_gemv_col(const S* M, const S* x, int nP, int t
   return (a0 + a1) + (a2 + a3);
 }
 
-// Pre-smoothing from zero on level l: u_P = Minv_P f_P.
+// Partial s of smem_gemv_col: its accumulator a_s (terms j = s mod 4 of the first
+// 4 floor(nP / 4), and for s = 0 the remainder), so that quad_combine of the four
+// partials equals smem_gemv_col bit for bit.
 template <typename S>
+__device__ __forceinline__ S smem_gemv_part(const S* M, const S* x, int nP, int t, int s) {
+  S a = 0;
+  const int n4 = nP & ~3;
+  for (int j = s; j < n4; j += 4) a = fma(M[(size_t)j * nP + t], x[j], a);
+  if (s == 0)
+    for (int j = n4; j < nP; ++j) a = fma(M[(size_t)j * nP + t], x[j], a);
+  return a;
+}
+
+// Threads of the per-level smoothing and residual kernels: four per row of the
+// parent (quad_combine), and at least the row-per-thread layout of
+// coarse_threads_d, whose warps form the restriction sums.
+__host__ __device__ inline unsigned coarse_threads4_d(int nP, int Ln) {
+  int t = 4 * nP;
+  const int t1 = (int)coarse_threads_d(nP, Ln);
+  if (t < t1) t = t1;
+  return (unsigned)((t + 31) / 32 * 32);
+}
+
+// Row layouts of the per-level kernels, the same bits either way: QUAD, four
+// threads per row (a level with few parents: shorter dependent chains, more
+// warps); otherwise thread t takes row t and forms the four partials in turn.
+// Pre-smoothing from zero on level l: u_P = Minv_P f_P.
+template <typename S, bool QUAD>
 __global__ void k_coarse_smooth_first(CoarseLevel lv, LevelData<S> D, const S* __restrict__ f, S* __restrict__ u,
                                       const PcgScalars* sc, int R) {
   const BatchIdx bi = batch_idx(R);
@@ -158,11 +204,20 @@ __global__ void k_coarse_smooth_first(CoarseLevel lv, LevelData<S> D, const S* _
   if (t < nP) fs[t] = __ldg(f + P * nP + t);
   cp_wait();
   __syncthreads();
-  if (t < nP) u[P * nP + t] = smem_gemv_col(Mi, fs, nP, t);
+  if constexpr (QUAD) {
+    const int row = t >> 2, sub = t & 3;
+    S q = row < nP ? smem_gemv_part(Mi, fs, nP, row, sub) : (S)0;
+    q = quad_combine(q);
+    if (row < nP && sub == 0) u[P * nP + row] = q;
+  } else {
+    if (t < nP) u[P * nP + t] = smem_gemv_col(Mi, fs, nP, t);
+  }
 }
 
 // Residual and restriction to level l+1: fn[P][j] = sum_i Psi[P][j][i] (f - A_l u)_i.
-template <int LT, typename S>
+// The residual rows by four threads each; the sums over the rows in the warps of
+// the row-per-thread layout (the order of the fused forms).
+template <int LT, typename S, bool QUAD>
 __global__ void k_coarse_resid_restrict(CoarseLevel lv, LevelData<S> D, const S* __restrict__ f,
                                         const S* __restrict__ u, S* __restrict__ fn, const PcgScalars* sc, int R) {
   const BatchIdx bi = batch_idx(R);
@@ -175,24 +230,35 @@ __global__ void k_coarse_resid_restrict(CoarseLevel lv, LevelData<S> D, const S*
   S* sm = reinterpret_cast<S*>(smraw);
   const int64_t P = bi.blk;
   const int nP = lv.nP, Ln = lv.Lnext;
-  const int nw = (blockDim.x + 31) >> 5;
+  const int nw = (int)(coarse_threads_d(nP, Ln) / 32);
   S* ps = sm;                            // [Ln][nP]
   S* red = sm + (size_t)Ln * nP;         // [Ln][nw]
+  S* rs = red + (size_t)Ln * nw;         // [nP] residual rows
   cta_cp(ps, D.Psi + (size_t)P * Ln * nP, Ln * nP);
   const int t = threadIdx.x;
-  const S rt = t < nP ? coarse_residual_row<LT>(lv, D, P, t, f, u) : (S)0;
+  if constexpr (QUAD) {
+    const int row = t >> 2, sub = t & 3;
+    S q = row < nP ? coarse_residual_part<LT>(lv, D, P, row, sub, f, u) : (S)0;
+    q = quad_combine(q);
+    if (row < nP && sub == 0) rs[row] = q;
+  } else {
+    if (t < nP) rs[t] = coarse_residual_row<LT>(lv, D, P, t, f, u);
+  }
   cp_wait();
   __syncthreads();
-  const int lane = t & 31, w = t >> 5;
-  for (int j = 0; j < Ln; ++j) {
-    S v = t < nP ? ps[(size_t)j * nP + t] * rt : (S)0;
-    v = warp_sum_t(v);
-    if (lane == 0) red[j * nw + w] = v;
+  if (t < nw * 32) {
+    const int lane = t & 31, w = t >> 5;
+    const S rt = t < nP ? rs[t] : (S)0;
+    for (int j = 0; j < Ln; ++j) {
+      S v = t < nP ? ps[(size_t)j * nP + t] * rt : (S)0;
+      v = warp_sum_t(v);
+      if (lane == 0) red[j * nw + w] = v;
+    }
   }
   __syncthreads();
   if (t < Ln) {
     S acc = 0;
-    for (int q = 0; q < nw; ++q) acc += red[t * nw + q];
+    for (int qq = 0; qq < nw; ++qq) acc += red[t * nw + qq];
     fn[P * Ln + t] = acc;
   }
 }
@@ -216,8 +282,9 @@ __global__ void k_coarse_prolong(CoarseLevel lv, LevelData<S> D, S* __restrict__
   u[P * lv.nP + t] += acc;
 }
 
-// Post-smoothing: out = u + Minv (f - A_l u)   (out must not alias u).
-template <int LT, typename S>
+// Post-smoothing: out = u + Minv (f - A_l u)   (out must not alias u); the residual
+// rows and the smoother GEMV by four threads per row.
+template <int LT, typename S, bool QUAD>
 __global__ void k_coarse_resid_smooth(CoarseLevel lv, LevelData<S> D, const S* __restrict__ f,
                                       const S* __restrict__ u, S* __restrict__ out, float* __restrict__ out32,
                                       const PcgScalars* sc, int R) {
@@ -237,13 +304,29 @@ __global__ void k_coarse_resid_smooth(CoarseLevel lv, LevelData<S> D, const S* _
   S* rs = sm + (size_t)nP * nP;
   cta_cp(Mi, D.Minv + (size_t)P * nP * nP, nP * nP);
   const int t = threadIdx.x;
-  if (t < nP) rs[t] = coarse_residual_row<LT>(lv, D, P, t, f, u);
-  cp_wait();
-  __syncthreads();
-  if (t < nP) {
-    const S v = u[P * nP + t] + smem_gemv_col(Mi, rs, nP, t);
-    out[P * nP + t] = v;
-    if (out32) out32[P * nP + t] = (float)v;
+  if constexpr (QUAD) {
+    const int row = t >> 2, sub = t & 3;
+    S q = row < nP ? coarse_residual_part<LT>(lv, D, P, row, sub, f, u) : (S)0;
+    q = quad_combine(q);
+    if (row < nP && sub == 0) rs[row] = q;
+    cp_wait();
+    __syncthreads();
+    S g = row < nP ? smem_gemv_part(Mi, rs, nP, row, sub) : (S)0;
+    g = quad_combine(g);
+    if (row < nP && sub == 0) {
+      const S v = u[P * nP + row] + g;
+      out[P * nP + row] = v;
+      if (out32) out32[P * nP + row] = (float)v;
+    }
+  } else {
+    if (t < nP) rs[t] = coarse_residual_row<LT>(lv, D, P, t, f, u);
+    cp_wait();
+    __syncthreads();
+    if (t < nP) {
+      const S v = u[P * nP + t] + smem_gemv_col(Mi, rs, nP, t);
+      out[P * nP + t] = v;
+      if (out32) out32[P * nP + t] = (float)v;
+    }
   }
 }
 
@@ -785,8 +868,9 @@ static inline size_t smem_smooth(const CoarseLevel& lv) {
 }
 template <typename S>
 static inline size_t smem_restrict(const CoarseLevel& lv) {
-  return ((size_t)lv.Lnext * lv.nP + (size_t)lv.Lnext * (coarse_threads(lv) / 32)) * sizeof(S) + 16;
+  return ((size_t)lv.Lnext * lv.nP + (size_t)lv.Lnext * (coarse_threads(lv) / 32) + lv.nP) * sizeof(S) + 16;
 }
+static inline unsigned coarse_threads4(const CoarseLevel& lv) { return coarse_threads4_d(lv.nP, lv.Lnext); }
 
 template <typename F>
 static void with_L(int L, F&& fn) {
@@ -809,11 +893,14 @@ static void prepare_t(msmg_ctx* c) {
   for (int l = 2; l < c->nL; ++l) {
     CoarseLevel& lv = c->lev[l];
     const int sm1 = (int)smem_smooth<S>(lv), sm2 = (int)smem_restrict<S>(lv);
-    cudaFuncSetAttribute(k_coarse_smooth_first<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1);
+    cudaFuncSetAttribute(k_coarse_smooth_first<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1);
+    cudaFuncSetAttribute(k_coarse_smooth_first<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1);
     with_L(lv.L, [&](auto LC) {
       constexpr int LT = decltype(LC)::value;
-      cudaFuncSetAttribute(k_coarse_resid_smooth<LT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1);
-      cudaFuncSetAttribute(k_coarse_resid_restrict<LT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+      cudaFuncSetAttribute(k_coarse_resid_smooth<LT, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1);
+      cudaFuncSetAttribute(k_coarse_resid_smooth<LT, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1);
+      cudaFuncSetAttribute(k_coarse_resid_restrict<LT, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+      cudaFuncSetAttribute(k_coarse_resid_restrict<LT, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
     });
   }
 }
@@ -1070,17 +1157,26 @@ static const S* coarse_cycle_t(msmg_ctx* c, int l, PcgScalars* sc, cudaStream_t 
   }
   const LevelData<S> D = level_data<S>(lv);
   S* fn = (S*)c->sb.vf[l + 1];
-  const unsigned thr = coarse_threads(lv);
   const unsigned grid = (unsigned)(lv.mP * R);
-  k_coarse_smooth_first<S><<<grid, thr, smem_smooth<S>(lv), s>>>(lv, D, f, u, sc, R);
+  // four threads per row when the level's CTAs leave the GPU short of warps
+  const bool quad = grid < (unsigned)(152 * 8);
+  const unsigned thr = coarse_threads(lv), thrs = quad ? coarse_threads4(lv) : thr;
+  if (quad) k_coarse_smooth_first<S, true><<<grid, thrs, smem_smooth<S>(lv), s>>>(lv, D, f, u, sc, R);
+  else k_coarse_smooth_first<S, false><<<grid, thrs, smem_smooth<S>(lv), s>>>(lv, D, f, u, sc, R);
   with_L(lv.L, [&](auto LC) {
-    k_coarse_resid_restrict<decltype(LC)::value, S><<<grid, thr, smem_restrict<S>(lv), s>>>(lv, D, f, u, fn, sc, R);
+    constexpr int LT = decltype(LC)::value;
+    if (quad)
+      k_coarse_resid_restrict<LT, S, true><<<grid, thrs, smem_restrict<S>(lv), s>>>(lv, D, f, u, fn, sc, R);
+    else
+      k_coarse_resid_restrict<LT, S, false><<<grid, thrs, smem_restrict<S>(lv), s>>>(lv, D, f, u, fn, sc, R);
   });
   const S* e = coarse_cycle_t<S>(c, l + 1, sc, s);
   k_coarse_prolong<S><<<grid, thr, 0, s>>>(lv, D, u, e, sc, R);
   with_L(lv.L, [&](auto LC) {
-    k_coarse_resid_smooth<decltype(LC)::value, S><<<grid, thr, smem_smooth<S>(lv), s>>>(
-        lv, D, f, u, w, l == 2 ? c->sb.ec32 : nullptr, sc, R);
+    constexpr int LT = decltype(LC)::value;
+    float* o32 = l == 2 ? c->sb.ec32 : nullptr;
+    if (quad) k_coarse_resid_smooth<LT, S, true><<<grid, thrs, smem_smooth<S>(lv), s>>>(lv, D, f, u, w, o32, sc, R);
+    else k_coarse_resid_smooth<LT, S, false><<<grid, thrs, smem_smooth<S>(lv), s>>>(lv, D, f, u, w, o32, sc, R);
   });
   return w;
 }
