@@ -25,6 +25,10 @@ reordering beyond what the definition states:
                     the coarsest Moore-Penrose pseudo-inverse.
 * ``solver``     -- the V-cycle (Algorithm 1, generalised recursively to any
                     number of levels) and preconditioned conjugate gradients.
+* ``impes``      -- two-phase flow by the improved IMPES scheme (Section 6):
+                    fluid model, well index, the pressure terms of Eq. (IMP)
+                    and the upstream-weighted saturation sub-steps of
+                    Eq. (ES).
 * ``learned``    -- the learned warm start of the level-1 eigensolves (not a
                     step of the paper): network forward, sign-invariant loss,
                     back-propagation and the Adam step.

@@ -48,6 +48,14 @@ class Options:
     # candidate eigenvectors (n_eig[l-1] of them) whose eigenvalues lie below the threshold
     # (B_c, B_cc), at least one; 0 (or a short list) keeps all n_eig[l-1] (Strategy 1)
     eig_threshold: list = field(default_factory=list)
+    # a nonnegative term added to the diagonal of A cell by cell (the well terms of
+    # Section 6: W_i = WI kappa lambda / mu at the cells a producer crosses), and to
+    # the left-hand forms of the local problems, as Section 6 modifies them; None: none
+    cell_diag: object = None
+
+    def singular(self) -> bool:
+        """A has the constant null space (no cell term)."""
+        return self.cell_diag is None or not np.any(np.asarray(self.cell_diag) > 0)
 
     def threshold(self, l: int) -> float:
         """B for the local problems on the elements of E_l (0: Strategy 1)."""
@@ -285,12 +293,15 @@ def setup(kappa, h, opts: Options) -> Hierarchy:
     shape = kappa.shape[-3:]
     T = face_transmissibilities(kappa, h)
     S = trace_weight(kappa, h)
+    W = None if opts.cell_diag is None else np.asarray(opts.cell_diag, dtype=np.float64).reshape(shape)
     A1 = assemble(T)
+    if W is not None:
+        A1 = (A1 + sp.diags(W.ravel())).tocsr()
     nL = opts.n_levels
 
     # level 1 -> 2: Eq. (spepb) on the elements of E_1; the candidates' unused slots
     # (Strategy 2) are zero rows of the padded basis array and no rows of R_1
-    lam1, Phi, cells = level1_eigenpairs(T, S, opts.block, opts.n_eig[0])
+    lam1, Phi, cells = level1_eigenpairs(T, S, opts.block, opts.n_eig[0], W)
     m1, L1, nb = Phi.shape
     cnt = np.array([kept_count(lam1[e], opts.threshold(1)) for e in range(m1)])
     keep = np.arange(L1)[None, :] < cnt[:, None]
@@ -327,6 +338,8 @@ def setup(kappa, h, opts: Options) -> Hierarchy:
             pd = np.array(pd)
         fine_box = [fine_box[d] * r[d] for d in range(3)]
         An = assemble(T * interior_face_mask(shape, fine_box))
+        if W is not None:
+            An = (An + sp.diags(W.ravel())).tocsr()
         An_coarse = (B.T @ An @ B).tocsr()
         Ll = opts.n_eig[l - 1]
         lam_c, vecs = coarse_eigenpairs_kept(An_coarse, list(pd), Ll, opts.threshold(l))

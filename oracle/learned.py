@@ -7,9 +7,12 @@ to the eigen-residual tolerance, so the preconditioner does not depend on it.
 
 Parameters are one flat array with the layout of the library (weight matrix
 l row-major [fan_in][fan_out] at w_off[l], bias at b_off[l]); the layout is an
-input here.  The products read the weights rounded to BF16 (``bf16_round``),
-as the library's kernels do; gradients are taken with respect to those
-rounded weights and applied to the FP32 masters.
+input here.  The products read BF16 operands, as the library's tensor-core
+products do: the weights rounded to BF16 (``bf16_round``) and the activations
+x, h1, h2 rounded to BF16 before the product that reads them (after rounding
+the exact value to FP32, the precision in which the library accumulates).
+Gradients are taken with respect to the rounded weights, through the rounding
+of the activations as through the identity, and applied to the FP32 masters.
 """
 from __future__ import annotations
 
@@ -46,16 +49,23 @@ def out_weight(x: np.ndarray) -> np.ndarray:
     return np.sqrt(e / e.sum(axis=-1, keepdims=True))
 
 
-def forward(Ws, bs, x: np.ndarray):
-    """h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), o = h2 W3 + b3 and the output
-    y_k = w * o_k with w = out_weight(x) (the network predicts phi; y = S^{1/2} phi
-    up to the element's normalisation).  Returns (h1, h2, y)."""
+def forward(Ws, bs, x: np.ndarray, acts: bool = False):
+    """h1 = relu(x' W1 + b1), h2 = relu(h1' W2 + b2), o = h2' W3 + b3, with ' the
+    rounding of an activation to BF16, and the output y_k = w * o_k with
+    w = out_weight(x) (the network predicts phi; y = S^{1/2} phi up to the
+    element's normalisation).  Returns (h1, h2, y), or with ``acts`` also the
+    rounded operands (x', h1', h2')."""
     x = np.asarray(x, dtype=np.float64)
-    h1 = np.maximum(x @ Ws[0] + bs[0], 0.0)
-    h2 = np.maximum(h1 @ Ws[1] + bs[1], 0.0)
-    o = h2 @ Ws[2] + bs[2]
+    xr = bf16_round(x)
+    h1 = np.maximum(xr @ Ws[0] + bs[0], 0.0)
+    h1r = bf16_round(h1)
+    h2 = np.maximum(h1r @ Ws[1] + bs[1], 0.0)
+    h2r = bf16_round(h2)
+    o = h2r @ Ws[2] + bs[2]
     B, n_in = x.shape
     y = (o.reshape(B, -1, n_in) * out_weight(x)[:, None, :]).reshape(B, -1)
+    if acts:
+        return h1, h2, y, (xr, h1r, h2r)
     return h1, h2, y
 
 
@@ -78,18 +88,18 @@ def gradients(params, dims, w_off, b_off, x, target, n_vec: int):
     """Loss and gradient (flat, parameter layout) by back-propagation."""
     Ws, bs = unpack(params, dims, w_off, b_off)
     x = np.asarray(x, dtype=np.float64)
-    h1, h2, out = forward(Ws, bs, x)
+    h1, h2, out, ops = forward(Ws, bs, x, acts=True)
     loss, dy = loss_and_grad(out, target, n_vec)
     B, n_in = x.shape
     d3 = (dy.reshape(B, -1, n_in) * out_weight(x)[:, None, :]).reshape(B, -1)
     g = np.zeros(np.asarray(params).shape, dtype=np.float64)
-    acts = [x, h1, h2]
+    pre = [None, h1, h2]                      # ReLU masks from the layer outputs
     d = d3
     for l in (2, 1, 0):
-        g[w_off[l]:w_off[l] + dims[l] * dims[l + 1]] = (acts[l].T @ d).ravel()
+        g[w_off[l]:w_off[l] + dims[l] * dims[l + 1]] = (ops[l].T @ d).ravel()
         g[b_off[l]:b_off[l] + dims[l + 1]] = d.sum(axis=0)
         if l > 0:
-            d = (d @ Ws[l].T) * (acts[l] > 0.0)
+            d = (d @ Ws[l].T) * (pre[l] > 0.0)
     return loss, g
 
 

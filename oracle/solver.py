@@ -127,7 +127,7 @@ class PCGResult:
 
 
 def pcg(A, b: np.ndarray, precond=None, rtol: float = 1e-8, max_iter: int = 1000,
-        x0: np.ndarray | None = None, flexible: bool = False) -> PCGResult:
+        x0: np.ndarray | None = None, flexible: bool = False, singular: bool = True) -> PCGResult:
     """Preconditioned conjugate gradients (Hestenes-Stiefel recurrences) for the
     singular consistent system A x = b of Eq. (p).
 
@@ -137,16 +137,17 @@ def pcg(A, b: np.ndarray, precond=None, rtol: float = 1e-8, max_iter: int = 1000
     ``flexible`` the direction update takes the Polak-Ribiere coefficient
     beta = z_{k+1}^T (r_{k+1} - r_k) / z_k^T r_k, which tolerates a
     preconditioner that is not exactly the same linear map every time (the
-    mixed form's rounded V-cycle)."""
+    mixed form's rounded V-cycle).  With ``singular`` False (A has a cell term,
+    the wells of Section 6) b is taken as it is and x keeps its mean."""
     b = np.asarray(b, dtype=np.float64)
-    mean = float(b.mean())
+    mean = float(b.mean()) if singular else 0.0
     b = b - mean
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     r = b - A @ x
     bnorm = float(np.linalg.norm(b))
     res = [float(np.linalg.norm(r))]
     if bnorm == 0.0 or res[0] <= rtol * bnorm:
-        return PCGResult(x - x.mean(), 0, True, res, mean)
+        return PCGResult(x - x.mean() if singular else x, 0, True, res, mean)
     apply_p = precond if precond is not None else (lambda v: v.copy())
     z = apply_p(r)
     p = z.copy()
@@ -173,7 +174,7 @@ def pcg(A, b: np.ndarray, precond=None, rtol: float = 1e-8, max_iter: int = 1000
             beta = rz_new / rz
         p = z + beta * p
         rz = rz_new
-    return PCGResult(x - x.mean(), k, converged, res, mean)
+    return PCGResult(x - x.mean() if singular else x, k, converged, res, mean)
 
 
 def solve(H: Hierarchy, b: np.ndarray, rtol: float = 1e-8, max_iter: int = 1000, mixed: bool = False,
@@ -186,4 +187,5 @@ def solve(H: Hierarchy, b: np.ndarray, rtol: float = 1e-8, max_iter: int = 1000,
         pre = lambda r: vcycle_two_grid(H, r)
     else:
         pre = (lambda r: vcycle_mixed(H, r)) if mixed else (lambda r: vcycle(H, r))
-    return pcg(H.A[0], np.asarray(b, dtype=np.float64).ravel(), pre, rtol, max_iter, flexible=mixed)
+    return pcg(H.A[0], np.asarray(b, dtype=np.float64).ravel(), pre, rtol, max_iter, flexible=mixed,
+               singular=H.opts.singular())

@@ -42,13 +42,16 @@ def element_cells(shape, box) -> np.ndarray:
     return origin[:, None] + local[None, :]
 
 
-def level1_eigenpairs(T: np.ndarray, S: np.ndarray, box, L: int):
-    """Smallest ``L`` eigenpairs of Eq. (spepb) on every level-1 element.
+def level1_eigenpairs(T: np.ndarray, S: np.ndarray, box, L: int, W: np.ndarray | None = None):
+    """Smallest ``L`` eigenpairs of Eq. (spepb) on every level-1 element, with the
+    cell term W (wells, Section 6) added to the left-hand form when given.
 
     Returns (lam (m, L), Phi (m, L, nb), cells (m, nb)); Phi[e, k] is the k-th
     eigenvector on element e's cells (in element order), S-orthonormal."""
     shape = T.shape[1:]
     An = assemble(T * interior_face_mask(shape, box))
+    if W is not None:
+        An = (An + sp.diags(np.asarray(W, dtype=np.float64).ravel())).tocsr()
     cells = element_cells(shape, box)
     s = S.ravel()
     m, nb = cells.shape

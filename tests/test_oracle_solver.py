@@ -210,3 +210,44 @@ def test_two_grid_equals_vcycle_with_two_levels():
     r = np.random.default_rng(2).standard_normal(H.dims[0])
     r -= r.mean()
     np.testing.assert_allclose(oracle.vcycle_two_grid(H, r), oracle.vcycle(H, r), rtol=1e-10, atol=1e-12)
+
+
+# ------------------------------------------------------------------ cell term (wells, Section 6)
+def test_cell_term_shifts_local_spectrum_by_its_weight():
+    # with W = c S cell by cell, A_K phi + W phi = lambda S phi has the W-free eigenvectors
+    # and eigenvalues shifted by exactly c (the right-hand form is S)
+    rng = np.random.default_rng(8)
+    shape = (8, 8, 8)
+    h = (1 / 8,) * 3
+    kap = np.exp(rng.normal(0, 1.5, size=shape))
+    T = oracle.face_transmissibilities(kap, h)
+    S = oracle.trace_weight(kap, h)
+    lam0, Phi0, _ = oracle.level1_eigenpairs(T, S, (4, 4, 4), 5)
+    lam1, Phi1, _ = oracle.level1_eigenpairs(T, S, (4, 4, 4), 5, W=0.37 * S)
+    np.testing.assert_allclose(lam1, lam0 + 0.37, rtol=0, atol=1e-10)
+    for e in range(8):       # same spans (projectors, S-orthonormal bases)
+        np.testing.assert_allclose(Phi1[e].T @ Phi1[e], Phi0[e].T @ Phi0[e], atol=1e-8)
+
+
+def test_cell_term_nonsingular_solve():
+    rng = np.random.default_rng(9)
+    shape = (8, 8, 16)
+    h = (1 / 16, 1 / 8, 1 / 8)
+    kap = np.exp(rng.normal(0, 2, size=shape))
+    W = np.zeros(shape)
+    W[:, 0, 0] = 50.0                      # a producer column
+    W[:, -1, -1] = 80.0
+    opts = oracle.Options(n_levels=3, block=(2, 2, 2), ratio=[(2, 2, 2)], n_eig=[3, 4], nu=[1, 1], cell_diag=W)
+    H = oracle.setup(kap, h, opts)
+    A = H.A[0].toarray()
+    np.testing.assert_allclose(A - oracle.assemble(H.T).toarray(), np.diag(W.ravel()), atol=1e-12)
+    assert np.linalg.eigvalsh(A).min() > 0
+    b = rng.standard_normal(A.shape[0]) + 3.0          # a mean that must not be removed
+    res = oracle.solve(H, b, rtol=1e-10)
+    np.testing.assert_allclose(res.x, np.linalg.solve(A, b), rtol=1e-8, atol=1e-12)
+    # the preconditioned spectrum stays in (0, 1] (Section 4 with a positive definite A)
+    n = A.shape[0]
+    V = np.column_stack([oracle.vcycle(H, np.eye(n)[:, j]) for j in range(n)])
+    C = np.linalg.cholesky(0.5 * (V + V.T))
+    w = np.linalg.eigvalsh(C.T @ A @ C)
+    assert w[-1] <= 1.0 + 1e-9 and w[0] > 1e-6
