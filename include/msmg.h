@@ -125,6 +125,13 @@ typedef struct {
                                        /* (Strategy 1).  The arrays keep n_eig[i] slots per element: */
                                        /* an unused slot holds a zero basis vector and, one level     */
                                        /* up, a decoupled unknown that stays zero                     */
+    const double* cell_diag;           /* NULL, or device, nx*ny*nz FP64 values >= 0, natural order: */
+                                       /* a term W added to the diagonal of A (the well terms of     */
+                                       /* Section 6, W = WI kappa lambda at the cells a producer      */
+                                       /* crosses) and to the left-hand forms of the local problems, */
+                                       /* as Section 6 modifies them.  With some W > 0 the system is  */
+                                       /* nonsingular: msmg_solve then removes no mean, and the       */
+                                       /* coarsest solve is a plain inverse.  Read by msmg_setup only */
 } msmg_options;
 
 typedef struct {
@@ -344,12 +351,51 @@ int msmg_export_operator(msmg_ctx* ctx, int level, double* out, msmg_stream stre
  *   f        device, n FP64 sources, natural order (msmg_solve's rhs; its mean is removed
  *            here as the solve removes it)
  *   v        device, 3 x n FP64, natural order: v[d][cell] = velocity on the cell's +d face
- *   balance  host, 2 doubles (may be NULL): ||div - b||_2 and ||b||_2; their ratio equals the
- *            solve's relative residual ||b - A p|| / ||b||.  With balance the call
- *            synchronises the stream.
+ *   balance  host, 2 doubles (may be NULL): ||div - b||_2 and ||b||_2; ||div - b|| equals the
+ *            solve's residual ||f' - A p|| (f' = f - mean(f)), so their ratio is its relative
+ *            residual.  With a cell term W (options.cell_diag, wells) b = f - W p, the net source
+ *            (injection and the flow that leaves through the wells), no mean is removed, and
+ *            ||div - b|| equals ||f - (A + W) p||.  With balance the call synchronises the stream.
  * Uses the context's reduction scratch: not concurrently with a solve on the same context.
  */
 int msmg_velocity(msmg_ctx* ctx, const double* p, const double* f, double* v, double* balance, msmg_stream stream);
+
+/*
+ * ------------------------------------------------------------ two-phase flow (Section 6)
+ * The improved IMPES scheme around the pressure solve.  Fluid model: S* = (S - s_wc) /
+ * (1 - s_wc - s_or) clipped to [0, 1], k_rw = S*^2, k_ro = (1 - S*)^2, total mobility
+ * lambda = k_rw / mu_w + k_ro / mu_o, fractional flow f_w = (k_rw / mu_w) / lambda (the paper:
+ * mu_w = 0.3, mu_o = 3.0, s_wc = s_or = 0.2).  A time step: msmg_impes_pressure_terms, then
+ * msmg_setup with kappa_eff and options.cell_diag = w, msmg_solve(b) (Eq. (IMP)), msmg_velocity,
+ * then msmg_impes_transport (Eq. (ES)).
+ */
+typedef struct {
+    double mu_w, mu_o;       /* water and oil viscosities                   */
+    double s_wc, s_or;       /* connate water and residual oil saturations  */
+} msmg_fluid;
+
+/* The pressure system of Eq. (IMP) at saturation S (natural order, device arrays):
+ *   kappa       3 x n permeability (kappa^x, kappa^y, kappa^z)
+ *   wi          n: well index of each cell a producer crosses (Section 6's formula), 0 elsewhere
+ *   q_inj       n: injection rate per unit volume (the injector's rate spread over its cells)
+ *   kappa_eff   out, 3 x n: lambda(S) kappa, the permeability of the pressure solve
+ *   w           out, n: W = wi kappa^x lambda(S), the producers' term of A (options.cell_diag)
+ *   b           out, n: q_inj + W p_bh, the right-hand side
+ * Asynchronous; MSMG_ERR_INVALID_ARG on a bad size or fluid. */
+int msmg_impes_pressure_terms(int64_t n, const msmg_fluid* fluid, const double* S, const double* kappa,
+                              const double* wi, const double* q_inj, double p_bh, double* kappa_eff, double* w,
+                              double* b, msmg_stream stream);
+
+/* M explicit saturation sub-steps of Eq. (ES) on the context's grid, upstream weighting of
+ * f_w at every face (the saturation of the cell the flow leaves), sources q_w = q_inj + f_w(S)
+ * w (p_bh - p): each sub-step takes dt = ds_max / max |dS/dt|, so no cell changes by more than
+ * ds_max.  v: 3 x n face velocities of msmg_velocity for the pressure p; w, q_inj, p_bh as in
+ * msmg_impes_pressure_terms; phi: n porosities (> 0); S: n saturations, updated in place.
+ * dt_host (may be NULL) receives the sum of the sub-steps' dt (the synchronising case).
+ * Uses the context's solve buffers as scratch (not during a solve on the same context). */
+int msmg_impes_transport(msmg_ctx* ctx, const msmg_fluid* fluid, const double* v, const double* p, const double* w,
+                         double p_bh, const double* q_inj, const double* phi, double* S, int M, double ds_max,
+                         double* dt_host, msmg_stream stream);
 
 /* Face coefficients T[d][cell] (d = x, y, z; face between cell and its +d neighbour,
  * zero on the boundary), FP64, natural order: device, 3 x (nx*ny*nz). */

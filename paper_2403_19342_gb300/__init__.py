@@ -55,7 +55,7 @@ class msmg_options(C.Structure):
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int), ("autotune", C.c_int),
                 ("warm_start", C.c_void_p), ("coarse_smoother", C.c_int), ("two_grid", C.c_int),
                 ("inner_rtol", C.c_double), ("inner_max_iter", C.c_int),
-                ("eig_threshold", C.c_double * MAX_LEVELS)]
+                ("eig_threshold", C.c_double * MAX_LEVELS), ("cell_diag", C.c_void_p)]
 
 
 class msmg_setup_info(C.Structure):
@@ -69,6 +69,10 @@ class msmg_setup_info(C.Structure):
 
 class msmg_net_desc(C.Structure):
     _fields_ = [("n_in", C.c_int), ("hidden", C.c_int * 2), ("n_vec", C.c_int), ("batch_max", C.c_int)]
+
+
+class msmg_fluid(C.Structure):
+    _fields_ = [("mu_w", C.c_double), ("mu_o", C.c_double), ("s_wc", C.c_double), ("s_or", C.c_double)]
 
 
 class msmg_solve_info(C.Structure):
@@ -125,6 +129,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_dot_noalloc": (I, [P, P, I64, C.POINTER(D), P]),
         "msmg_check_conversions": (I, [P, P, I64, P, P, P]),
         "msmg_velocity": (I, [P, P, P, P, C.POINTER(D), P]),
+        "msmg_impes_pressure_terms": (I, [I64, C.POINTER(msmg_fluid), P, P, P, P, D, P, P, P, P]),
+        "msmg_impes_transport": (I, [P, C.POINTER(msmg_fluid), P, P, P, D, P, P, P, I, D, C.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -144,7 +150,8 @@ def exported_symbols():
             "msmg_net_workspace_size", "msmg_net_create",
             "msmg_net_destroy", "msmg_net_param_count", "msmg_net_param_offsets", "msmg_net_get_params",
             "msmg_net_set_params", "msmg_net_forward", "msmg_net_gradients", "msmg_net_train_step",
-            "msmg_learning_data", "msmg_check_conversions", "msmg_velocity"]
+            "msmg_learning_data", "msmg_check_conversions", "msmg_velocity", "msmg_impes_pressure_terms",
+            "msmg_impes_transport"]
 
 
 def _check(status: int) -> int:
@@ -187,6 +194,7 @@ class Options:
     inner_rtol: float = 0.0            # P_TG inner tolerance (0: library default 1e-10)
     inner_max_iter: int = 0            # P_TG inner iteration cap (0: library default 200)
     eig_threshold: list = field(default_factory=list)   # Strategy 2: B per level (0: keep n_eig)
+    cell_diag: object = None           # CUDA FP64 tensor (nz, ny, nx) >= 0: well term W added to A
 
     def to_c(self) -> msmg_options:
         o = msmg_options()
@@ -213,6 +221,11 @@ class Options:
         o.inner_max_iter = self.inner_max_iter
         for i, v in enumerate(self.eig_threshold[:MAX_LEVELS]):
             o.eig_threshold[i] = v
+        if self.cell_diag is not None:
+            w = self.cell_diag
+            if not (isinstance(w, torch.Tensor) and w.is_cuda and w.dtype == torch.float64 and w.is_contiguous()):
+                raise TypeError("cell_diag: a contiguous CUDA float64 tensor of nz*ny*nx values")
+            o.cell_diag = w.data_ptr()
         return o
 
 
@@ -385,6 +398,43 @@ def msmg_velocity(ctx: int, p: torch.Tensor, f: torch.Tensor, v: torch.Tensor, s
     _check(load_library().msmg_velocity(ctx, _ptr(p, torch.float64), _ptr(f, torch.float64), _ptr(v, torch.float64),
                                         bal, _stream(stream)))
     return bal[0], bal[1]
+
+
+def make_fluid(mu_w: float = 0.3, mu_o: float = 3.0, s_wc: float = 0.2, s_or: float = 0.2) -> msmg_fluid:
+    """Section 6's fluid model (defaults: the paper's values)."""
+    f = msmg_fluid()
+    f.mu_w, f.mu_o, f.s_wc, f.s_or = mu_w, mu_o, s_wc, s_or
+    return f
+
+
+def msmg_impes_pressure_terms(fluid: msmg_fluid, S: torch.Tensor, kappa: torch.Tensor, wi: torch.Tensor,
+                              q_inj: torch.Tensor, p_bh: float, stream=None):
+    """(kappa_eff [3, ...], w, b) of the pressure system of Eq. (IMP) at saturation S."""
+    n = S.numel()
+    if kappa.numel() != 3 * n or wi.numel() != n or q_inj.numel() != n:
+        raise ValueError("S, wi, q_inj: n values; kappa: 3 n values")
+    ke = torch.empty_like(kappa)
+    w = torch.empty_like(S)
+    b = torch.empty_like(S)
+    _check(load_library().msmg_impes_pressure_terms(n, C.byref(fluid), _ptr(S, torch.float64), _ptr(kappa, torch.float64),
+                                                    _ptr(wi, torch.float64), _ptr(q_inj, torch.float64), p_bh,
+                                                    _ptr(ke), _ptr(w), _ptr(b), _stream(stream)))
+    return ke, w, b
+
+
+def msmg_impes_transport(ctx: int, fluid: msmg_fluid, v: torch.Tensor, p: torch.Tensor, w: torch.Tensor, p_bh: float,
+                         q_inj: torch.Tensor, phi: torch.Tensor, S: torch.Tensor, M: int, ds_max: float,
+                         stream=None) -> float:
+    """M saturation sub-steps of Eq. (ES) in place on S; returns the time they cover."""
+    n = S.numel()
+    if v.numel() != 3 * n or any(t.numel() != n for t in (p, w, q_inj, phi)):
+        raise ValueError("v: 3 n values; p, w, q_inj, phi, S: n values")
+    dt = C.c_double(0.0)
+    _check(load_library().msmg_impes_transport(ctx, C.byref(fluid), _ptr(v, torch.float64), _ptr(p, torch.float64),
+                                               _ptr(w, torch.float64), p_bh, _ptr(q_inj, torch.float64),
+                                               _ptr(phi, torch.float64), _ptr(S, torch.float64), M, ds_max,
+                                               C.byref(dt), _stream(stream)))
+    return dt.value
 
 
 def msmg_export_faces(ctx: int, out: torch.Tensor, stream=None) -> None:

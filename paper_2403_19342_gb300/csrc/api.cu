@@ -12,6 +12,7 @@ static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 
 void launch_mixed_copies(msmg_ctx* c, cudaStream_t s);
+void launch_cell_diag(msmg_ctx* c, const double* w_nat, cudaStream_t s);
 void launch_kept_sums(msmg_ctx* c, cudaStream_t s);
 void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s);
 int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess, float* block);
@@ -157,6 +158,10 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
     f.T32 = ar.take<float>(3 * n);
     f.invd32 = ar.take<float>(n);
     f.Phi32 = ar.take<float>(f.m * f.L * f.nb);
+  }
+  if (o->cell_diag) {
+    f.Wd = ar.take<double>(n);
+    if (mixed) f.Wd32 = ar.take<float>(n);
   }
   for (int l = 2; l <= nL; ++l) {
     CoarseLevel& lv = c->lev[l];
@@ -428,6 +433,7 @@ int msmg_setup(const msmg_grid* grid, const void* kappa, int kappa_components, i
   MSMG_CUDA_TRY(cudaMemsetAsync(c->dtmp, 0, 16 * sizeof(double), s));
   MSMG_CUDA_TRY(cudaMemsetAsync(c->red.counter, 0, (size_t)c->max_rhs * sizeof(unsigned), s));
   launch_faces(c, kappa, kappa_components, kappa_dtype, s);
+  if (opts->cell_diag) launch_cell_diag(c, opts->cell_diag, s);
   {
     // stop before any eigensolve when the permeability is not positive and finite
     int h0 = 0;

@@ -645,6 +645,7 @@ struct InnerArgs {
   float* out32;     // FP32 copy of the solution (mixed form) or null
   double rtol2;
   int max_iter;
+  int singular;     // A_2 has the constant's null vector (no cell term)
 };
 
 // (A_2 v)_i, i = (element a, coordinate k); v(j) returns the vector's entry j
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(kTailThreads) k_inner_pcg(TailArgs A, InnerArg
   for (int r = warp; r < R; r += NW) {
     const double zr = inner_total(I.part, ncta, R, r, 0, lane);
     const double zz = inner_total(I.part, ncta, R, r, 1, lane);
-    const double cz = zz > 0.0 ? zr / zz : 0.0;
+    const double cz = (I.singular && zz > 0.0) ? zr / zz : 0.0;
     double v = 0.0;
     for (int64_t i = row0 + lane; i < row1; i += 32) {
       const double t = fma(-cz, lv.z[i], rv[(int64_t)r * n2 + i]);
@@ -851,7 +852,7 @@ __global__ void __launch_bounds__(kTailThreads) k_inner_pcg(TailArgs A, InnerArg
     if (osc && osc[r].done) continue;
     const double zx = inner_total(I.part, ncta, R, r, 0, lane);
     const double zz = inner_total(I.part, ncta, R, r, 1, lane);
-    const double cz = zz > 0.0 ? zx / zz : 0.0;
+    const double cz = (I.singular && zz > 0.0) ? zx / zz : 0.0;
     for (int64_t i = row0 + lane; i < row1; i += 32) {
       const double xi = fma(-cz, lv.z[i], I.x[(int64_t)r * n2 + i]);
       I.x[(int64_t)r * n2 + i] = xi;
@@ -1089,6 +1090,7 @@ static const double* launch_inner(msmg_ctx* c, PcgScalars* sc, cudaStream_t s) {
   I.out32 = c->sb.ec32;
   I.rtol2 = c->opts.inner_rtol * c->opts.inner_rtol;
   I.max_iter = c->opts.inner_max_iter;
+  I.singular = c->fine.Wd == nullptr ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)c->inner_grid);
   cfg.blockDim = dim3(kTailThreads);

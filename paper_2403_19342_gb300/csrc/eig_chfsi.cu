@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(512, 2) k_eig_l1_chfsi(const double* __restric
                                                       int mdeg, int max_iter, double tol,
                                                       const float* __restrict__ guess, int guess_vecs,
                                                       float* __restrict__ block_out, double* __restrict__ Phi,
-                                                      double* __restrict__ lam, double* stats, int* flags) {
+                                                      double* __restrict__ lam, double* stats, int* flags,
+                                                      const double* __restrict__ Wd) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nb = bx * by * bz, bxy = bx * by;
   R* g = reinterpret_cast<R*>(smraw);
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(512, 2) k_eig_l1_chfsi(const double* __restric
     if (ly > 0) diag += Te[n + c - bx];
     if (lz < bz - 1) { const double t = Te[2 * n + c]; diag += t; w2 = t * isq * isq_s[c + bxy]; }
     if (lz > 0) diag += Te[2 * n + c - bxy];
+    if (Wd) diag += Wd[e * nb + c];   // cell term (wells), added to the left-hand form (Section 6)
     g[c] = (R)(diag * isq * isq);
     wx[c] = (R)w0; wy[c] = (R)w1; wz[c] = (R)w2;
   }
@@ -414,13 +416,13 @@ int launch_level1_chfsi(msmg_ctx* c, cudaStream_t s, const float* guess, float* 
     const double tol1 = tol > kMixedPhase1Tol ? tol : kMixedPhase1Tol;
     k_eig_l1_chfsi<float><<<(unsigned)f.m, thr, sm1, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, L, K, mdeg, max_iter,
                                                           tol1, guess, guess_vecs, block, nullptr, nullptr, c->dtmp,
-                                                          c->flags);
+                                                          c->flags, f.Wd);
   }
   const size_t sm = chfsi_smem(f.nb, K, sizeof(double));
   cudaFuncSetAttribute(k_eig_l1_chfsi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_eig_l1_chfsi<double><<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, L, K, mdeg, max_iter, tol,
                                                         block ? block : guess, block ? K : guess_vecs, nullptr, f.Phi,
-                                                        f.lam, c->dtmp, c->flags);
+                                                        f.lam, c->dtmp, c->flags, f.Wd);
   return 0;
 }
 

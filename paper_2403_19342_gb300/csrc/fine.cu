@@ -172,7 +172,7 @@ __global__ void k_faces(const KT* __restrict__ kappa, int comps, int nx, int ny,
 // d_c = a_cc - sum_{j < c, j ~ c in element} T^2 / d_j, a_cc = sum of the six face
 // coefficients.  Writes 1/d.  flags[1] <- 1 on a non-positive pivot.
 __global__ void k_pivots(const double* __restrict__ T, int64_t n, Geo g, int64_t m, const int* __restrict__ nbr,
-                         double* __restrict__ invd, double* __restrict__ D, int* flags) {
+                         const double* __restrict__ Wd, double* __restrict__ invd, double* __restrict__ D, int* flags) {
   extern __shared__ double smem[];
   const Slot s = make_slot(g, m, blockIdx.x);
   double* t0 = smem + (size_t)s.eloc * (3 * g.P + g.nb);
@@ -185,6 +185,7 @@ __global__ void k_pivots(const double* __restrict__ T, int64_t n, Geo g, int64_t
   const int sy = g.bx + 2, sz = (g.bx + 2) * (g.by + 2);
   double diag = 0.0;
   if (s.valid) diag = t0[c] + t0[c - 1] + t1[c] + t1[c - sy] + t2[c] + t2[c - sz];
+  if (s.valid && Wd) diag += Wd[s.e * g.nb + s.p];   // cell term (wells)
   const int smax = g.bx + g.by + g.bz - 3;
   const int sc = s.lx + s.ly + s.lz;
   for (int w = 0; w <= smax; ++w) {
@@ -233,7 +234,8 @@ __global__ void k_perm(const Tin* __restrict__ in, Tout* __restrict__ out, int64
 // and the PCG step length (finaliser).
 template <bool Reduce>
 __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, const double* __restrict__ T, int64_t n,
-                         Geo g, int64_t m, const int* __restrict__ nbr, RedSlot red, PcgScalars* sc, int R) {
+                         Geo g, int64_t m, const int* __restrict__ nbr, const double* __restrict__ Wd, RedSlot red,
+                         PcgScalars* sc, int R) {
   const BatchIdx bi = batch_idx(R);
   if (Reduce) sc += bi.r;
   if (Reduce && sc->done) return;
@@ -252,7 +254,8 @@ __global__ void k_matvec(const double* __restrict__ p, double* __restrict__ q, c
   __syncthreads();
   double v[1] = {0.0};
   if (s.valid) {
-    const double a = apply_A_cell(pt, t0, t1, t2, g, s.lx, s.ly, s.lz);
+    double a = apply_A_cell(pt, t0, t1, t2, g, s.lx, s.ly, s.lz);
+    if (Wd) a += Wd[s.e * g.nb + s.p] * pt[pad(g, s.lx, s.ly, s.lz)];   // cell term (wells)
     q[s.e * g.nb + s.p] = a;
     v[0] = a * pt[pad(g, s.lx, s.ly, s.lz)];
   }
@@ -291,8 +294,8 @@ void launch_pivots(msmg_ctx* c, cudaStream_t s) {
   const Geo g = fine_geo(c);
   const size_t sm = (size_t)g.epc * (3 * g.P + g.nb) * sizeof(double);
   cudaFuncSetAttribute(k_pivots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_pivots<<<fine_grid(c, g), fine_threads(g), sm, s>>>(c->fine.T, c->n, g, c->fine.m, c->fine.nbr, c->fine.invd,
-                                                         c->fine.D, c->flags);
+  k_pivots<<<fine_grid(c, g), fine_threads(g), sm, s>>>(c->fine.T, c->n, g, c->fine.m, c->fine.nbr, c->fine.Wd,
+                                                         c->fine.invd, c->fine.D, c->flags);
 }
 
 void launch_nat_to_blk(msmg_ctx* c, const double* in, double* out, cudaStream_t s) {
@@ -318,7 +321,18 @@ void launch_matvec(msmg_ctx* c, const double* p, double* q, cudaStream_t s, int 
   const size_t sm = (size_t)g.epc * 4 * g.P * sizeof(double);
   cudaFuncSetAttribute(k_matvec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_matvec<false><<<fine_grid(c, g) * R, fine_threads(g), sm, s>>>(p, q, c->fine.T, c->n, g, c->fine.m, c->fine.nbr,
-                                                                    c->red, nullptr, R);
+                                                                    c->fine.Wd, c->red, nullptr, R);
+}
+
+// The cell term W (wells) in block-major order; a negative or non-finite value
+// raises the same flag as a bad permeability.
+__global__ void k_check_nonneg(const double* __restrict__ w, int64_t n, int* flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !(w[i] >= 0.0 && w[i] < INFINITY)) atomicExch(&flags[0], 1);
+}
+void launch_cell_diag(msmg_ctx* c, const double* w_nat, cudaStream_t s) {
+  launch_nat_to_blk(c, w_nat, c->fine.Wd, s);
+  k_check_nonneg<<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>(c->fine.Wd, c->n, c->flags);
 }
 
 // ---- kernel timing (roofline figures)
@@ -483,6 +497,7 @@ void launch_mixed_copies(msmg_ctx* c, cudaStream_t s) {
   const int64_t n = c->n;
   cvt(c->fine.T, c->fine.T32, 3 * n);
   cvt(c->fine.invd, c->fine.invd32, n);
+  if (c->fine.Wd) cvt(c->fine.Wd, c->fine.Wd32, n);
   cvt(c->fine.Phi, c->fine.Phi32, c->fine.m * c->fine.L * c->fine.nb);
 }
 

@@ -336,6 +336,14 @@ __device__ __forceinline__ V w_apply_A_s(const WStage<V>& s, const G& g, int c) 
   return acc;
 }
 
+// The cell term of A (wells) times u_c from the staged tile; 0 without one.
+template <typename V, typename G>
+__device__ __forceinline__ V w_cell_term(const V* __restrict__ Wd, int64_t base, const V* ut, const G& g, int c) {
+  if (!Wd) return (V)0;
+  const int lx = c % g.bx, t = c / g.bx;
+  return __ldg(Wd + base + c) * ut[wpad(g, lx, t % g.by, t / g.by)];
+}
+
 // Cells of an 8^3 element by hyperplane lx + ly + lz = w (w = 0 .. 21), each plane in
 // (lz, ly) order; kPlane8Off[w] is the first entry of plane w.  With these, a
 // warp gives every lane at most two cells of the current plane (30 warp-steps
@@ -568,9 +576,9 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
 // L accumulators (the sum over each eigenvector's cells keeps its order).
 template <typename V, typename BT, typename G>
 __global__ void __launch_bounds__(stage_warps<restrict_layout<V>(), V>() * 32, sizeof(V) == 4 ? 7 : 1)
-    k_restrict(const V* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T, const BT* __restrict__ Phi,
-               int L, double* __restrict__ rc, int64_t nc, int64_t n, G g, int64_t m, const int* __restrict__ nbr,
-               const PcgScalars* sc, int R) {
+    k_restrict(const V* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T, const V* __restrict__ Wd,
+               const BT* __restrict__ Phi, int L, double* __restrict__ rc, int64_t nc, int64_t n, G g, int64_t m,
+               const int* __restrict__ nbr, const PcgScalars* sc, int R) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -604,7 +612,7 @@ __global__ void __launch_bounds__(stage_warps<restrict_layout<V>(), V>() * 32, s
 #pragma unroll
     for (int i = 0; i < kC; ++i) {
       const int c = lane + 32 * i;
-      if (i < ncl && c < g.nb) w[i] -= w_apply_A_s(s, g, c);
+      if (i < ncl && c < g.nb) w[i] -= w_apply_A_s(s, g, c) + w_cell_term(Wd, E.base, ut, g, c);
     }
   } else {
   // w -= A u: the six face coefficients of kG cells loaded before the products
@@ -638,6 +646,7 @@ __global__ void __launch_bounds__(stage_warps<restrict_layout<V>(), V>() * 32, s
       V acc = t0[j] * (uc - ut[pc + 1]) + mx[j] * (uc - ut[pc - 1]);
       acc += t1[j] * (uc - ut[pc + sy]) + my[j] * (uc - ut[pc - sy]);
       acc += t2[j] * (uc - ut[pc + sz]) + mz[j] * (uc - ut[pc - sz]);
+      if (Wd) acc += __ldg(Wd + E.base + c) * uc;   // cell term (wells)
       w[i0 + j] -= acc;
     }
   }
@@ -888,6 +897,7 @@ __global__ void __launch_bounds__(256) k_prolong4(float* __restrict__ u, const f
 template <typename V, typename BT, typename G, bool FUSE>
 __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(const V* __restrict__ f, const double* __restrict__ r,
                                                             const V* __restrict__ u, const V* __restrict__ T,
+                                                            const V* __restrict__ Wd,
                                                             const V* __restrict__ invd, const BT* __restrict__ Phi,
                                                             const V* __restrict__ ec, int L, int64_t nc,
                                                             double* __restrict__ z, const double* __restrict__ qv,
@@ -937,7 +947,7 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
 #pragma unroll
       for (int i = 0; i < kC; ++i) {
         const int c = lane + 32 * i;
-        if (i < ncl && c < g.nb) s.y[c] = fr[i] - w_apply_A_s(s, g, c);
+        if (i < ncl && c < g.nb) s.y[c] = fr[i] - (w_apply_A_s(s, g, c) + w_cell_term(Wd, base, s.ut, g, c));
       }
     }
     // r and q are needed only after the sweeps: their loads overlap them
@@ -978,7 +988,8 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
       w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
       __syncwarp();
     }
-    for (int c = lane; c < g.nb; c += 32) s.y[c] = __ldg(f + base + c) - w_apply_A_s(s, g, c);
+    for (int c = lane; c < g.nb; c += 32)
+      s.y[c] = __ldg(f + base + c) - (w_apply_A_s(s, g, c) + w_cell_term(Wd, base, s.ut, g, c));
     __syncwarp();
     w_ic0_s(s, g, lane, tab);
     for (int c = lane; c < g.nb; c += 32) {
@@ -1146,6 +1157,7 @@ struct FineOps {
   const V* T;
   const V* invd;
   const BT* Phi;
+  const V* Wd;     // cell term (wells) or null
 };
 
 template <int LAYOUT, typename V, typename G>
@@ -1186,7 +1198,7 @@ static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cud
   SolveBuffers& B = c->sb;
   constexpr int W = stage_warps<restrict_layout<V>(), V>();
   k_restrict<V, BT, G><<<fine_wgrid(c, W), W * 32, wsmem<restrict_layout<V>(), V>(g), s>>>(
-      (const V*)B.rv, (const V*)B.vu[1], o.T, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
+      (const V*)B.rv, (const V*)B.vu[1], o.T, o.Wd, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
       c->fine.nbr, sc, B.R);
 }
 
@@ -1197,11 +1209,11 @@ static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, const doub
   constexpr int W = stage_warps<kStageFull, V>();
   if (fuse)
     k_post<V, BT, G, true><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
-        (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
+        (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.Wd, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
         c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R);
   else
     k_post<V, BT, G, false><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
-        (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
+        (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.Wd, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
         c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R);
 }
 
@@ -1279,10 +1291,10 @@ static void vcycle_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, const dou
 static void pcg_step_vcycle_ev(msmg_ctx* c, int update, const double* qv, PcgScalars* sc, cudaStream_t s,
                                cudaEvent_t* ev) {
   if (c->opts.precision == MSMG_MIXED) {
-    FineOps<float, float> o{c->fine.T32, c->fine.invd32, c->fine.Phi32};
+    FineOps<float, float> o{c->fine.T32, c->fine.invd32, c->fine.Phi32, c->fine.Wd32};
     vcycle_t<float, float>(c, o, update, qv, sc, s, ev);
   } else {
-    FineOps<double, double> o{c->fine.T, c->fine.invd, c->fine.Phi};
+    FineOps<double, double> o{c->fine.T, c->fine.invd, c->fine.Phi, c->fine.Wd};
     vcycle_t<double, double>(c, o, update, qv, sc, s, ev);
   }
 }

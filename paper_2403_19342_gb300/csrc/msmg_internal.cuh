@@ -122,6 +122,8 @@ struct FineLevel {
   float* T32;                   // mixed-precision copies (nullptr in FP64 mode)
   float* invd32;
   float* Phi32;
+  double* Wd;                   // [n] cell term W of A (wells), block-major; nullptr: none
+  float* Wd32;                  // its FP32 copy (mixed form)
 };
 
 struct CoarseLevel {            // level l >= 2 (W_l)

@@ -43,6 +43,13 @@ struct msmg_net {
   float* wgt;                   // [batch_max][n_in] output weighting of the current batch
   float* loss;                  // [batch_max * n_vec + 32]
   int64_t step;
+  // tensor-core forward (tcgen05): layer widths multiples of 64
+  bool tc;
+  __nv_bfloat16* wt16;          // BF16 weights transposed, W_l^T [fan_out][fan_in], same offsets
+  __nv_bfloat16* xb;            // [batch_max][n_in] BF16 input (the products' A operand)
+  __nv_bfloat16* h1b;           // [batch_max][h1] BF16 activations
+  __nv_bfloat16* h2b;           // [batch_max][h2]
+  int* err;                     // device error word: a bounded tensor-core wait gave up
 };
 
 namespace msmg {
@@ -131,6 +138,189 @@ static void gemm(const TAe* A, int lda, const TBe* B, int ldb, float* C, int ldc
                  int K, cudaStream_t s) {
   dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
   k_gemm<TAe, TBe, TA, TB, EPI><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, bias, M, N, K);
+}
+
+// ------------------------------------------------------------------ tensor-core GEMM (tcgen05)
+// C[M][N] = epi(A[M][K] . Bt[N][K]^T (+ bias)), A and Bt BF16 with K contiguous,
+// FP32 accumulation in tensor memory (TMEM).  One CTA of 4 warps per 128 x 128
+// output tile; K in blocks of 64 staged in shared memory by all threads (two
+// stages), in the canonical K-major layout without swizzle: 8-row x 16-byte core
+// matrices, the two 8-element halves of a 16-wide K step 128 bytes apart, 8-row
+// groups 256 bytes apart, each 16-wide K step of a 128-row block a 4 KB sub-block.
+// One thread issues the four 128 x 128 x 16 MMAs of a block and commits them to
+// the stage's mbarrier; a stage is refilled once that mbarrier has fired.  The
+// epilogue reads the accumulator with tcgen05.ld (warp w: TMEM lanes 32w ..
+// 32w + 31 = rows), adds the bias, applies the ReLU and writes FP32 and, when
+// asked, a BF16 copy (the next layer's A operand).  Every wait is bounded: on
+// timeout the error word is set, the MMAs get a second bounded wait and the TMEM
+// is freed before the CTA returns.  K must be a multiple of 64 and the row
+// strides multiples of 8 elements (16-byte loads).
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
+constexpr int kTcStage = 2 * kTcM * kTcK * 2;          // A and B blocks of one stage: 32 KB
+constexpr size_t kTcSmem = 2 * (size_t)kTcStage + 1024;
+
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {
+  return (uint32_t)((k >> 4) * (kTcM * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+// shared-memory matrix descriptor: start, leading (K direction) and stride (8-row
+// groups) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tc_mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int EPI>   // 1: + bias; 2: + bias, ReLU
+__global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict__ A, int lda,
+                                                 const __nv_bfloat16* __restrict__ Bt, int ldb, float* __restrict__ C,
+                                                 int ldc, __nv_bfloat16* __restrict__ Cb, const float* __restrict__ bias,
+                                                 int M, int N, int K, int* err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ uint32_t tmem_slot;
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTcN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 0) {
+    tc_mbar_init(smem_u32(&bars[0]));
+    tc_mbar_init(smem_u32(&bars[1]));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const int nk = K / kTcK;
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+  for (int kb = 0; kb < nk && ok; ++kb) {
+    const int st = kb & 1;
+    unsigned char* sA = smem + st * kTcStage;
+    unsigned char* sB = sA + kTcStage / 2;
+    if (kb >= 2) {   // the MMAs that last read this stage are done
+      ok = tc_mbar_wait(smem_u32(&bars[st]), phase[st]);
+      phase[st] ^= 1u;
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+    }
+    // 128 rows x 64 values of A and of Bt: 16-byte chunks, 8 per row
+    for (int i = threadIdx.x; i < kTcM * (kTcK / 8); i += 128) {
+      const int r = i >> 3, kc = (i & 7) * 8;
+      uint4 va = make_uint4(0u, 0u, 0u, 0u), vb = make_uint4(0u, 0u, 0u, 0u);
+      if (m0 + r < M) va = *reinterpret_cast<const uint4*>(A + (int64_t)(m0 + r) * lda + kb * kTcK + kc);
+      if (n0 + r < N) vb = *reinterpret_cast<const uint4*>(Bt + (int64_t)(n0 + r) * ldb + kb * kTcK + kc);
+      *reinterpret_cast<uint4*>(sA + tc_off(r, kc)) = va;
+      *reinterpret_cast<uint4*>(sB + tc_off(r, kc)) = vb;
+    }
+    // the tensor core reads shared memory through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t idesc = tc_idesc(kTcM, kTcN);
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 16; ++kk) {
+        const uint64_t da = tc_desc(smem_u32(sA) + kk * kTcM * 32);
+        const uint64_t db = tc_desc(smem_u32(sB) + kk * kTcM * 32);
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&bars[st]))
+                   : "memory");
+    }
+  }
+  // the last commit covers every MMA this CTA issued
+  const int last = (nk - 1) & 1;
+  bool done = ok && tc_mbar_wait(smem_u32(&bars[last]), phase[last]);
+  done = __syncthreads_and(done);
+  if (!done) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 1);
+      tc_mbar_wait(smem_u32(&bars[last]), phase[last]);   // second bounded wait before freeing TMEM
+    }
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTcN; c0 += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col >= N) continue;
+          float x = __uint_as_float(v[j]);
+          if (EPI >= 1) x += bias[col];
+          if (EPI == 2) x = x > 0.f ? x : 0.f;
+          C[(int64_t)row * ldc + col] = x;
+          if (Cb) Cb[(int64_t)row * ldc + col] = __float2bfloat16(x);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcN));
+  }
+}
+
+template <int EPI>
+static void gemm_tc(const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, float* C, int ldc,
+                    __nv_bfloat16* Cb, const float* bias, int M, int N, int K, int* err, cudaStream_t s) {
+  dim3 grid((N + kTcN - 1) / kTcN, (M + kTcM - 1) / kTcM);
+  k_gemm_tc<EPI><<<grid, 128, kTcSmem, s>>>(A, lda, Bt, ldb, C, ldc, Cb, bias, M, N, K, err);
+}
+
+// BF16 copy of an FP32 matrix (the tensor-core A operand of layer 1)
+__global__ void k_bf16_copy(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16(a[i]);
+}
+// Wt[c][r] = bf16(W[r][c]) for a rows x cols FP32 matrix
+__global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols, __nv_bfloat16* __restrict__ Wt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)rows * cols) return;
+  const int r = (int)(i / cols), c = (int)(i % cols);
+  Wt[(int64_t)c * rows + r] = __float2bfloat16(W[i]);
 }
 
 // ------------------------------------------------------------------ output weighting
@@ -271,16 +461,40 @@ __global__ void k_init_uniform(float* __restrict__ w, int64_t n, uint64_t seed, 
 static inline unsigned g256(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 // ------------------------------------------------------------------ passes
+// The products' operands are BF16: the weights (the masters' BF16 copies) and
+// the activations (x, h1, h2 rounded to BF16 before the product that reads them);
+// accumulation and the stored activations are FP32.  With layer widths multiples
+// of 64 the products run on the tensor cores (tcgen05, k_gemm_tc), otherwise on
+// the CUDA cores (k_gemm) with the same operands.
+static void net_refresh_bf16(msmg_net* t, cudaStream_t s) {
+  const int64_t dims[4] = {t->d.n_in, t->d.hidden[0], t->d.hidden[1], t->n_out};
+  for (int l = 0; l < 3; ++l)
+    k_transpose_bf16<<<g256(dims[l] * dims[l + 1]), 256, 0, s>>>(t->w32 + t->off_w[l], (int)dims[l], (int)dims[l + 1],
+                                                                  t->wt16 + t->off_w[l]);
+}
+
 // forward for `batch` rows of x; output in net->out
 static void net_forward(msmg_net* t, const float* x, int batch, cudaStream_t s) {
   const msmg_net_desc& d = t->d;
   const int h1 = d.hidden[0], h2 = d.hidden[1], no = t->n_out;
-  gemm<float, __nv_bfloat16, false, false, 2>(x, d.n_in, t->w16 + t->off_w[0], h1, t->h1, h1, t->w32 + t->off_b[0],
-                                              batch, h1, d.n_in, s);
-  gemm<float, __nv_bfloat16, false, false, 2>(t->h1, h1, t->w16 + t->off_w[1], h2, t->h2, h2, t->w32 + t->off_b[1],
-                                              batch, h2, h1, s);
-  gemm<float, __nv_bfloat16, false, false, 1>(t->h2, h2, t->w16 + t->off_w[2], no, t->out, no, t->w32 + t->off_b[2],
-                                              batch, no, h2, s);
+  k_bf16_copy<<<g256((int64_t)batch * d.n_in), 256, 0, s>>>(x, t->xb, (int64_t)batch * d.n_in);
+  if (t->tc) {
+    gemm_tc<2>(t->xb, d.n_in, t->wt16 + t->off_w[0], d.n_in, t->h1, h1, t->h1b, t->w32 + t->off_b[0], batch, h1,
+               d.n_in, t->err, s);
+    gemm_tc<2>(t->h1b, h1, t->wt16 + t->off_w[1], h1, t->h2, h2, t->h2b, t->w32 + t->off_b[1], batch, h2, h1, t->err,
+               s);
+    gemm_tc<1>(t->h2b, h2, t->wt16 + t->off_w[2], h2, t->out, no, nullptr, t->w32 + t->off_b[2], batch, no, h2,
+               t->err, s);
+  } else {
+    gemm<__nv_bfloat16, __nv_bfloat16, false, false, 2>(t->xb, d.n_in, t->w16 + t->off_w[0], h1, t->h1, h1,
+                                                        t->w32 + t->off_b[0], batch, h1, d.n_in, s);
+    k_bf16_copy<<<g256((int64_t)batch * h1), 256, 0, s>>>(t->h1, t->h1b, (int64_t)batch * h1);
+    gemm<__nv_bfloat16, __nv_bfloat16, false, false, 2>(t->h1b, h1, t->w16 + t->off_w[1], h2, t->h2, h2,
+                                                        t->w32 + t->off_b[1], batch, h2, h1, s);
+    k_bf16_copy<<<g256((int64_t)batch * h2), 256, 0, s>>>(t->h2, t->h2b, (int64_t)batch * h2);
+    gemm<__nv_bfloat16, __nv_bfloat16, false, false, 1>(t->h2b, h2, t->w16 + t->off_w[2], no, t->out, no,
+                                                        t->w32 + t->off_b[2], batch, no, h2, s);
+  }
   k_out_weight<<<(unsigned)batch, 128, 0, s>>>(x, d.n_in, t->wgt);
   k_apply_weight<<<g256((int64_t)batch * no), 256, 0, s>>>(t->out, t->wgt, batch, d.n_vec, d.n_in);
 }
@@ -298,19 +512,22 @@ static void net_backward(msmg_net* t, const float* x, const float* target, int b
   k_apply_weight<<<g256((int64_t)batch * no), 256, 0, s>>>(t->d_out, t->wgt, batch, d.n_vec, d.n_in);
   float* g = t->grad;
   // layer 3: dW3 = h2^T d_out, db3, d_h2 = d_out W3^T (relu mask)
-  gemm<float, float, true, false, 0>(t->h2, h2, t->d_out, no, g + t->off_w[2], no, nullptr, h2, no, batch, s);
+  gemm<__nv_bfloat16, float, true, false, 0>(t->h2b, h2, t->d_out, no, g + t->off_w[2], no, nullptr, h2, no, batch,
+                                             s);
   k_colsum<<<g256(no), 256, 0, s>>>(t->d_out, batch, no, g + t->off_b[2]);
   gemm<float, __nv_bfloat16, false, true, 0>(t->d_out, no, t->w16 + t->off_w[2], no, t->d_h2, h2, nullptr, batch, h2,
                                              no, s);
   k_relu_back<<<g256((int64_t)batch * h2), 256, 0, s>>>(t->d_h2, t->h2, (int64_t)batch * h2);
   // layer 2
-  gemm<float, float, true, false, 0>(t->h1, h1, t->d_h2, h2, g + t->off_w[1], h2, nullptr, h1, h2, batch, s);
+  gemm<__nv_bfloat16, float, true, false, 0>(t->h1b, h1, t->d_h2, h2, g + t->off_w[1], h2, nullptr, h1, h2, batch,
+                                             s);
   k_colsum<<<g256(h2), 256, 0, s>>>(t->d_h2, batch, h2, g + t->off_b[1]);
   gemm<float, __nv_bfloat16, false, true, 0>(t->d_h2, h2, t->w16 + t->off_w[1], h2, t->d_h1, h1, nullptr, batch, h1,
                                              h2, s);
   k_relu_back<<<g256((int64_t)batch * h1), 256, 0, s>>>(t->d_h1, t->h1, (int64_t)batch * h1);
   // layer 1
-  gemm<float, float, true, false, 0>(x, d.n_in, t->d_h1, h1, g + t->off_w[0], h1, nullptr, d.n_in, h1, batch, s);
+  gemm<__nv_bfloat16, float, true, false, 0>(t->xb, d.n_in, t->d_h1, h1, g + t->off_w[0], h1, nullptr, d.n_in, h1,
+                                             batch, s);
   k_colsum<<<g256(h1), 256, 0, s>>>(t->d_h1, batch, h1, g + t->off_b[0]);
 }
 
@@ -356,6 +573,11 @@ static int64_t net_carve(const msmg_net_desc* d, Arena& ar, msmg_net* t) {
   float* dh1 = ar.take<float>(B * d->hidden[0]);
   float* loss = ar.take<float>(B * d->n_vec + 32);
   float* wgt = ar.take<float>(B * d->n_in);
+  __nv_bfloat16* wt16 = ar.take<__nv_bfloat16>(np);
+  __nv_bfloat16* xb = ar.take<__nv_bfloat16>(B * d->n_in);
+  __nv_bfloat16* h1b = ar.take<__nv_bfloat16>(B * d->hidden[0]);
+  __nv_bfloat16* h2b = ar.take<__nv_bfloat16>(B * d->hidden[1]);
+  int* err = ar.take<int>(4);
   if (t) {
     t->d = *d;
     t->n_out = no;
@@ -365,6 +587,8 @@ static int64_t net_carve(const msmg_net_desc* d, Arena& ar, msmg_net* t) {
     t->h1 = h1; t->h2 = h2; t->out = out; t->d_out = dout; t->d_h2 = dh2; t->d_h1 = dh1; t->loss = loss;
     t->wgt = wgt;
     t->step = 0;
+    t->wt16 = wt16; t->xb = xb; t->h1b = h1b; t->h2b = h2b; t->err = err;
+    t->tc = d->n_in % 64 == 0 && d->hidden[0] % 64 == 0 && d->hidden[1] % 64 == 0;
   }
   return np;
 }
@@ -420,6 +644,8 @@ void launch_net_features(msmg_ctx* c, float* x, const int* lex_of_hid, cudaStrea
   k_net_features<<<(unsigned)c->fine.m, 128, 0, s>>>(c->fine.S, c->fine.nb, c->fine.m, lex_of_hid, x);
 }
 
+int net_status(msmg_net* t, cudaStream_t s);
+
 // Guesses for every element, in chunks of the network's batch: g[e][k-1][c].
 int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream_t s) {
   msmg_net* t = const_cast<msmg_net*>(net);
@@ -433,6 +659,19 @@ int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream
                                   cudaMemcpyDeviceToDevice, s));
   }
   MSMG_CUDA_TRY(cudaGetLastError());
+  return net_status(t, s);
+}
+
+// MSMG_ERR_DEVICE_TIMEOUT when a tensor-core wait of the network's products gave up
+// (synchronises the stream; clears the word)
+int net_status(msmg_net* t, cudaStream_t s) {
+  int e = 0;
+  MSMG_CUDA_TRY(cudaMemcpyAsync(&e, t->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSMG_CUDA_TRY(cudaStreamSynchronize(s));
+  if (e) {
+    MSMG_CUDA_TRY(cudaMemsetAsync(t->err, 0, sizeof(int), s));
+    return MSMG_ERR_DEVICE_TIMEOUT;
+  }
   return 0;
 }
 
@@ -474,6 +713,10 @@ int msmg_net_create(const msmg_net_desc* desc, void* workspace, size_t workspace
                                            sqrtf(6.f / (float)dims[l]) * (l == 2 ? 0.25f : 1.f));
   }
   k_to_bf16<<<g256(t->n_param), 256, 0, s>>>(t->w32, t->w16, t->n_param);
+  net_refresh_bf16(t, s);
+  MSMG_CUDA_TRY(cudaMemsetAsync(t->err, 0, 4 * sizeof(int), s));
+  MSMG_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+  MSMG_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
   MSMG_CUDA_TRY(cudaGetLastError());
   *out = t;
   return 0;
@@ -501,6 +744,7 @@ int msmg_net_set_params(msmg_net* net, const float* params, msmg_stream stream) 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   MSMG_CUDA_TRY(cudaMemcpyAsync(net->w32, params, (size_t)net->n_param * sizeof(float), cudaMemcpyDeviceToDevice, s));
   k_to_bf16<<<g256(net->n_param), 256, 0, s>>>(net->w32, net->w16, net->n_param);
+  net_refresh_bf16(net, s);
   MSMG_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -515,7 +759,7 @@ int msmg_net_forward(msmg_net* net, const float* x, float* y, int batch, msmg_st
                                   cudaMemcpyDeviceToDevice, s));
   }
   MSMG_CUDA_TRY(cudaGetLastError());
-  return 0;
+  return net_status(net, s);
 }
 
 int msmg_net_gradients(msmg_net* net, const float* x, const float* target, int batch, float* grad, float* loss_host,
@@ -525,6 +769,10 @@ int msmg_net_gradients(msmg_net* net, const float* x, const float* target, int b
   net_backward(net, x, target, batch, s);
   if (grad)
     MSMG_CUDA_TRY(cudaMemcpyAsync(grad, net->grad, (size_t)net->n_param * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  {
+    const int st = net_status(net, s);
+    if (st) return st;
+  }
   if (loss_host) {
     const int nl = batch * net->d.n_vec;
     MSMG_CUDA_TRY(cudaMemcpyAsync(loss_host, net->loss + nl, sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -545,6 +793,11 @@ int msmg_net_train_step(msmg_net* net, const float* x, const float* target, int 
   const float c1 = 1.f - powf(b1, (float)net->step), c2 = 1.f - powf(b2, (float)net->step);
   k_adam<<<g256(net->n_param), 256, 0, s>>>(net->w32, net->w16, net->grad, net->adam_m, net->adam_v, net->n_param, lr,
                                             b1, b2, eps, c1, c2);
+  net_refresh_bf16(net, s);
+  {
+    const int st = net_status(net, s);
+    if (st) return st;
+  }
   if (loss_host) {
     const int nl = batch * net->d.n_vec;
     MSMG_CUDA_TRY(cudaMemcpyAsync(loss_host, net->loss + nl, sizeof(float), cudaMemcpyDeviceToHost, s));

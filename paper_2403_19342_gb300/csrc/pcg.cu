@@ -175,6 +175,7 @@ __global__ void k_set_scalars(PcgScalars* sc, int max_iter, int flexible, int R)
   sc[r].flexible = flexible;
   sc[r].done = 0;
   sc[r].iter = 0;
+  sc[r].mean = 0.0;   // stays 0 when A has a cell term (nonsingular: no mean to remove)
 }
 
 void launch_dot(const double* a, const double* b, int64_t n, RedSlot red, double* out, cudaStream_t s) {
@@ -262,7 +263,9 @@ struct PcgRun {
     flexible = c->opts.precision == MSMG_MIXED;
     vc_launches = 4 + 4 * (int64_t)(c->nL - 2) + 1;
     k_set_scalars<<<1, 32 * ((R + 31) / 32), 0, s>>>(sc, max_iter, flexible ? 1 : 0, R);
-    k_sum<<<vg, kVecThreads, 0, s>>>(B.b, n, c->red, &sc->mean, kScStride, 1.0 / (double)n, R);
+    // compatibility condition (Section 2.1) of the singular system; a cell term
+    // (wells) makes A nonsingular and the right-hand side is taken as it is
+    if (!c->fine.Wd) k_sum<<<vg, kVecThreads, 0, s>>>(B.b, n, c->red, &sc->mean, kScStride, 1.0 / (double)n, R);
     if (use_x0) {
       launch_matvec(c, B.x, B.q, s, R);
       k_init_x0<<<vg, kVecThreads, 0, s>>>(B.b, B.r, B.q, n, c->red, sc, rtol * rtol, R);
@@ -386,9 +389,11 @@ struct PcgRun {
           return restart_recurrence(max_iter - min_iter);
         }
         // zero-mean solution (uniqueness condition, Section 2.1)
-        k_sum<<<vg, kVecThreads, 0, s>>>(B.x, n, c->red, B.dres + 1, 2, 1.0, R);
-        k_sub_scalar<<<vg, kVecThreads, 0, s>>>(B.x, n, B.dres + 1, 2, 1.0 / (double)n, R);
-        launches += 2;
+        if (!c->fine.Wd) {
+          k_sum<<<vg, kVecThreads, 0, s>>>(B.x, n, c->red, B.dres + 1, 2, 1.0, R);
+          k_sub_scalar<<<vg, kVecThreads, 0, s>>>(B.x, n, B.dres + 1, 2, 1.0 / (double)n, R);
+          launches += 2;
+        }
         MSMG_CUDA_TRY(cudaEventRecord(c->poll_evs[2], s));
         phase = kFinal;
         return 0;

@@ -27,7 +27,7 @@ namespace msmg {
 // One CTA per element, nb <= 96.  stats[0] <- max eigen-residual.
 __global__ void k_eig_l1_jacobi(const double* __restrict__ T, const double* __restrict__ S, int64_t n, int bx, int by,
                                 int bz, int64_t m, int L, double* __restrict__ Phi, double* __restrict__ lam,
-                                double* stats) {
+                                double* stats, const double* __restrict__ Wd) {
   extern __shared__ double sm[];
   const int nb = bx * by * bz;
   double* A = sm;
@@ -60,6 +60,7 @@ __global__ void k_eig_l1_jacobi(const double* __restrict__ T, const double* __re
         A[c * nb + c - st[d]] = -t * isq[c] * isq[c - st[d]];
       }
     }
+    if (Wd) diag += Wd[e * nb + c];   // cell term (wells), added to the left-hand form (Section 6)
     A[c * nb + c] = diag * isq[c] * isq[c];
   }
   __syncthreads();
@@ -133,7 +134,7 @@ __global__ void k_kept_sum(const int* __restrict__ cnt, int64_t m, unsigned long
 __global__ void k_galerkin1(const double* __restrict__ T, const double* __restrict__ S, int64_t n, int bx, int by,
                             int bz, int64_t m, const int* __restrict__ nbr, int L, const double* __restrict__ Phi,
                             double* __restrict__ Ad, double* __restrict__ Ao, double* __restrict__ F,
-                            double* __restrict__ z, const int* __restrict__ cnt) {
+                            double* __restrict__ z, const int* __restrict__ cnt, const double* __restrict__ Wd) {
   extern __shared__ double sm[];
   const int nb = bx * by * bz;
   double* Ph = sm;            // [L][nb]
@@ -159,6 +160,7 @@ __global__ void k_galerkin1(const double* __restrict__ T, const double* __restri
     const int lc[3] = {c % bx, (c / bx) % by, c / (bx * by)};
     double diag = 0.0;
     for (int d = 0; d < 3; ++d) diag += T[(int64_t)d * n + a * nb + c] + Tm[d * nb + c];
+    if (Wd) diag += Wd[a * nb + c];   // cell term (wells)
     for (int k = 0; k < L; ++k) {
       double acc = diag * Ph[k * nb + c];
       for (int d = 0; d < 3; ++d) {
@@ -636,7 +638,7 @@ int launch_level1_eigen(msmg_ctx* c, cudaStream_t s) {
   const size_t sm = jac_smem(f.nb, 3);
   cudaFuncSetAttribute(k_eig_l1_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_eig_l1_jacobi<<<(unsigned)f.m, 256, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, f.L, f.Phi, f.lam,
-                                                  c->dtmp);
+                                                  c->dtmp, f.Wd);
   return 0;
 }
 
@@ -649,7 +651,7 @@ void launch_level1_galerkin(msmg_ctx* c, cudaStream_t s, bool threshold) {
   cudaFuncSetAttribute(k_galerkin1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const unsigned thr = f.nb >= 256 ? 256 : (unsigned)((f.nb + 31) / 32 * 32 < 64 ? 64 : (f.nb + 31) / 32 * 32);
   k_galerkin1<<<(unsigned)f.m, thr, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, f.nbr, f.L, f.Phi, l2.Ad, l2.Ao,
-                                             l2.F, l2.z, l2.cnt);
+                                             l2.F, l2.z, l2.cnt, f.Wd);
 }
 
 int launch_coarse_setup(msmg_ctx* c, int l, cudaStream_t s) {
@@ -718,17 +720,24 @@ int launch_coarsest(msmg_ctx* c, cudaStream_t s) {
     k_pack_vec<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(lv.z, lv.cmap, nk, lv.pinv + nk * nk);
     z = lv.pinv + nk * nk;
   }
-  k_coarsest_scalars<<<1, 256, 0, s>>>(B, z, nk, scal);
   const unsigned g2 = (unsigned)((nk * nk + 255) / 256);
-  k_add_null_shift<<<g2, 256, 0, s>>>(B, z, nk, scal);
   const unsigned g1 = (unsigned)((nk + 255) / 256);
+  const bool singular = c->fine.Wd == nullptr;   // a cell term (wells) removes the null space
+  if (singular) {
+    k_coarsest_scalars<<<1, 256, 0, s>>>(B, z, nk, scal);
+    k_add_null_shift<<<g2, 256, 0, s>>>(B, z, nk, scal);
+  }
   for (int64_t k = 0; k < nk; ++k) {
     k_gj_copy<<<g1, 256, 0, s>>>(B, nk, k, rowk, colk);
     k_gj_update<<<g2, 256, 0, s>>>(B, nk, k, rowk, colk, c->dtmp);
   }
-  k_gemv_z<<<(unsigned)((nk * 32 + 255) / 256), 256, 0, s>>>(B, z, nk, scal, w);
-  k_dot_zw<<<1, 256, 0, s>>>(z, w, nk, scal);
-  k_project<<<g2, 256, 0, s>>>(B, z, w, nk, scal, lv.pinv);
+  if (singular) {
+    k_gemv_z<<<(unsigned)((nk * 32 + 255) / 256), 256, 0, s>>>(B, z, nk, scal, w);
+    k_dot_zw<<<1, 256, 0, s>>>(z, w, nk, scal);
+    k_project<<<g2, 256, 0, s>>>(B, z, w, nk, scal, lv.pinv);
+  } else {
+    MSMG_CUDA_TRY(cudaMemcpyAsync(lv.pinv, B, (size_t)nk * nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   return 0;
 }
 

@@ -36,6 +36,7 @@ __global__ void k_vel_mean(const double* __restrict__ f, int64_t n, RedSlot red,
 // v[d][c] for the +d face of every cell c (natural order), and the balance
 // sums out[1] = sum_i (div_i - b_i)^2, out[2] = sum_i b_i^2, b = f - mean(f).
 __global__ void k_velocity(const double* __restrict__ p, const double* __restrict__ f, const double* __restrict__ T,
+                           const double* __restrict__ Wd,
                            int nx, int ny, int nz, double hx, double hy, double hz, int bx, int by, int bz,
                            const int* __restrict__ lex_of_hid, const int* __restrict__ nbr, int gx, int gy,
                            double* __restrict__ v, RedSlot red, double* out) {
@@ -76,7 +77,9 @@ __global__ void k_velocity(const double* __restrict__ p, const double* __restric
       }
       div += (vp - vm) / h[d];
     }
-    const double b = f[c] - mean;
+    // the cell's net source: f - mean (the singular system), or f - W p with a cell
+    // term (wells: the flow leaves through the well, not through a face)
+    const double b = Wd ? f[c] - Wd[i] * pc : f[c] - mean;
     acc[0] = fma(div - b, div - b, acc[0]);
     acc[1] = fma(b, b, acc[1]);
   }
@@ -99,7 +102,7 @@ extern "C" int msmg_velocity(msmg_ctx* c, const double* p, const double* f, doub
   const unsigned grid = vel_grid(c->n);
   RedSlot red = c->red;
   k_vel_mean<<<grid, kVelThreads, 0, s>>>(f, c->n, red, out);
-  k_velocity<<<grid, kVelThreads, 0, s>>>(p, f, F.T, c->grid.nx, c->grid.ny, c->grid.nz, c->grid.hx, c->grid.hy,
+  k_velocity<<<grid, kVelThreads, 0, s>>>(p, f, F.T, F.Wd, c->grid.nx, c->grid.ny, c->grid.nz, c->grid.hx, c->grid.hy,
                                           c->grid.hz, F.bx, F.by, F.bz, F.lex_of_hid, F.nbr, F.gx, F.gy, v, red,
                                           out);
   MSMG_CUDA_TRY(cudaGetLastError());
