@@ -15,6 +15,8 @@ flushed (256 MiB write) before every timed step.
   python bench.py --workload layered [--steps K] [--warmup W]
   python bench.py --workload scale [--steps K] [--warmup W] [--hierarchy stated]
   python bench.py --workload strategy2 [--steps K] [--warmup W]
+  python bench.py --workload network [--steps K] [--warmup W]
+  python bench.py --workload impes [--steps K] [--warmup W]
 
 The default line also carries ``batched_rhs``: the same workload with 16
 zero-mean random right-hand sides solved in one call (one launch sequence for
@@ -676,14 +678,14 @@ def run_layered(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        pkg.msmg_solve(solver.ctx, f, x, RTOL, 2000, 0)
+        pkg.msmg_solve(solver.ctx, f, x, RTOL, 6000, 0)
     torch.cuda.synchronize()
     ms, info = [], None
     for k in range(args.steps):
         flush.fill_(float(k))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        st, info = pkg.msmg_solve(solver.ctx, f, x, RTOL, 2000, 0)
+        st, info = pkg.msmg_solve(solver.ctx, f, x, RTOL, 6000, 0)
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
@@ -779,6 +781,135 @@ def run_strategy2(args, world, rank, local):
             "data": "synthetic", "config": {"workload": STRAT2_WORKLOAD, "form": "mixed",
                                              "l2": "flushed before each step (256 MiB write); working set > L2"},
             "runs": recs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+NET_WORKLOAD = ("warm-start network forward pass (the a16 products): 8192 level-1 elements of 8^3 cells, "
+                "512 -> 1024 -> 1024 -> 5 x 512 with ReLU, BF16 operands, FP32 accumulation; tensor cores "
+                "(tcgen05, widths multiples of 64) against the CUDA-core products (hidden widths 1000)")
+
+
+def run_network(args, world, rank, local):
+    """Forward throughput of the warm-start network: the tcgen05 products against
+    the CUDA-core products of a network of nearly the same size."""
+    import torch
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    _build.build()
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    B = 8192
+    stream = torch.cuda.current_stream()
+    x = torch.randn(B, 512, device="cuda", dtype=torch.float32) * 0.5
+    out = {}
+    for name, hidden in (("tensor_cores", (1024, 1024)), ("cuda_cores", (1000, 1000))):
+        net = pkg.WarmStartNet(n_in=512, hidden=hidden, n_vec=5, batch_max=B, seed=1)
+        for _ in range(max(1, args.warmup)):
+            net.forward(x)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            net.forward(x)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        flops = 2.0 * B * (512 * hidden[0] + hidden[0] * hidden[1] + hidden[1] * 5 * 512)
+        out[name] = {"ms_per_forward": ms, "tflops": flops / (ms * 1e-3) / 1e12, "hidden": list(hidden)}
+        net.close()
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    tc = out["tensor_cores"]
+    line = {"metric": "warm-start network forward TFLOP/s (BF16 operands, FP32 accumulation)", "value": tc["tflops"],
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tc["ms_per_forward"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic", "config": {"workload": NET_WORKLOAD, "batch": B},
+            "roofline": {"bound": "tensor", "achieved": tc["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": tc["tflops"] / peak, "peak_source": "measured cuBLAS bf16 burst"},
+            "forms": out, "speedup_over_cuda_cores": out["cuda_cores"]["ms_per_forward"] / tc["ms_per_forward"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+IMPES_WORKLOAD = ("two-phase IMPES (Section 6) on the SPE10 grid shape: 60 x 220 x 85 cells of 20 x 10 x 2 ft, "
+                  "85 layers of 60 x 220 lognormal lattices with sinuous channels (the layered recipe, seed 100), "
+                  "kappa_z = kappa_x / 10; porosity U(0.05, 0.3); producers at BHP 4000 in the four corner columns "
+                  "(well index of Section 6, r_w = 1 ft), an injector in the centre column; mu_w 0.3, mu_o 3.0, "
+                  "s_wc = s_or = 0.2; DS_max 0.001, M = 50 sub-steps; 4x4x5 elements, ratio (3, 5, 1), 3 levels, "
+                  "4 eigenvectors per local problem, mixed form, rtol 1e-9, pressure warm-started")
+
+
+def run_impes(args, world, rank, local):
+    """Pressure steps of the improved IMPES scheme: mobility terms, set-up, warm-started
+    solve, velocity and M saturation sub-steps per step, all in the library's kernels."""
+    import torch
+    import fields
+    import paper_2403_19342_gb300 as pkg
+    from paper_2403_19342_gb300 import build as _build
+    from math import log, pi, sqrt
+    _build.build()
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nz, ny, nx = 85, 220, 60
+    shape = (nz, ny, nx)
+    h = (20.0, 10.0, 2.0)
+    kx = fields.layered_channels(shape, seed=100)
+    kappa = torch.tensor(np.stack([kx, kx, 0.1 * kx]), device=dev)
+    rng = np.random.default_rng(100)
+    phi = torch.tensor(rng.uniform(0.05, 0.3, size=shape), device=dev)
+    r1 = sqrt(9 * h[0] ** 2 + h[1] ** 2) / 2
+    r2 = sqrt(h[0] ** 2 + 9 * h[1] ** 2) / 2
+    wi_val = (1 / h[0] ** 2 + 1 / h[1] ** 2) / ((2 / pi) * (h[1] / h[0] * log(r1) + h[0] / h[1] * log(r2)) - 1)
+    wi = torch.zeros(shape, dtype=torch.float64, device=dev)
+    for (j, i) in ((0, 0), (0, nx - 1), (ny - 1, 0), (ny - 1, nx - 1)):
+        wi[:, j, i] = wi_val
+    q = torch.zeros(shape, dtype=torch.float64, device=dev)
+    q[:, ny // 2, nx // 2] = 1.0e3
+    S = torch.full(shape, 0.2, dtype=torch.float64, device=dev)
+    fl = pkg.make_fluid()
+    p = None
+    steps = []
+    n = nx * ny * nz
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    n_steps = max(args.steps, 1) + max(args.warmup, 0)
+    for k in range(n_steps):
+        e = [ev() for _ in range(5)]
+        e[0].record(stream)
+        ke, w, b = pkg.msmg_impes_pressure_terms(fl, S, kappa, wi, q, 4000.0)
+        e[1].record(stream)
+        sol = pkg.Solver(ke, pkg.Options(n_levels=3, block=(4, 4, 5), ratio=[(3, 5, 1)], n_eig=[4, 4],
+                                         precision=pkg.MIXED, eig_tol=1e-8, cell_diag=w), h=h)
+        e[2].record(stream)
+        p, info, _ = sol.solve(b, rtol=1e-9, x0=p)
+        e[3].record(stream)
+        v, bal = sol.velocity(p, b)
+        dt = pkg.msmg_impes_transport(sol.ctx, fl, v, p, w, 4000.0, q, phi, S, 50, 1e-3)
+        e[4].record(stream)
+        torch.cuda.synchronize()
+        i0 = sol.info
+        sol.close()
+        steps.append({"iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
+                      "terms_ms": e[0].elapsed_time(e[1]), "setup_ms": e[1].elapsed_time(e[2]),
+                      "solve_ms": e[2].elapsed_time(e[3]), "velocity_transport_ms": e[3].elapsed_time(e[4]),
+                      "dt": dt, "S_max": float(S.max()), "balance": bal[0] / max(bal[1], 1e-300)})
+    timed = steps[max(args.warmup, 0):]
+    solve_ms = float(np.mean([s_["solve_ms"] for s_ in timed]))
+    step_ms = float(np.mean([s_["terms_ms"] + s_["setup_ms"] + s_["solve_ms"] + s_["velocity_transport_ms"]
+                             for s_ in timed]))
+    line = {"metric": "IMPES pressure-solve DOF/s (rtol 1e-9, warm start) and time per IMPES step", "value": n / (solve_ms * 1e-3),
+            "unit": "DOF/s", "n_gpus": world, "steps": len(timed), "warmup": max(args.warmup, 0),
+            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic", "config": {"workload": IMPES_WORKLOAD},
+            "steps_record": steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -885,7 +1016,7 @@ def main():
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--max-iter", type=int, default=4)
     ap.add_argument("--workload", default="inclusions",
-                    choices=["inclusions", "batched", "layered", "scale", "strategy2"])
+                    choices=["inclusions", "batched", "layered", "scale", "strategy2", "network", "impes"])
     ap.add_argument("--hierarchy", default="tuned", choices=["tuned", "stated"],
                     help="layered / scale: the tuned hierarchy or the one the configuration states")
     ap.add_argument("--tuning-cache", default=os.path.join(os.environ.get("TMPDIR", "/tmp"), "msmg_tuning.json"),
@@ -898,7 +1029,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, world, rank)
     run = {"batched": run_batched, "layered": run_layered, "scale": run_scale,
-           "strategy2": run_strategy2}.get(args.workload, run_gpu)
+           "strategy2": run_strategy2, "network": run_network, "impes": run_impes}.get(args.workload, run_gpu)
     rc = run(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist

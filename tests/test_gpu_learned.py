@@ -37,27 +37,43 @@ def layout(net):
     return (d.n_in, d.hidden[0], d.hidden[1], d.n_vec * d.n_in), w_off, b_off
 
 
-def test_forward_loss_gradients_match_oracle(pkg):
-    net = make_net(pkg)
+# Tolerances of the network against its oracle.  Both round every activation to
+# BF16 before the product that reads it, the library after an FP32 accumulation,
+# the oracle after an exact one; where the two straddle a BF16 rounding boundary
+# (about 20 FP32 ulps in 2^16, a few activations in 10^4) the next product's
+# operand differs by one BF16 ulp (2^-8 relative).  So outputs and loss agree to
+# about 1e-3 relative and the gradients, which multiply two such factors, to 1e-2.
+FWD_TOL, GRAD_TOL = 3e-3, 1e-2
+
+
+@pytest.mark.parametrize("hidden,batch", [((256, 128), 64), ((512, 512), 300), ((100, 60), 64)],
+                         ids=["tensor_cores", "tensor_cores_ragged", "cuda_cores"])
+def test_forward_loss_gradients_match_oracle(pkg, hidden, batch):
+    # widths multiples of 64 run the products on the tensor cores (tcgen05), others on
+    # the CUDA cores; both read BF16 operands and accumulate in FP32
+    net = make_net(pkg, hidden=hidden, batch_max=batch)
     dims, w_off, b_off = layout(net)
     rng = np.random.default_rng(0)
-    x = rng.normal(0, 0.5, size=(64, 512)).astype(np.float32)
-    t = rng.normal(size=(64, 5, 512))
+    x = rng.normal(0, 0.5, size=(batch, 512)).astype(np.float32)
+    t = rng.normal(size=(batch, 5, 512))
     t /= np.linalg.norm(t, axis=-1, keepdims=True)
-    t = t.reshape(64, -1).astype(np.float32)
+    t = t.reshape(batch, -1).astype(np.float32)
     params = net.get_params().cpu().numpy()
-    # forward: FP32 accumulation against FP64 with the same BF16 weights
+    # forward: FP32 accumulation against FP64 with the same BF16 operands
     out = net.forward(torch.tensor(x, device="cuda")).cpu().numpy()
     Ws, bs = learned.unpack(params, dims, w_off, b_off)
     _, _, ref_out = learned.forward(Ws, bs, x)
-    assert rel(out, ref_out) < 1e-5
+    e_fwd = rel(out, ref_out)
     loss, g = net.gradients(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"))
     ref_loss, ref_g = learned.gradients(params, dims, w_off, b_off, x, t, n_vec=5)
-    assert loss == pytest.approx(ref_loss, rel=1e-5)
     g = g.cpu().numpy()
-    for l in range(3):
-        for off, size in ((w_off[l], dims[l] * dims[l + 1]), (b_off[l], dims[l + 1])):
-            assert rel(g[off:off + size], ref_g[off:off + size]) < 1e-4, (l, off)
+    e_g = max(rel(g[off:off + size], ref_g[off:off + size]) for l in range(3)
+              for off, size in ((w_off[l], dims[l] * dims[l + 1]), (b_off[l], dims[l + 1])))
+    print(f"hidden {hidden} batch {batch}: forward rel. error {e_fwd:.2e}, loss {loss:.6f} vs {ref_loss:.6f}, "
+          f"worst gradient block {e_g:.2e}")
+    assert e_fwd < FWD_TOL
+    assert loss == pytest.approx(ref_loss, rel=FWD_TOL)
+    assert e_g < GRAD_TOL
     net.close()
 
 

@@ -120,3 +120,17 @@ def test_forward_hand_computed():
     ref = np.array([[-2.0 / np.sqrt(2.0), 6.0 / np.sqrt(2.0)],
                     [-2.0 * np.sqrt(e8 / (1.0 + e8)), 4.0 * np.sqrt(1.0 / (1.0 + e8))]])
     np.testing.assert_allclose(y, ref, rtol=1e-15, atol=0)
+
+
+def test_forward_rounds_activations_to_bf16():
+    # identity layers: the activations are the BF16 roundings of the inputs, worked by hand:
+    # 1/3 = 0x3EAAAAAB -> 0x3EAB = 0.333984375, 0.1 = 0x3DCCCCCD -> 0x3DCD = 0.10009765625
+    eye = np.eye(2)
+    params = np.concatenate([eye.ravel(), np.zeros(2)] * 3)
+    dims, w_off, b_off = (2, 2, 2, 2), [0, 6, 12], [4, 10, 16]
+    Ws, bs = learned.unpack(params, dims, w_off, b_off)
+    x = np.array([[1.0 / 3.0, 0.1]])
+    h1, h2, y = learned.forward(Ws, bs, x)
+    np.testing.assert_array_equal(h1, [[0.333984375, 0.10009765625]])
+    np.testing.assert_array_equal(h2, h1)
+    np.testing.assert_allclose(y, h1 * learned.out_weight(x), rtol=1e-15)
