@@ -54,6 +54,23 @@ static inline GeoR make_geor(int bx, int by, int bz) {
   return g;
 }
 
+template <typename G>
+struct IsCube8 : std::false_type {};
+template <>
+struct IsCube8<GeoC<8, 8, 8>> : std::true_type {};
+
+// Threads per element of the staged kernels: two warps for an 8^3 element in
+// the FP64 k_post (a wavefront has at most 48 cells, so each thread takes at
+// most one cell of it, and an SM keeps twice the warps for the same staged
+// bytes: 182 -> 168 us on 128^3), one warp otherwise (there the pair's
+// barriers cost more than the extra warps gain).  A two-warp element is a CTA
+// of its own, so that its barriers are the CTA's.
+constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2, kStageRestrictT = 3;
+template <int LAYOUT, typename G, typename V>
+__host__ __device__ constexpr int elem_threads() {
+  return IsCube8<G>::value && sizeof(V) == 8 && LAYOUT == kStageFull ? 64 : 32;
+}
+
 constexpr int kWarpsPerCta = 4;
 constexpr int kProlongLMax = 8;   // local basis sizes with all loads of a cell in flight at once
 
@@ -130,45 +147,89 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   return false;
 }
 
-// Completion of a warp's bulk copies, the same answer in every lane.  When the
-// bounded wait gives up, the error word is set (whatever path launched the
-// kernel), the right-hand side is marked as broken down, and the copies get a
-// second bounded wait before the warp skips its element: it then uses none of
-// the staged data.
-__device__ __forceinline__ bool bulk_landed(bool bulk, unsigned bar, PcgScalars* sc, int* err) {
-  const bool ok = __all_sync(0xffffffffu, !bulk || mbar_wait(bar, 0));
+// Barrier of the NT threads that work on one element: the warp, or the CTA
+// when the element has one to itself (NT > 32).
+template <int NT>
+__device__ __forceinline__ void ebar() {
+  if constexpr (NT == 32) __syncwarp();
+  else __syncthreads();
+}
+// AND of a predicate over the element's threads, the same answer in all of
+// them; also a barrier.
+template <int NT>
+__device__ __forceinline__ bool eall(bool p) {
+  if constexpr (NT == 32) {
+    const bool r = __all_sync(0xffffffffu, p);
+    __syncwarp();
+    return r;
+  } else {
+    return __syncthreads_and(p) != 0;
+  }
+}
+
+// Completion of an element's bulk copies, the same answer in all its threads.
+// When the bounded wait gives up, the error word is set (whatever path
+// launched the kernel), the right-hand side is marked as broken down, and the
+// copies get a second bounded wait before the threads skip the element: they
+// then use none of the staged data.
+template <int NT>
+__device__ __forceinline__ bool bulk_landed(bool bulk, unsigned bar, PcgScalars* sc, int* err, int et) {
+  const bool ok = eall<NT>(!bulk || mbar_wait(bar, 0));
   if (!ok) {
-    if ((threadIdx.x & 31) == 0) {
+    if (et == 0) {
       atomicExch(err, 1);
       if (sc) sc->done = 2;
     }
     mbar_wait(bar, 0);
   }
-  __syncwarp();
+  ebar<NT>();
   return ok;
 }
 
+// L2 prefetch (bulk, nothing waits for it) of bytes at p: 16-byte aligned,
+// a multiple of 16 bytes.
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+// The element (e2, right-hand side r2) that slot ``slot`` of the CTA ``pf``
+// places ahead will work on, if that CTA exists: with pf = the CTAs resident
+// at once, each wave's CTAs prefetch the next wave's arrays into L2 while they
+// compute.  k_post uses it for batched launches (many waves: 624 -> 536 us
+// at 16 right-hand sides on 128^3); at one right-hand side (two waves) it
+// cost 2 us, and the launch passes pf = 0.
+__device__ __forceinline__ bool ahead_elem(int pf, int R, int W, int slot, int64_t m, int64_t* e2, int* r2) {
+  if (pf <= 0) return false;
+  const unsigned b = blockIdx.x + (unsigned)pf;
+  if (b >= gridDim.x) return false;
+  *r2 = (int)(b % (unsigned)R);
+  *e2 = (int64_t)(b / (unsigned)R) * W + slot;
+  return *e2 < m;
+}
+
+// The staging helpers below are run by the NT threads of an element (lane =
+// the thread's index among them).
+
 // one element's chunk of an array; 16-byte copies when the chunk allows it
-template <typename V, typename G>
+template <int NT = 32, typename V, typename G>
 __device__ __forceinline__ void w_cp_array(V* dst, const V* __restrict__ src, const G& g, int lane) {
   if ((g.nb * (int)sizeof(V)) % 16 == 0) {
     constexpr int per = 16 / sizeof(V);
 #pragma unroll
-    for (int i = 0; i < (g.nb / per + 31) / 32; ++i) {
-      const int k = lane + 32 * i;
+    for (int i = 0; i < (g.nb / per + NT - 1) / NT; ++i) {
+      const int k = lane + NT * i;
       if (k < g.nb / per) cp_async_16(dst + k * per, src + k * per);
     }
   } else {
-    for (int i = lane; i < g.nb; i += 32) cp_async_elem(dst + i, src + i);
+    for (int i = lane; i < g.nb; i += NT) cp_async_elem(dst + i, src + i);
   }
 }
 
 // element interior into the padded tile
-template <typename V, typename G>
+template <int NT = 32, typename V, typename G>
 __device__ __forceinline__ void w_cp_padded(V* tile, const V* __restrict__ src, const G& g, int lane) {
 #pragma unroll
-  for (int i = 0; i < (g.nb + 31) / 32; ++i) {
-    const int c = lane + 32 * i;
+  for (int i = 0; i < (g.nb + NT - 1) / NT; ++i) {
+    const int c = lane + NT * i;
     if (c < g.nb) {
       const int lx = c % g.bx, t = c / g.bx;
       cp_async_elem(tile + wpad(g, lx, t % g.by, t / g.by), src + c);
@@ -177,14 +238,14 @@ __device__ __forceinline__ void w_cp_padded(V* tile, const V* __restrict__ src, 
 }
 
 // face halo f of X into the padded tile (zero on the domain boundary)
-template <typename V, typename G>
+template <int NT = 32, typename V, typename G>
 __device__ __forceinline__ void w_cp_face(V* tile, const V* __restrict__ X, const WElem& E, const G& g, int lane,
                                           int f) {
   const int d = f >> 1;
   const bool plus = f & 1;
   const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
   const int64_t nb = E.nb6[f];
-  for (int h = lane; h < F; h += 32) {
+  for (int h = lane; h < F; h += NT) {
     int dx, dy, dz, sx, sy, sz;
     if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
     else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
@@ -195,28 +256,28 @@ __device__ __forceinline__ void w_cp_face(V* tile, const V* __restrict__ X, cons
   }
 }
 
-template <typename V, typename G>
+template <int NT = 32, typename V, typename G>
 __device__ __forceinline__ void w_cp_halo(V* tile, const V* __restrict__ X, const WElem& E, const G& g, int lane) {
 #pragma unroll
-  for (int f = 0; f < 6; ++f) w_cp_face(tile, X, E, g, lane, f);
+  for (int f = 0; f < 6; ++f) w_cp_face<NT>(tile, X, E, g, lane, f);
 }
 
 // coefficients of the element's -d boundary faces (held by the -d neighbour)
-template <typename V, typename G>
+template <int NT = 32, typename V, typename G>
 __device__ __forceinline__ void w_cp_tminus(V* tm0, V* tm1, V* tm2, const V* __restrict__ T, int64_t n,
                                             const WElem& E, const G& g, int lane) {
-  for (int h = lane; h < g.by * g.bz; h += 32) {          // (ly, lz) = h, source lx = bx - 1
+  for (int h = lane; h < g.by * g.bz; h += NT) {          // (ly, lz) = h, source lx = bx - 1
     const int64_t nb = E.nb6[0];
     if (nb >= 0) cp_async_elem(tm0 + h, T + nb + (g.bx - 1) + g.bx * h);
     else tm0[h] = (V)0;
   }
-  for (int h = lane; h < g.bx * g.bz; h += 32) {          // (lx, lz), source ly = by - 1
+  for (int h = lane; h < g.bx * g.bz; h += NT) {          // (lx, lz), source ly = by - 1
     const int64_t nb = E.nb6[2];
     const int lx = h % g.bx, lz = h / g.bx;
     if (nb >= 0) cp_async_elem(tm1 + h, T + n + nb + lx + g.bx * ((g.by - 1) + g.by * lz));
     else tm1[h] = (V)0;
   }
-  for (int h = lane; h < g.bx * g.by; h += 32) {          // (lx, ly), source lz = bz - 1
+  for (int h = lane; h < g.bx * g.by; h += NT) {          // (lx, ly), source lz = bz - 1
     const int64_t nb = E.nb6[4];
     if (nb >= 0) cp_async_elem(tm2 + h, T + 2 * n + nb + h + g.bx * g.by * (g.bz - 1));
     else tm2[h] = (V)0;
@@ -226,7 +287,7 @@ __device__ __forceinline__ void w_cp_tminus(V* tm0, V* tm1, V* tm2, const V* __r
 // per-warp shared-memory carve of the staged working set; each kernel carves
 // only what it uses (more warps fit on an SM):
 //   kStageFull      u tile with halo, T, 1/d, y, -d face coefficients (k_post)
-//   kStagePre       T, 1/d, y, -d face coefficients             (k_pre)
+//   kStagePre       T, 1/d, y                                     (k_pre)
 //   kStageRestrict  u tile with halo                              (k_restrict FP32,
 //                   which reads its face coefficients into registers)
 //   kStageRestrictT u tile with halo, T, -d face coefficients     (k_restrict FP64,
@@ -235,19 +296,27 @@ template <typename V>
 struct WStage {
   V *ut, *t0, *t1, *t2, *tm0, *tm1, *tm2, *dinv, *y;
 };
-constexpr int kStageFull = 0, kStagePre = 1, kStageRestrict = 2, kStageRestrictT = 3;
 template <typename V>
 __host__ __device__ constexpr int restrict_layout() { return sizeof(V) == 8 ? kStageRestrictT : kStageRestrict; }
-// Warps (one element each) per CTA of the staged kernels: the CTA size that
-// keeps the most warps resident per SM for the staging footprint of an 8^3
-// element (FP32: 11 KB per warp for k_pre and k_restrict, 15 KB for k_post;
-// FP64 twice that), which also sets how many elements one wave covers.
-template <int LAYOUT, typename V>
-__host__ __device__ constexpr int stage_warps() {
+// Elements per CTA of the staged kernels: the CTA size that keeps the most
+// elements resident per SM for the staging footprint of an 8^3 element (FP32:
+// 10 KB for k_pre, 4 KB for k_restrict, 15 KB for k_post; FP64 twice that),
+// which also sets how many elements one wave covers.
+template <int LAYOUT, typename V, typename G = GeoR>
+__host__ __device__ constexpr int stage_elems() {
+  if (elem_threads<LAYOUT, G, V>() > 32) return 1;
   if (LAYOUT == kStageRestrict) return 4;
   if (LAYOUT == kStageRestrictT) return 2;
   if (sizeof(V) == 4) return LAYOUT == kStageFull ? 2 : 4;
   return LAYOUT == kStageFull ? 1 : 2;
+}
+// CTAs per SM the shared memory allows for k_post on 8^3 elements: the
+// register cap that keeps them all resident; 0 leaves the register count to
+// the compiler (an explicit minimum of 1 makes it take far more registers).
+template <int LAYOUT, typename V, typename G>
+__host__ __device__ constexpr int stage_min_ctas() {
+  if (!IsCube8<G>::value || LAYOUT != kStageFull) return 0;
+  return 7;
 }
 __host__ __device__ constexpr int r4(int x) { return (x + 3) / 4 * 4; }
 template <int LAYOUT, typename G>
@@ -255,7 +324,8 @@ __host__ __device__ inline int wstage_elems(const G& g) {
   if (LAYOUT == kStageRestrict) return r4(g.P);
   const int tut = LAYOUT == kStagePre ? 0 : r4(g.P);
   const int nv = LAYOUT == kStageRestrictT ? 3 : 5;
-  return tut + nv * r4(g.nb) + r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
+  const int tm = LAYOUT == kStagePre ? 0 : r4(g.by * g.bz) + r4(g.bx * g.bz) + r4(g.bx * g.by);
+  return tut + nv * r4(g.nb) + tm;
 }
 template <typename V, int LAYOUT = kStageFull, typename G>
 __device__ __forceinline__ WStage<V> w_stage(unsigned char* base, const G& g, int warp) {
@@ -271,6 +341,10 @@ __device__ __forceinline__ WStage<V> w_stage(unsigned char* base, const G& g, in
   if (LAYOUT != kStageRestrictT) {
     s.dinv = p; p += r4(g.nb);
     s.y = p; p += r4(g.nb);
+  }
+  if (LAYOUT == kStagePre) {   // k_pre's sweeps use no halo coefficients
+    s.tm0 = s.tm1 = s.tm2 = nullptr;
+    return s;
   }
   s.tm0 = p; p += r4(g.by * g.bz);
   s.tm1 = p; p += r4(g.bx * g.bz);
@@ -289,10 +363,11 @@ __device__ __forceinline__ void w_stage_T(const WStage<V>& s, const V* __restric
 }
 
 // The same with the four in-element arrays (T[0..2], 1/d) as bulk copies on the
-// warp's mbarrier ``bar`` (lane 0 issues them) where their size allows, the -d
-// halo coefficients (gathered from three neighbours) by per-lane copies when
-// asked for.  Returns whether the caller must wait on ``bar`` (phase 0).
-template <typename V, typename G>
+// element's mbarrier ``bar`` (its thread 0 issues them) where their size
+// allows, the -d halo coefficients (gathered from three neighbours) by
+// per-thread copies when asked for.  Returns whether the caller must wait on
+// ``bar`` (phase 0).
+template <int NT, typename V, typename G>
 __device__ __forceinline__ bool w_stage_T_bulk(const WStage<V>& s, const V* __restrict__ T,
                                                const V* __restrict__ invd, int64_t n, const WElem& E, const G& g,
                                                int lane, unsigned bar, bool with_tm) {
@@ -307,15 +382,15 @@ __device__ __forceinline__ bool w_stage_T_bulk(const WStage<V>& s, const V* __re
       bulk_g2s(s.t2, T + 2 * n + E.base, bytes, bar);
       bulk_g2s(s.dinv, invd + E.base, bytes, bar);
     }
-    // the other lanes poll the barrier only after lane 0 initialised it
-    __syncwarp();
+    // the other threads poll the barrier only after thread 0 initialised it
+    ebar<NT>();
   } else {
-    w_cp_array(s.t0, T + E.base, g, lane);
-    w_cp_array(s.t1, T + n + E.base, g, lane);
-    w_cp_array(s.t2, T + 2 * n + E.base, g, lane);
-    w_cp_array(s.dinv, invd + E.base, g, lane);
+    w_cp_array<NT>(s.t0, T + E.base, g, lane);
+    w_cp_array<NT>(s.t1, T + n + E.base, g, lane);
+    w_cp_array<NT>(s.t2, T + 2 * n + E.base, g, lane);
+    w_cp_array<NT>(s.dinv, invd + E.base, g, lane);
   }
-  if (with_tm) w_cp_tminus(s.tm0, s.tm1, s.tm2, T, n, E, g, lane);
+  if (with_tm) w_cp_tminus<NT>(s.tm0, s.tm1, s.tm2, T, n, E, g, lane);
   return bulk;
 }
 
@@ -345,9 +420,9 @@ __device__ __forceinline__ V w_cell_term(const V* __restrict__ Wd, int64_t base,
 }
 
 // Cells of an 8^3 element by hyperplane lx + ly + lz = w (w = 0 .. 21), each plane in
-// (lz, ly) order; kPlane8Off[w] is the first entry of plane w.  With these, a
-// warp gives every lane at most two cells of the current plane (30 warp-steps
-// per sweep instead of 44 with two fixed x-lines per lane).
+// (lz, ly) order; off[w] is the first entry of plane w.  With these, a warp
+// gives every lane at most two cells of the current plane (30 warp-steps per
+// sweep instead of 44 with two fixed x-lines per lane).
 struct Plane8 {
   unsigned short cell[512];
   unsigned short off[23];
@@ -368,23 +443,22 @@ constexpr Plane8 make_plane8() {
 }
 __device__ const Plane8 kPlane8 = make_plane8();
 
-template <typename G>
-struct IsCube8 : std::false_type {};
-template <>
-struct IsCube8<GeoC<8, 8, 8>> : std::true_type {};
-
-// The table is read at every wavefront step, so each CTA keeps a copy in shared
-// memory (after the warps' staging areas): a global read there would queue
-// behind the kernel's outstanding loads.
+// Which sweep a kernel runs on 8^3 elements: the plane table (k_pre, and the
+// FP64 k_post) or the unrolled fixed lines (the FP32 k_post, where it measured
+// faster).  The table is read at every wavefront step, so each CTA keeps a
+// copy in shared memory (after the elements' staging areas): a global read
+// there would queue behind the kernel's outstanding loads.
+template <int LAYOUT, typename V, typename G>
+__host__ __device__ constexpr bool plane_sweeps() {
+  return IsCube8<G>::value && (LAYOUT == kStagePre || (LAYOUT == kStageFull && sizeof(V) == 8));
+}
 constexpr int kPlaneShorts = 512 + 23;
 constexpr size_t kPlaneSmemBytes = 1088;
-template <typename G>
-__host__ __device__ constexpr size_t plane_smem(const G&) { return IsCube8<G>::value ? kPlaneSmemBytes : 0; }
 
 // copy the table (all threads of the CTA; ends with a CTA barrier); returns it
-template <typename G>
+template <bool TABLE>
 __device__ __forceinline__ const unsigned short* w_plane_table(unsigned char* at) {
-  if constexpr (IsCube8<G>::value) {
+  if constexpr (TABLE) {
     unsigned short* t = reinterpret_cast<unsigned short*>(at);
     const unsigned short* src = reinterpret_cast<const unsigned short*>(&kPlane8);
     for (int i = threadIdx.x; i < kPlaneShorts; i += blockDim.x) t[i] = src[i];
@@ -395,20 +469,26 @@ __device__ __forceinline__ const unsigned short* w_plane_table(unsigned char* at
 }
 
 // y <- M^{-1} y from the staged tiles, M = (D~ + L) D~^{-1} (D~ + L^T):
-// forward then backward wavefronts lx + ly + lz = w.  8^3 elements: the cells of
-// each plane are dealt to the lanes from kPlane8; other shapes: lane l owns the
-// lines l, l + 32, ... (line = ly + by * lz).  The arithmetic per cell is the same.
-template <typename V, typename G>
+// forward then backward wavefronts lx + ly + lz = w, run by the element's NT
+// threads.  With the table (8^3 elements): the cells of each plane are dealt
+// to the threads.  Otherwise thread l owns the x-lines l, l + NT, ... (line =
+// ly + by * lz), so at wavefront w it updates cell lx = w - ly - lz of each of
+// its lines; on 8^3 elements the 22 wavefronts are unrolled, which makes every
+// address an immediate offset from the line's base (cell = 7 ly + 63 lz + w),
+// and the x-neighbour is the value the thread produced at the previous
+// wavefront (kept in a register).  The arithmetic per cell is the same in all
+// forms.
+template <int NT, bool TABLE, typename V, typename G>
 __device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane, const unsigned short* tab) {
-  if constexpr (IsCube8<G>::value) {
+  V* y = s.y;
+  if constexpr (TABLE) {
     const unsigned short* cell = tab;
     const unsigned short* off = tab + 512;
-    V* y = s.y;
     for (int w = 0; w <= 21; ++w) {
       const int o0 = off[w], o1 = off[w + 1];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int k = o0 + lane + 32 * j;
+      for (int j = 0; j < (48 + NT - 1) / NT; ++j) {
+        const int k = o0 + lane + NT * j;
         if (k >= o1) continue;
         const int c = cell[k];
         const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
@@ -418,13 +498,13 @@ __device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane
         if (lz > 0) acc += s.t2[c - 64] * y[c - 64];
         y[c] = acc * s.dinv[c];
       }
-      __syncwarp();
+      ebar<NT>();
     }
     for (int w = 21; w >= 0; --w) {
       const int o0 = off[w], o1 = off[w + 1];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int k = o0 + lane + 32 * j;
+      for (int j = 0; j < (48 + NT - 1) / NT; ++j) {
+        const int k = o0 + lane + NT * j;
         if (k >= o1) continue;
         const int c = cell[k];
         const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
@@ -434,17 +514,69 @@ __device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane
         if (lz < 7) acc += s.t2[c] * y[c + 64];
         y[c] += s.dinv[c] * acc;
       }
-      __syncwarp();
+      ebar<NT>();
+    }
+    return;
+  } else if constexpr (IsCube8<G>::value) {
+    constexpr int LPT = 64 / NT;              // lines per thread
+    int base[LPT], off[LPT];
+    bool hy[LPT], hz[LPT], ty[LPT], tz[LPT];
+    V prev[LPT];
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+      const int l = lane + NT * j, ly = l & 7, lz = l >> 3;
+      base[j] = 7 * ly + 63 * lz;
+      off[j] = ly + lz;
+      hy[j] = ly > 0;
+      hz[j] = lz > 0;
+      ty[j] = ly < 7;
+      tz[j] = lz < 7;
+      prev[j] = (V)0;
+    }
+#pragma unroll
+    for (int w = 0; w <= 21; ++w) {
+#pragma unroll
+      for (int j = 0; j < LPT; ++j) {
+        const int lx = w - off[j];
+        if ((unsigned)lx < 8u) {
+          const int c = base[j] + w;
+          V acc = y[c];
+          if (lx > 0) acc += s.t0[c - 1] * prev[j];
+          if (hy[j]) acc += s.t1[c - 8] * y[c - 8];
+          if (hz[j]) acc += s.t2[c - 64] * y[c - 64];
+          acc = acc * s.dinv[c];
+          y[c] = acc;
+          prev[j] = acc;
+        }
+      }
+      ebar<NT>();
+    }
+#pragma unroll
+    for (int w = 21; w >= 0; --w) {
+#pragma unroll
+      for (int j = 0; j < LPT; ++j) {
+        const int lx = w - off[j];
+        if ((unsigned)lx < 8u) {
+          const int c = base[j] + w;
+          V acc = (V)0;
+          if (lx < 7) acc += s.t0[c] * prev[j];
+          if (ty[j]) acc += s.t1[c] * y[c + 8];
+          if (tz[j]) acc += s.t2[c] * y[c + 64];
+          const V v = y[c] + s.dinv[c] * acc;
+          y[c] = v;
+          prev[j] = v;
+        }
+      }
+      ebar<NT>();
     }
     return;
   }
   const int smax = g.bx + g.by + g.bz - 3;
   const int bxy = g.bx * g.by;
-  V* y = s.y;
   for (int w = 0; w <= smax; ++w) {
 #pragma unroll
-    for (int i = 0; i < (g.nlines + 31) / 32; ++i) {
-      const int l = lane + 32 * i;
+    for (int i = 0; i < (g.nlines + NT - 1) / NT; ++i) {
+      const int l = lane + NT * i;
       if (l >= g.nlines) continue;
       const int ly = l % g.by, lz = l / g.by;
       const int lx = w - ly - lz;
@@ -456,12 +588,12 @@ __device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane
       if (lz > 0) acc += s.t2[c - bxy] * y[c - bxy];
       y[c] = acc * s.dinv[c];
     }
-    __syncwarp();
+    ebar<NT>();
   }
   for (int w = smax; w >= 0; --w) {
 #pragma unroll
-    for (int i = 0; i < (g.nlines + 31) / 32; ++i) {
-      const int l = lane + 32 * i;
+    for (int i = 0; i < (g.nlines + NT - 1) / NT; ++i) {
+      const int l = lane + NT * i;
       if (l >= g.nlines) continue;
       const int ly = l % g.by, lz = l / g.by;
       const int lx = w - ly - lz;
@@ -473,7 +605,7 @@ __device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane
       if (lz < g.bz - 1) acc += s.t2[c] * y[c + bxy];
       y[c] += s.dinv[c] * acc;
     }
-    __syncwarp();
+    ebar<NT>();
   }
 }
 
@@ -481,7 +613,8 @@ __device__ __forceinline__ void w_ic0_s(const WStage<V>& s, const G& g, int lane
 // update != 0: x += alpha p, r -= alpha q, rr = r.r (convergence bookkeeping);
 // then f = r (in V precision, also written to rv) and u = M^{-1} f.
 template <typename V, typename G>
-__global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double* __restrict__ x, double* __restrict__ r,
+__global__ void __launch_bounds__(stage_elems<kStagePre, V, G>() * elem_threads<kStagePre, G, V>(),
+                                  stage_min_ctas<kStagePre, V, G>()) k_pre(double* __restrict__ x, double* __restrict__ r,
                                                            const double* __restrict__ p, const double* __restrict__ q,
                                                            const V* __restrict__ T, const V* __restrict__ invd,
                                                            V* __restrict__ rv, V* __restrict__ u, int64_t n, G g,
@@ -495,30 +628,33 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
     x += off; r += off; p += off; q += off; rv += off; u += off;
   }
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int W = stage_warps<kStagePre, V>();
-  const int64_t e = (int64_t)bi.blk * W + warp;
+  constexpr int NT = elem_threads<kStagePre, G, V>();
+  const int lane = threadIdx.x % NT, slot = threadIdx.x / NT;   // thread in the element, element in the CTA
+  constexpr int W = stage_elems<kStagePre, V, G>();
+  static_assert(NT == 32 || W == 1, "a two-warp element is a CTA of its own");
+  const int64_t e = (int64_t)bi.blk * W + slot;
   const bool act = e < m;
-  const WStage<V> s = w_stage<V, kStagePre>(smem, g, warp);
-  const unsigned short* tab = w_plane_table<G>(smem + (size_t)W * wstage_elems<kStagePre>(g) * sizeof(V));
-  __shared__ __align__(8) unsigned long long s_bar[W];   // one mbarrier per warp
-  const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp]);
+  const WStage<V> s = w_stage<V, kStagePre>(smem, g, slot);
+  __shared__ __align__(8) unsigned long long s_bar[W];   // one mbarrier per element
+  const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[slot]);
+  constexpr bool TABLE = plane_sweeps<kStagePre, V, G>();
+  const unsigned short* tab = w_plane_table<TABLE>(smem + (size_t)W * wstage_elems<kStagePre>(g) * sizeof(V));
   double acc = 0.0;
   if (act) {
     const WElem E = w_elem(e, nbr, g);
     // the element's face coefficients and inverse pivots (the sweeps use no
     // halo coefficients)
-    const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, false);
+    const bool bulk = w_stage_T_bulk<NT>(s, T, invd, n, E, g, lane, bar, false);
     const double alpha = update ? sc->alpha : 0.0;
     const int64_t base = E.base;
-    // batches of 8 cells per lane: all loads of a batch are issued before use
-    constexpr int kB = 8;
-    const int ncl = (g.nb + 31) / 32;
+    // batches of kB cells per thread: all loads of a batch are issued before use
+    constexpr int kB = NT == 64 ? 4 : 8;
+    const int ncl = (g.nb + NT - 1) / NT;
     for (int b0 = 0; b0 < ncl; b0 += kB) {
       double rr[kB], qq[kB], xx[kB], pp[kB];
 #pragma unroll
       for (int i = 0; i < kB; ++i) {
-        const int c = lane + 32 * (b0 + i);
+        const int c = lane + NT * (b0 + i);
         const bool in = b0 + i < ncl && c < g.nb;
         rr[i] = in ? r[base + c] : 0.0;
         qq[i] = (in && update) ? q[base + c] : 0.0;
@@ -527,7 +663,7 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
       }
 #pragma unroll
       for (int i = 0; i < kB; ++i) {
-        const int c = lane + 32 * (b0 + i);
+        const int c = lane + NT * (b0 + i);
         if (!(b0 + i < ncl && c < g.nb)) continue;
         double rc = rr[i];
         if (update) {
@@ -545,11 +681,11 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
     }
     cp_async_wait_all();
     do {   // left early when the staged data never landed
-    if (!bulk_landed(bulk, bar, sc, err)) break;
-    w_ic0_s(s, g, lane, tab);
+    if (!bulk_landed<NT>(bulk, bar, sc, err, lane)) break;
+    w_ic0_s<NT, TABLE>(s, g, lane, tab);
 #pragma unroll 4
-    for (int i = 0; i < (g.nb + 31) / 32; ++i) {
-      const int c = lane + 32 * i;
+    for (int i = 0; i < (g.nb + NT - 1) / NT; ++i) {
+      const int c = lane + NT * i;
       if (c < g.nb) u[base + c] = s.y[c];
     }
     } while (0);
@@ -575,7 +711,7 @@ __global__ void __launch_bounds__(stage_warps<kStagePre, V>() * 32) k_pre(double
 // one wave.  The basis loads of all eigenvectors are issued cell by cell into
 // L accumulators (the sum over each eigenvector's cells keeps its order).
 template <typename V, typename BT, typename G>
-__global__ void __launch_bounds__(stage_warps<restrict_layout<V>(), V>() * 32, sizeof(V) == 4 ? 7 : 1)
+__global__ void __launch_bounds__(stage_elems<restrict_layout<V>(), V>() * 32, sizeof(V) == 4 ? 7 : 1)
     k_restrict(const V* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T, const V* __restrict__ Wd,
                const BT* __restrict__ Phi, int L, double* __restrict__ rc, int64_t nc, int64_t n, G g, int64_t m,
                const int* __restrict__ nbr, const PcgScalars* sc, int R) {
@@ -589,7 +725,7 @@ __global__ void __launch_bounds__(stage_warps<restrict_layout<V>(), V>() * 32, s
   constexpr int kC = 16;                                   // cells per lane held in registers
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int LAY = restrict_layout<V>();
-  const int64_t e = (int64_t)bi.blk * stage_warps<LAY, V>() + warp;
+  const int64_t e = (int64_t)bi.blk * stage_elems<LAY, V>() + warp;
   if (e >= m) return;
   const WStage<V> s = w_stage<V, kStageRestrictT>(smem, g, warp);   // used in the FP64 layout only
   V* ut = LAY == kStageRestrictT ? s.ut : reinterpret_cast<V*>(smem) + (size_t)warp * r4(g.P);
@@ -721,13 +857,13 @@ __device__ __forceinline__ V w_coarse_corr(const BT* __restrict__ ph, const V* _
   return acc;
 }
 
-template <typename V, typename BT, typename G>
+template <int NT, typename V, typename BT, typename G>
 __device__ __forceinline__ void w_prolong_tile(V* ut, const BT* __restrict__ Phi, const V* __restrict__ ec, int L,
                                                int64_t e, const WElem& E, const G& g, int lane) {
   if (L > kProlongLMax) {
     const V* en = ec + e * L;
     const BT* ph = Phi + (size_t)e * L * g.nb;
-    for (int c = lane; c < g.nb; c += 32) {
+    for (int c = lane; c < g.nb; c += NT) {
       const int lx = c % g.bx, t = c / g.bx;
       ut[wpad(g, lx, t % g.by, t / g.by)] += w_coarse_corr(ph, en, L, g.nb, c);
     }
@@ -738,7 +874,7 @@ __device__ __forceinline__ void w_prolong_tile(V* ut, const BT* __restrict__ Phi
       const int d = f >> 1;
       const bool plus = f & 1;
       const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
-      for (int h = lane; h < F; h += 32) {
+      for (int h = lane; h < F; h += NT) {
         int dx, dy, dz, sx, sy, sz;
         if (d == 0) { const int uu = h % g.by, vv = h / g.by; dy = sy = uu; dz = sz = vv; dx = plus ? g.bx : -1; sx = plus ? 0 : g.bx - 1; }
         else if (d == 1) { const int uu = h % g.bx, vv = h / g.bx; dx = sx = uu; dz = sz = vv; dy = plus ? g.by : -1; sy = plus ? 0 : g.by - 1; }
@@ -754,13 +890,13 @@ __device__ __forceinline__ void w_prolong_tile(V* ut, const BT* __restrict__ Phi
   for (int k = 0; k < kProlongLMax; ++k) ev[k] = k < L ? ec[e * L + k] : (V)0;
   {
     const BT* ph = Phi + (size_t)e * L * g.nb;
-    const int ncl = (g.nb + 31) / 32;
+    const int ncl = (g.nb + NT - 1) / NT;
     for (int i0 = 0; i0 < ncl; i0 += 4) {
       int src[4], dst[4];
       int cnt = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int c = lane + 32 * (i0 + j);
+        const int c = lane + NT * (i0 + j);
         src[j] = c;
         dst[j] = 0;
         if (i0 + j < ncl && c < g.nb) {
@@ -783,12 +919,12 @@ __device__ __forceinline__ void w_prolong_tile(V* ut, const BT* __restrict__ Phi
     const int d = f >> 1;
     const bool plus = f & 1;
     const int F = d == 0 ? g.by * g.bz : (d == 1 ? g.bx * g.bz : g.bx * g.by);
-    for (int h0 = 0; h0 < F; h0 += 4 * 32) {
+    for (int h0 = 0; h0 < F; h0 += 4 * NT) {
       int src[4], dst[4];
       int cnt = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int h = h0 + lane + 32 * j;
+        const int h = h0 + lane + NT * j;
         src[j] = 0;
         dst[j] = 0;
         if (h < F) {
@@ -895,14 +1031,15 @@ __global__ void __launch_bounds__(256) k_prolong4(float* __restrict__ u, const f
 // z = u + M^{-1} (f - A u), written in FP64; reductions: r.z and z.q (flexible
 // beta).  f, r and q are loaded into registers before the wavefronts start.
 template <typename V, typename BT, typename G, bool FUSE>
-__global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(const V* __restrict__ f, const double* __restrict__ r,
+__global__ void __launch_bounds__(stage_elems<kStageFull, V, G>() * elem_threads<kStageFull, G, V>(),
+                                  stage_min_ctas<kStageFull, V, G>()) k_post(const V* __restrict__ f, const double* __restrict__ r,
                                                             const V* __restrict__ u, const V* __restrict__ T,
                                                             const V* __restrict__ Wd,
                                                             const V* __restrict__ invd, const BT* __restrict__ Phi,
                                                             const V* __restrict__ ec, int L, int64_t nc,
                                                             double* __restrict__ z, const double* __restrict__ qv,
                                                             int64_t n, G g, int64_t m, const int* __restrict__ nbr,
-                                                            RedSlot red, PcgScalars* sc, int* err, int R) {
+                                                            RedSlot red, PcgScalars* sc, int* err, int R, int pf) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -913,40 +1050,60 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
     ec += (int64_t)bi.r * nc;
   }
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int kC = 16;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int W = stage_warps<kStageFull, V>();
-  const int64_t e = (int64_t)bi.blk * W + warp;
+  constexpr int NT = elem_threads<kStageFull, G, V>();
+  constexpr int kC = 512 / NT;                 // cells per thread held in registers
+  const int lane = threadIdx.x % NT, slot = threadIdx.x / NT;   // thread in the element, element in the CTA
+  constexpr int W = stage_elems<kStageFull, V, G>();
+  static_assert(NT == 32 || W == 1, "a two-warp element is a CTA of its own");
+  const int64_t e = (int64_t)bi.blk * W + slot;
   const bool act = e < m;
-  const WStage<V> s = w_stage<V>(smem, g, warp);
-  const unsigned short* tab = w_plane_table<G>(smem + (size_t)W * wstage_elems<kStageFull>(g) * sizeof(V));
-  __shared__ __align__(8) unsigned long long s_bar[W];   // one mbarrier per warp
-  const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[warp]);
-  const int ncl = (g.nb + 31) / 32;
+  const WStage<V> s = w_stage<V>(smem, g, slot);
+  __shared__ __align__(8) unsigned long long s_bar[W];   // one mbarrier per element
+  const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[slot]);
+  constexpr bool TABLE = plane_sweeps<kStageFull, V, G>();
+  const unsigned short* tab = w_plane_table<TABLE>(smem + (size_t)W * wstage_elems<kStageFull>(g) * sizeof(V));
+  const int ncl = (g.nb + NT - 1) / NT;
   double v[2] = {0.0, 0.0};
   if (act && ncl <= kC) {
     const WElem E = w_elem(e, nbr, g);
     const int64_t base = E.base;
-    w_cp_padded(s.ut, u + base, g, lane);
-    w_cp_halo(s.ut, u, E, g, lane);
-    const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, true);
+    w_cp_padded<NT>(s.ut, u + base, g, lane);
+    w_cp_halo<NT>(s.ut, u, E, g, lane);
+    const bool bulk = w_stage_T_bulk<NT>(s, T, invd, n, E, g, lane, bar, true);
     cp_async_wait_all();
     do {   // left early when the staged data never landed
-    if (!bulk_landed(bulk, bar, sc, err)) break;
+    if (!bulk_landed<NT>(bulk, bar, sc, err, lane)) break;
+    {
+      int64_t e2;
+      int r2;
+      if (lane == 0 && bulk && ahead_elem(pf, R, W, slot, m, &e2, &r2)) {
+        const unsigned bv = (unsigned)(g.nb * sizeof(V)), bd = (unsigned)(g.nb * sizeof(double));
+        const int64_t b2 = e2 * g.nb, o2 = (int64_t)(r2 - bi.r) * n + b2;
+        l2_prefetch(T + b2, bv);
+        l2_prefetch(T + n + b2, bv);
+        l2_prefetch(T + 2 * n + b2, bv);
+        l2_prefetch(invd + b2, bv);
+        l2_prefetch(u + o2, bv);
+        l2_prefetch(f + o2, bv);
+        if (sc) l2_prefetch(r + o2, bd);
+        if (qv) l2_prefetch(qv + o2, bd);
+        if (FUSE) l2_prefetch(Phi + b2 * L, (unsigned)(L * g.nb * sizeof(BT)));
+      }
+    }
     if (FUSE) {
-      w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
-      __syncwarp();
+      w_prolong_tile<NT>(s.ut, Phi, ec, L, e, E, g, lane);
+      ebar<NT>();
     }
     {
       V fr[kC];
 #pragma unroll
       for (int i = 0; i < kC; ++i) {
-        const int c = lane + 32 * i;
+        const int c = lane + NT * i;
         fr[i] = (i < ncl && c < g.nb) ? __ldg(f + base + c) : (V)0;
       }
 #pragma unroll
       for (int i = 0; i < kC; ++i) {
-        const int c = lane + 32 * i;
+        const int c = lane + NT * i;
         if (i < ncl && c < g.nb) s.y[c] = fr[i] - (w_apply_A_s(s, g, c) + w_cell_term(Wd, base, s.ut, g, c));
       }
     }
@@ -954,16 +1111,16 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
     double rr[kC], qq[kC];
 #pragma unroll
     for (int i = 0; i < kC; ++i) {
-      const int c = lane + 32 * i;
+      const int c = lane + NT * i;
       const bool in = i < ncl && c < g.nb;
       rr[i] = (in && sc) ? __ldg(r + base + c) : 0.0;
       qq[i] = (in && qv) ? __ldg(qv + base + c) : 0.0;
     }
-    __syncwarp();
-    w_ic0_s(s, g, lane, tab);
+    ebar<NT>();
+    w_ic0_s<NT, TABLE>(s, g, lane, tab);
 #pragma unroll
     for (int i = 0; i < kC; ++i) {
-      const int c = lane + 32 * i;
+      const int c = lane + NT * i;
       if (!(i < ncl && c < g.nb)) continue;
       const int lx = c % g.bx, t = c / g.bx;
       const V zv = s.ut[wpad(g, lx, t % g.by, t / g.by)] + s.y[c];
@@ -978,21 +1135,21 @@ __global__ void __launch_bounds__(stage_warps<kStageFull, V>() * 32) k_post(cons
   } else if (act) {
     const WElem E = w_elem(e, nbr, g);
     const int64_t base = E.base;
-    w_cp_padded(s.ut, u + base, g, lane);
-    w_cp_halo(s.ut, u, E, g, lane);
-    const bool bulk = w_stage_T_bulk(s, T, invd, n, E, g, lane, bar, true);
+    w_cp_padded<NT>(s.ut, u + base, g, lane);
+    w_cp_halo<NT>(s.ut, u, E, g, lane);
+    const bool bulk = w_stage_T_bulk<NT>(s, T, invd, n, E, g, lane, bar, true);
     cp_async_wait_all();
     do {   // left early when the staged data never landed
-    if (!bulk_landed(bulk, bar, sc, err)) break;
+    if (!bulk_landed<NT>(bulk, bar, sc, err, lane)) break;
     if (FUSE) {
-      w_prolong_tile(s.ut, Phi, ec, L, e, E, g, lane);
-      __syncwarp();
+      w_prolong_tile<NT>(s.ut, Phi, ec, L, e, E, g, lane);
+      ebar<NT>();
     }
-    for (int c = lane; c < g.nb; c += 32)
+    for (int c = lane; c < g.nb; c += NT)
       s.y[c] = __ldg(f + base + c) - (w_apply_A_s(s, g, c) + w_cell_term(Wd, base, s.ut, g, c));
-    __syncwarp();
-    w_ic0_s(s, g, lane, tab);
-    for (int c = lane; c < g.nb; c += 32) {
+    ebar<NT>();
+    w_ic0_s<NT, TABLE>(s, g, lane, tab);
+    for (int c = lane; c < g.nb; c += NT) {
       const int lx = c % g.bx, t = c / g.bx;
       const double zc = (double)(s.ut[wpad(g, lx, t % g.by, t / g.by)] + s.y[c]);
       z[base + c] = zc;
@@ -1162,8 +1319,8 @@ struct FineOps {
 
 template <int LAYOUT, typename V, typename G>
 static inline size_t wsmem(const G& g) {
-  return (size_t)stage_warps<LAYOUT, V>() * wstage_elems<LAYOUT>(g) * sizeof(V) +
-         (LAYOUT == kStageRestrict || LAYOUT == kStageRestrictT ? 0 : plane_smem(g));
+  return (size_t)stage_elems<LAYOUT, V, G>() * wstage_elems<LAYOUT>(g) * sizeof(V) +
+         (plane_sweeps<LAYOUT, V, G>() ? kPlaneSmemBytes : 0);
 }
 template <typename G>
 static inline size_t wsmem_p(const G& g) {
@@ -1187,8 +1344,8 @@ static inline unsigned fine_wgrid(const msmg_ctx* c, int W = kWarpsPerCta) {
 template <typename V, typename BT, typename G>
 static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  constexpr int W = stage_warps<kStagePre, V>();
-  k_pre<V, G><<<fine_wgrid(c, W), W * 32, wsmem<kStagePre, V>(g), s>>>(
+  constexpr int W = stage_elems<kStagePre, V, G>();
+  k_pre<V, G><<<fine_wgrid(c, W), W * elem_threads<kStagePre, G, V>(), wsmem<kStagePre, V>(g), s>>>(
       B.x, B.r, B.pcur, B.q, o.T, o.invd, (V*)B.rv, (V*)B.vu[1], c->n, g, c->fine.m, c->fine.nbr, update, c->red, sc,
       c->flags + 6, B.R);
 }
@@ -1196,7 +1353,7 @@ static void pre_t(msmg_ctx* c, const FineOps<V, BT>& o, int update, PcgScalars* 
 template <typename V, typename BT, typename G>
 static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cudaStream_t s, const G& g) {
   SolveBuffers& B = c->sb;
-  constexpr int W = stage_warps<restrict_layout<V>(), V>();
+  constexpr int W = stage_elems<restrict_layout<V>(), V>();
   k_restrict<V, BT, G><<<fine_wgrid(c, W), W * 32, wsmem<restrict_layout<V>(), V>(g), s>>>(
       (const V*)B.rv, (const V*)B.vu[1], o.T, o.Wd, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
       c->fine.nbr, sc, B.R);
@@ -1206,15 +1363,16 @@ template <typename V, typename BT, typename G>
 static void post_t(msmg_ctx* c, const FineOps<V, BT>& o, const V* ec, const double* qv, PcgScalars* sc,
                    cudaStream_t s, const G& g, bool fuse) {
   SolveBuffers& B = c->sb;
-  constexpr int W = stage_warps<kStageFull, V>();
+  constexpr int W = stage_elems<kStageFull, V, G>();
+  constexpr int NT = elem_threads<kStageFull, G, V>();
   if (fuse)
-    k_post<V, BT, G, true><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
+    k_post<V, BT, G, true><<<fine_wgrid(c, W), W * NT, wsmem<kStageFull, V>(g), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.Wd, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
-        c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R);
+        c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R, B.R > 1 ? c->pf_post[1] : 0);
   else
-    k_post<V, BT, G, false><<<fine_wgrid(c, W), W * 32, wsmem<kStageFull, V>(g), s>>>(
+    k_post<V, BT, G, false><<<fine_wgrid(c, W), W * NT, wsmem<kStageFull, V>(g), s>>>(
         (const V*)B.rv, B.r, (const V*)B.vu[1], o.T, o.Wd, o.invd, o.Phi, ec, c->fine.L, c->lev[2].n, B.z, qv, c->n, g,
-        c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R);
+        c->fine.m, c->fine.nbr, c->red, sc, c->flags + 6, B.R, B.R > 1 ? c->pf_post[0] : 0);
 }
 
 template <typename V, typename BT, typename G>
@@ -1242,8 +1400,19 @@ static void pmatvec_t(msmg_ctx* c, PcgScalars* sc, cudaStream_t s, const G& g) {
 
 // Shared-memory limits of the fine-level kernels, set once per context (never
 // during stream capture).
+// CTAs of kernel k resident at once on the device (the launch's first wave)
+static int resident_ctas(const void* k, int threads, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;   // no prefetch
+  }
+  return per * sms;
+}
+
 template <typename V, typename BT, typename G>
-static void prepare_t(const G& g) {
+static void prepare_t(msmg_ctx* c, const G& g) {
   const int smv = (int)wsmem<kStageFull, V>(g), smd = (int)wsmem_p(g);
   cudaFuncSetAttribute(k_pre<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem<kStagePre, V>(g));
   cudaFuncSetAttribute(k_restrict<V, BT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1252,14 +1421,21 @@ static void prepare_t(const G& g) {
                        cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
   cudaFuncSetAttribute(k_post<V, BT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smv);
+  cudaFuncSetAttribute(k_post<V, BT, G, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_post<V, BT, G, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd);
   cudaFuncSetAttribute(k_pmatvec<G>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  constexpr int NT = elem_threads<kStageFull, G, V>();
+  c->pf_post[0] = resident_ctas((const void*)k_post<V, BT, G, false>, stage_elems<kStageFull, V, G>() * NT, smv);
+  c->pf_post[1] = resident_ctas((const void*)k_post<V, BT, G, true>, stage_elems<kStageFull, V, G>() * NT, smv);
 }
 
 void prepare_fine_kernels(msmg_ctx* c) {
   with_geo(c, [&](auto g) {
-    if (c->opts.precision == MSMG_MIXED) prepare_t<float, float>(g);
-    else prepare_t<double, double>(g);
+    if (c->opts.precision == MSMG_MIXED) prepare_t<float, float>(c, g);
+    else prepare_t<double, double>(c, g);
   });
 }
 

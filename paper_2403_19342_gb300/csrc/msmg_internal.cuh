@@ -211,6 +211,7 @@ struct msmg_ctx {
   int tune_fused[2];                            // prolongation inside k_post (1) or separate (0)
   int tune_tail[2];                             // coarse cycle: per level (0), cluster tail (1), one grid (2)
   int tuned[2];                                 // set once measured
+  int pf_post[2];                               // resident CTAs of k_post (unfused, fused): its L2 prefetch distance
   int tail_l0;                                  // first level of the cluster tail (0: none)
   int tail_cs;                                  // CTAs per cluster
   int tail_lt;                                  // compile-time L of the tail levels (0: runtime)
