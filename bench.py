@@ -818,6 +818,21 @@ def run_network(args, world, rank, local):
         ms = a.elapsed_time(b) / args.steps
         flops = 2.0 * B * (512 * hidden[0] + hidden[0] * hidden[1] + hidden[1] * 5 * 512)
         out[name] = {"ms_per_forward": ms, "tflops": flops / (ms * 1e-3) / 1e12, "hidden": list(hidden)}
+        if name == "tensor_cores":
+            # each product alone, CUDA events on its own launch, L2 flushed before each pass
+            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+            dims = (512, hidden[0], hidden[1], 5 * 512)
+            acc = [0.0, 0.0, 0.0]
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                t = pkg.msmg_net_time_products(net.handle, x, stream)
+                acc = [u + v for u, v in zip(acc, t)]
+            per = []
+            for l in range(3):
+                ms_l = acc[l] / args.steps
+                fl = 2.0 * B * dims[l] * dims[l + 1]
+                per.append({"M": B, "N": dims[l + 1], "K": dims[l], "ms": ms_l, "tflops": fl / (ms_l * 1e-3) / 1e12})
+            out[name]["products"] = per
         net.close()
     peak = None
     try:
@@ -830,8 +845,10 @@ def run_network(args, world, rank, local):
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tc["ms_per_forward"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic", "config": {"workload": NET_WORKLOAD, "batch": B},
-            "roofline": {"bound": "tensor", "achieved": tc["tflops"], "peak": peak, "unit": "TFLOP/s",
-                         "frac": tc["tflops"] / peak, "peak_source": "measured cuBLAS bf16 burst"},
+            "roofline": {"bound": "tensor", "kernel": "k_gemm_tc (layer 3, the largest product)",
+                         "achieved": tc["products"][2]["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": tc["products"][2]["tflops"] / peak, "peak_source": "measured cuBLAS bf16 burst",
+                         "traffic": None},
             "forms": out, "speedup_over_cuda_cores": out["cuda_cores"]["ms_per_forward"] / tc["ms_per_forward"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

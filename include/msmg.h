@@ -452,6 +452,13 @@ int msmg_net_set_params(msmg_net* net, const float* params, msmg_stream stream);
 /* y[b] = network(x[b]) for b < batch (device, row-major [batch][n_in] -> [batch][n_vec * n_in]). */
 int msmg_net_forward(msmg_net* net, const float* x, float* y, int batch, msmg_stream stream);
 
+/* Device time of the forward pass's three products for one batch (<= batch_max) of x:
+ * one forward pass forms their operands, then each product is launched once more between
+ * CUDA events on `stream`; ms[l] receives the milliseconds of layer l's product.  Needs
+ * the tensor-core form (layer widths multiples of 64), else MSMG_ERR_UNSUPPORTED.
+ * Synchronises the stream. */
+int msmg_net_time_products(msmg_net* net, const float* x, int batch, double* ms, msmg_stream stream);
+
 /* Loss of a batch (<= batch_max) and its gradient with respect to every parameter
  * (device array of msmg_net_param_count floats, may be NULL); loss_host may be NULL. */
 int msmg_net_gradients(msmg_net* net, const float* x, const float* target, int batch, float* grad,

@@ -123,6 +123,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "msmg_net_get_params": (I, [P, P, P]),
         "msmg_net_set_params": (I, [P, P, P]),
         "msmg_net_forward": (I, [P, P, P, I, P]),
+        "msmg_net_time_products": (I, [P, P, I, C.POINTER(D), P]),
         "msmg_net_gradients": (I, [P, P, P, I, P, C.POINTER(C.c_float), P]),
         "msmg_net_train_step": (I, [P, P, P, I, C.c_float, C.POINTER(C.c_float), P]),
         "msmg_learning_data": (I, [P, P, P, P]),
@@ -149,7 +150,8 @@ def exported_symbols():
             "msmg_solve_batched", "msmg_max_batch_rhs", "msmg_autotune", "msmg_set_tuning",
             "msmg_net_workspace_size", "msmg_net_create",
             "msmg_net_destroy", "msmg_net_param_count", "msmg_net_param_offsets", "msmg_net_get_params",
-            "msmg_net_set_params", "msmg_net_forward", "msmg_net_gradients", "msmg_net_train_step",
+            "msmg_net_set_params", "msmg_net_forward", "msmg_net_time_products", "msmg_net_gradients",
+            "msmg_net_train_step",
             "msmg_learning_data", "msmg_check_conversions", "msmg_velocity", "msmg_impes_pressure_terms",
             "msmg_impes_transport"]
 
@@ -478,6 +480,13 @@ def msmg_net_create(desc: msmg_net_desc, workspace: torch.Tensor, seed: int = 0,
 def msmg_net_forward(net: int, x: torch.Tensor, y: torch.Tensor, stream=None) -> None:
     _check(load_library().msmg_net_forward(net, _ptr(x, torch.float32), _ptr(y, torch.float32), x.shape[0],
                                            _stream(stream)))
+
+
+def msmg_net_time_products(net: int, x: torch.Tensor, stream=None) -> list:
+    """Device milliseconds of the forward pass's three products (tensor-core form)."""
+    ms = (C.c_double * 3)()
+    _check(load_library().msmg_net_time_products(net, _ptr(x, torch.float32), x.shape[0], ms, _stream(stream)))
+    return [float(v) for v in ms]
 
 
 def msmg_net_gradients(net: int, x: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,

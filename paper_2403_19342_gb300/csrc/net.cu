@@ -20,6 +20,7 @@
 //
 // All kernels are deterministic (no atomics): a training run is reproducible.
 #include "msmg_internal.cuh"
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <new>
 
@@ -50,6 +51,9 @@ struct msmg_net {
   __nv_bfloat16* h1b;           // [batch_max][h1] BF16 activations
   __nv_bfloat16* h2b;           // [batch_max][h2]
   int* err;                     // device error word: a bounded tensor-core wait gave up
+  int map_err;                  // host: a tensor map of the tensor-core products could not be encoded
+  CUtensorMap tmap[3][2];               // per layer: A (activations) and Bt (weights), for batch tmap_batch
+  int tmap_batch;                       // 0: not encoded
 };
 
 namespace msmg {
@@ -142,33 +146,43 @@ static void gemm(const TAe* A, int lda, const TBe* B, int ldb, float* C, int ldc
 
 // ------------------------------------------------------------------ tensor-core GEMM (tcgen05)
 // C[M][N] = epi(A[M][K] . Bt[N][K]^T (+ bias)), A and Bt BF16 with K contiguous,
-// FP32 accumulation in tensor memory (TMEM).  One CTA of 4 warps per 128 x 128
-// output tile; K in blocks of 64 staged in shared memory by all threads (two
-// stages), in the canonical K-major layout without swizzle: 8-row x 16-byte core
-// matrices, the two 8-element halves of a 16-wide K step 128 bytes apart, 8-row
-// groups 256 bytes apart, each 16-wide K step of a 128-row block a 4 KB sub-block.
-// One thread issues the four 128 x 128 x 16 MMAs of a block and commits them to
-// the stage's mbarrier; a stage is refilled once that mbarrier has fired.  The
-// epilogue reads the accumulator with tcgen05.ld (warp w: TMEM lanes 32w ..
-// 32w + 31 = rows), adds the bias, applies the ReLU and writes FP32 and, when
-// asked, a BF16 copy (the next layer's A operand).  Every wait is bounded: on
-// timeout the error word is set, the MMAs get a second bounded wait and the TMEM
-// is freed before the CTA returns.  K must be a multiple of 64 and the row
-// strides multiples of 8 elements (16-byte loads).
-constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
-constexpr int kTcStage = 2 * kTcM * kTcK * 2;          // A and B blocks of one stage: 32 KB
-constexpr size_t kTcSmem = 2 * (size_t)kTcStage + 1024;
+// FP32 accumulation in tensor memory (TMEM).  One CTA of 4 warps per
+// 128 x BN output tile (BN = 256, 128 or 64, the largest dividing N), K in
+// blocks of 64 through a ring of tc_stages<BN>() shared-memory stages:
+//   warp 0, one thread: TMA (cp.async.bulk.tensor.2d) of the A and Bt blocks of
+//     a stage, 128-byte swizzle, completion counted in bytes on the stage's
+//     "full" mbarrier; it refills a stage once its "empty" mbarrier has fired;
+//   warp 1, one thread: the four 128 x BN x 16 MMAs of a block (shared-memory
+//     descriptors, K-major, 128-byte swizzle: 8-row groups 1024 bytes apart, the
+//     16-wide K steps 32 bytes apart inside the swizzle atom), then
+//     tcgen05.commit to the stage's "empty" barrier; after the last block a
+//     commit to the "done" barrier;
+//   all warps: the epilogue, tcgen05.ld of the accumulator (warp w: TMEM lanes
+//     32w .. 32w + 31 = rows) into shared memory, then row by row with whole
+//     row segments per store: bias, ReLU, FP32 store and, when asked, a BF16
+//     copy (the next layer's A operand).
+// Rows of A beyond M and of Bt beyond N read as zeros (TMA bounds).  Every wait
+// is bounded: on timeout the error word is set, the threads drain what they
+// issued with a second bounded wait, and the TMEM is freed before the CTA
+// returns.  K must be a multiple of 64, the row strides multiples of 8 elements
+// and the bases 16-byte aligned (the tensor maps' rules).
+constexpr int kTcM = 128, kTcK = 64;
+template <int BN>
+__host__ __device__ constexpr int tc_stages() { return BN == 256 ? 4 : (BN == 128 ? 6 : 8); }
+template <int BN>
+__host__ __device__ constexpr size_t tc_stage_bytes() { return (size_t)(kTcM + BN) * kTcK * 2; }
+template <int BN>
+__host__ __device__ constexpr size_t tc_smem_bytes() { return tc_stages<BN>() * tc_stage_bytes<BN>() + 1024; }
 
-__device__ __forceinline__ uint32_t tc_off(int r, int k) {
-  return (uint32_t)((k >> 4) * (kTcM * 32) + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-// shared-memory matrix descriptor: start, leading (K direction) and stride (8-row
-// groups) byte offsets, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+// shared-memory matrix descriptor, K-major with 128-byte swizzle: start address,
+// leading offset unused (1), stride between 8-row groups 1024 bytes, descriptor
+// version 1, layout type 2 (128-byte swizzle)
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(128u >> 4) << 16;
-  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 // instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both K-major, M x N
@@ -178,10 +192,9 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void tc_mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 __device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < (1 << 24); ++it) {
     uint32_t done;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done)
@@ -191,63 +204,82 @@ __device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
   }
   return false;
 }
+__device__ __forceinline__ void tc_tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
 
-template <int EPI>   // 1: + bias; 2: + bias, ReLU
-__global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict__ A, int lda,
-                                                 const __nv_bfloat16* __restrict__ Bt, int ldb, float* __restrict__ C,
-                                                 int ldc, __nv_bfloat16* __restrict__ Cb, const float* __restrict__ bias,
-                                                 int M, int N, int K, int* err) {
+template <int EPI, int BN>   // EPI 1: + bias; 2: + bias, ReLU
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+                                                    const __grid_constant__ CUtensorMap mapB, float* __restrict__ C,
+                                                    int ldc, __nv_bfloat16* __restrict__ Cb,
+                                                    const float* __restrict__ bias, int M, int N, int K, int* err) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __shared__ __align__(8) unsigned long long bars[2];
+  constexpr int kTcStages = tc_stages<BN>();
+  __shared__ __align__(8) unsigned long long full[kTcStages], empty[kTcStages], done_bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  constexpr uint32_t kStage = (uint32_t)tc_stage_bytes<BN>();
+  constexpr uint32_t kBytesA = kTcM * kTcK * 2;
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
+  const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * BN;
+  const int nk = K / kTcK;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(kTcN));
+                 "r"(BN < 32 ? 32 : BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
-  if (threadIdx.x == 0) {
-    tc_mbar_init(smem_u32(&bars[0]));
-    tc_mbar_init(smem_u32(&bars[1]));
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < kTcStages; ++i) {
+      tc_mbar_init(smem_u32(&full[i]));
+      tc_mbar_init(smem_u32(&empty[i]));
+    }
+    tc_mbar_init(smem_u32(&done_bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_fail = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const int nk = K / kTcK;
-  uint32_t phase[2] = {0u, 0u};
-  bool ok = true;
-  for (int kb = 0; kb < nk && ok; ++kb) {
-    const int st = kb & 1;
-    unsigned char* sA = smem + st * kTcStage;
-    unsigned char* sB = sA + kTcStage / 2;
-    if (kb >= 2) {   // the MMAs that last read this stage are done
-      ok = tc_mbar_wait(smem_u32(&bars[st]), phase[st]);
-      phase[st] ^= 1u;
-      ok = __syncthreads_and(ok);
-      if (!ok) break;
+  if (threadIdx.x == 0) {
+    // producer: stage kb % S is refilled once the MMAs of block kb - S released it
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int st = kb % kTcStages, use = kb / kTcStages;
+      if (use > 0 && !tc_mbar_wait(smem_u32(&empty[st]), (uint32_t)((use - 1) & 1))) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      if (*(volatile int*)&s_fail) break;
+      const uint32_t sA = smem_u32(smem + st * kStage), sB = sA + kBytesA;
+      const uint32_t fb = smem_u32(&full[st]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(kStage) : "memory");
+      tc_tma_2d(sA, &mapA, kb * kTcK, m0, fb);
+      tc_tma_2d(sB, &mapB, kb * kTcK, n0, fb);
     }
-    // 128 rows x 64 values of A and of Bt: 16-byte chunks, 8 per row
-    for (int i = threadIdx.x; i < kTcM * (kTcK / 8); i += 128) {
-      const int r = i >> 3, kc = (i & 7) * 8;
-      uint4 va = make_uint4(0u, 0u, 0u, 0u), vb = make_uint4(0u, 0u, 0u, 0u);
-      if (m0 + r < M) va = *reinterpret_cast<const uint4*>(A + (int64_t)(m0 + r) * lda + kb * kTcK + kc);
-      if (n0 + r < N) vb = *reinterpret_cast<const uint4*>(Bt + (int64_t)(n0 + r) * ldb + kb * kTcK + kc);
-      *reinterpret_cast<uint4*>(sA + tc_off(r, kc)) = va;
-      *reinterpret_cast<uint4*>(sB + tc_off(r, kc)) = vb;
-    }
-    // the tensor core reads shared memory through the async proxy
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    // a load issued but never consumed must land before the CTA may exit
+    for (int j = kb - kTcStages < 0 ? 0 : kb - kTcStages; j < kb; ++j)
+      tc_mbar_wait(smem_u32(&full[j % kTcStages]), (uint32_t)((j / kTcStages) & 1));
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    constexpr uint32_t idesc = tc_idesc(kTcM, BN);
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int st = kb % kTcStages, use = kb / kTcStages;
+      if (!tc_mbar_wait(smem_u32(&full[st]), (uint32_t)(use & 1)) || *(volatile int*)&s_fail) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t idesc = tc_idesc(kTcM, kTcN);
+      const uint32_t sA = smem_u32(smem + st * kStage), sB = sA + kBytesA;
 #pragma unroll
       for (int kk = 0; kk < kTcK / 16; ++kk) {
-        const uint64_t da = tc_desc(smem_u32(sA) + kk * kTcM * 32);
-        const uint64_t db = tc_desc(smem_u32(sB) + kk * kTcM * 32);
+        const uint64_t da = tc_desc_sw128(sA + kk * 32), db = tc_desc_sw128(sB + kk * 32);
         const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -255,24 +287,31 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
             "l"(da), "l"(db), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       smem_u32(&bars[st]))
+                       smem_u32(&empty[st]))
                    : "memory");
     }
+    // the commit covers every MMA issued before it
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(&done_bar))
+                 : "memory");
   }
-  // the last commit covers every MMA this CTA issued
-  const int last = (nk - 1) & 1;
-  bool done = ok && tc_mbar_wait(smem_u32(&bars[last]), phase[last]);
-  done = __syncthreads_and(done);
-  if (!done) {
+  __syncwarp();
+  bool ok = tc_mbar_wait(smem_u32(&done_bar), 0u);
+  ok = __syncthreads_and(ok && s_fail == 0);
+  if (!ok) {
     if (threadIdx.x == 0) {
       atomicExch(err, 1);
-      tc_mbar_wait(smem_u32(&bars[last]), phase[last]);   // second bounded wait before freeing TMEM
+      tc_mbar_wait(smem_u32(&done_bar), 0u);   // second bounded wait before freeing TMEM
     }
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
+    // the accumulator rows of this warp through shared memory (the pipeline stages
+    // are idle now), rows padded by 4 floats: then every store writes whole row
+    // segments of the output
+    constexpr int kLd = BN + 4;
+    float* st = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * kLd;
 #pragma unroll 1
-    for (int c0 = 0; c0 < kTcN; c0 += 16) {
+    for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t v[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -281,16 +320,36 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
             "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (row < M) {
+      float4* dst = reinterpret_cast<float4*>(st + (size_t)lane * kLd + c0);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col >= N) continue;
-          float x = __uint_as_float(v[j]);
-          if (EPI >= 1) x += bias[col];
-          if (EPI == 2) x = x > 0.f ? x : 0.f;
-          C[(int64_t)row * ldc + col] = x;
-          if (Cb) Cb[(int64_t)row * ldc + col] = __float2bfloat16(x);
+      for (int j = 0; j < 4; ++j)
+        dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
+                             __uint_as_float(v[4 * j + 3]));
+    }
+    __syncwarp();
+    // lane l takes columns 4l .. 4l + 3 of each 128-column span of a row
+#pragma unroll 1
+    for (int r = 0; r < 32; ++r) {
+      const int row = m0 + warp * 32 + r;
+      if (row >= M) break;
+#pragma unroll
+      for (int c = lane * 4; c < BN; c += 128) {
+        float4 q = *reinterpret_cast<const float4*>(st + (size_t)r * kLd + c);
+        if (EPI >= 1) {
+          const float4 bb = __ldg(reinterpret_cast<const float4*>(bias + n0 + c));
+          q.x += bb.x; q.y += bb.y; q.z += bb.z; q.w += bb.w;
+        }
+        if (EPI == 2) {
+          q.x = q.x > 0.f ? q.x : 0.f; q.y = q.y > 0.f ? q.y : 0.f;
+          q.z = q.z > 0.f ? q.z : 0.f; q.w = q.w > 0.f ? q.w : 0.f;
+        }
+        *reinterpret_cast<float4*>(C + (int64_t)row * ldc + n0 + c) = q;
+        if (Cb) {
+          const __nv_bfloat162 h0 = __floats2bfloat162_rn(q.x, q.y), h1 = __floats2bfloat162_rn(q.z, q.w);
+          uint2 w;
+          w.x = *reinterpret_cast<const uint32_t*>(&h0);
+          w.y = *reinterpret_cast<const uint32_t*>(&h1);
+          *reinterpret_cast<uint2*>(Cb + (int64_t)row * ldc + n0 + c) = w;
         }
       }
     }
@@ -299,15 +358,60 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN < 32 ? 32 : BN));
   }
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against
+// the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+// 2-D BF16 map of a rows x cols matrix (cols contiguous, row stride ld elements),
+// box of box_rows x 64, 128-byte swizzle, zero fill outside
+static bool tc_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int cols, int ld, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// widest output tile dividing N (N a multiple of 64)
+static inline int tc_bn(int N) { return N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64); }
 template <int EPI>
-static void gemm_tc(const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, float* C, int ldc,
-                    __nv_bfloat16* Cb, const float* bias, int M, int N, int K, int* err, cudaStream_t s) {
-  dim3 grid((N + kTcN - 1) / kTcN, (M + kTcM - 1) / kTcM);
-  k_gemm_tc<EPI><<<grid, 128, kTcSmem, s>>>(A, lda, Bt, ldb, C, ldc, Cb, bias, M, N, K, err);
+static void gemm_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int ldc, __nv_bfloat16* Cb,
+                    const float* bias, int M, int N, int K, int* err, cudaStream_t s) {
+  const int bn = tc_bn(N);
+  dim3 grid((unsigned)(N / bn), (unsigned)((M + kTcM - 1) / kTcM));
+  if (bn == 256) k_gemm_tc<EPI, 256><<<grid, 128, tc_smem_bytes<256>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
+  else if (bn == 128) k_gemm_tc<EPI, 128><<<grid, 128, tc_smem_bytes<128>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
+  else k_gemm_tc<EPI, 64><<<grid, 128, tc_smem_bytes<64>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
+}
+template <int EPI>
+static void gemm_tc_prepare() {
+  cudaFuncSetAttribute(k_gemm_tc<EPI, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<256>());
+  cudaFuncSetAttribute(k_gemm_tc<EPI, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<128>());
+  cudaFuncSetAttribute(k_gemm_tc<EPI, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<64>());
 }
 
 // BF16 copy of an FP32 matrix (the tensor-core A operand of layer 1)
@@ -473,18 +577,52 @@ static void net_refresh_bf16(msmg_net* t, cudaStream_t s) {
                                                                   t->wt16 + t->off_w[l]);
 }
 
+// Tensor maps of the three products for `batch` rows (encoded when the batch
+// size changes; the buffers and weights never move).
+static bool net_encode_maps(msmg_net* t, int batch) {
+  if (t->tmap_batch == batch) return true;
+  const msmg_net_desc& d = t->d;
+  const int dims[4] = {d.n_in, d.hidden[0], d.hidden[1], t->n_out};
+  const __nv_bfloat16* acts[3] = {t->xb, t->h1b, t->h2b};
+  for (int l = 0; l < 3; ++l) {
+    const int K = dims[l], N = dims[l + 1];
+    if (!tc_map(&t->tmap[l][0], acts[l], batch, K, K, kTcM) ||
+        !tc_map(&t->tmap[l][1], t->wt16 + t->off_w[l], N, K, K, tc_bn(N))) {
+      t->tmap_batch = 0;
+      return false;
+    }
+  }
+  t->tmap_batch = batch;
+  return true;
+}
+
+// The three products on the tensor cores; with ev (6 events) each launch is
+// bracketed by ev[2l], ev[2l + 1].
+static void net_tc_products(msmg_net* t, int batch, cudaStream_t s, cudaEvent_t* ev) {
+  const msmg_net_desc& d = t->d;
+  const int h1 = d.hidden[0], h2 = d.hidden[1], no = t->n_out;
+  if (!net_encode_maps(t, batch)) {
+    t->map_err = 1;
+    return;
+  }
+  if (ev) cudaEventRecord(ev[0], s);
+  gemm_tc<2>(t->tmap[0][0], t->tmap[0][1], t->h1, h1, t->h1b, t->w32 + t->off_b[0], batch, h1, d.n_in, t->err, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  if (ev) cudaEventRecord(ev[2], s);
+  gemm_tc<2>(t->tmap[1][0], t->tmap[1][1], t->h2, h2, t->h2b, t->w32 + t->off_b[1], batch, h2, h1, t->err, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  if (ev) cudaEventRecord(ev[4], s);
+  gemm_tc<1>(t->tmap[2][0], t->tmap[2][1], t->out, no, nullptr, t->w32 + t->off_b[2], batch, no, h2, t->err, s);
+  if (ev) cudaEventRecord(ev[5], s);
+}
+
 // forward for `batch` rows of x; output in net->out
 static void net_forward(msmg_net* t, const float* x, int batch, cudaStream_t s) {
   const msmg_net_desc& d = t->d;
   const int h1 = d.hidden[0], h2 = d.hidden[1], no = t->n_out;
   k_bf16_copy<<<g256((int64_t)batch * d.n_in), 256, 0, s>>>(x, t->xb, (int64_t)batch * d.n_in);
   if (t->tc) {
-    gemm_tc<2>(t->xb, d.n_in, t->wt16 + t->off_w[0], d.n_in, t->h1, h1, t->h1b, t->w32 + t->off_b[0], batch, h1,
-               d.n_in, t->err, s);
-    gemm_tc<2>(t->h1b, h1, t->wt16 + t->off_w[1], h1, t->h2, h2, t->h2b, t->w32 + t->off_b[1], batch, h2, h1, t->err,
-               s);
-    gemm_tc<1>(t->h2b, h2, t->wt16 + t->off_w[2], h2, t->out, no, nullptr, t->w32 + t->off_b[2], batch, no, h2,
-               t->err, s);
+    net_tc_products(t, batch, s, nullptr);
   } else {
     gemm<__nv_bfloat16, __nv_bfloat16, false, false, 2>(t->xb, d.n_in, t->w16 + t->off_w[0], h1, t->h1, h1,
                                                         t->w32 + t->off_b[0], batch, h1, d.n_in, s);
@@ -663,8 +801,13 @@ int net_guesses(msmg_ctx* c, const msmg_net* net, float* x, float* g, cudaStream
 }
 
 // MSMG_ERR_DEVICE_TIMEOUT when a tensor-core wait of the network's products gave up
-// (synchronises the stream; clears the word)
+// (synchronises the stream; clears the word), MSMG_ERR_CUDA when a tensor map
+// could not be encoded (the products were not launched)
 int net_status(msmg_net* t, cudaStream_t s) {
+  if (t->map_err) {
+    t->map_err = 0;
+    return MSMG_ERR_CUDA;
+  }
   int e = 0;
   MSMG_CUDA_TRY(cudaMemcpyAsync(&e, t->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   MSMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -715,8 +858,8 @@ int msmg_net_create(const msmg_net_desc* desc, void* workspace, size_t workspace
   k_to_bf16<<<g256(t->n_param), 256, 0, s>>>(t->w32, t->w16, t->n_param);
   net_refresh_bf16(t, s);
   MSMG_CUDA_TRY(cudaMemsetAsync(t->err, 0, 4 * sizeof(int), s));
-  MSMG_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-  MSMG_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+  gemm_tc_prepare<1>();
+  gemm_tc_prepare<2>();
   MSMG_CUDA_TRY(cudaGetLastError());
   *out = t;
   return 0;
@@ -759,6 +902,25 @@ int msmg_net_forward(msmg_net* net, const float* x, float* y, int batch, msmg_st
                                   cudaMemcpyDeviceToDevice, s));
   }
   MSMG_CUDA_TRY(cudaGetLastError());
+  return net_status(net, s);
+}
+
+int msmg_net_time_products(msmg_net* net, const float* x, int batch, double* ms, msmg_stream stream) {
+  if (!net || !x || !ms || batch < 1 || batch > net->d.batch_max) return MSMG_ERR_INVALID_ARG;
+  if (!net->tc) return MSMG_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) MSMG_CUDA_TRY(cudaEventCreate(&ev[i]));
+  net_forward(net, x, batch, s);   // the products' operands: BF16 input and activations
+  net_tc_products(net, batch, s, ev);
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, ev[2 * l], ev[2 * l + 1]);
+    ms[l] = t;
+  }
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  MSMG_CUDA_TRY(e);
   return net_status(net, s);
 }
 
