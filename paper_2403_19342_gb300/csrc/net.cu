@@ -146,33 +146,40 @@ static void gemm(const TAe* A, int lda, const TBe* B, int ldb, float* C, int ldc
 
 // ------------------------------------------------------------------ tensor-core GEMM (tcgen05)
 // C[M][N] = epi(A[M][K] . Bt[N][K]^T (+ bias)), A and Bt BF16 with K contiguous,
-// FP32 accumulation in tensor memory (TMEM).  One CTA of 4 warps per
-// 128 x BN output tile (BN = 256, 128 or 64, the largest dividing N), K in
-// blocks of 64 through a ring of tc_stages<BN>() shared-memory stages:
-//   warp 0, one thread: TMA (cp.async.bulk.tensor.2d) of the A and Bt blocks of
-//     a stage, 128-byte swizzle, completion counted in bytes on the stage's
-//     "full" mbarrier; it refills a stage once its "empty" mbarrier has fired;
-//   warp 1, one thread: the four 128 x BN x 16 MMAs of a block (shared-memory
+// FP32 accumulation in tensor memory (TMEM).  Persistent: one CTA per SM takes
+// the 128 x BN output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (BN =
+// 256, 128 or 64, the widest dividing N; N-tiles fastest, so consecutive tiles
+// share their A rows in L2), with six warps in three roles:
+//   warp 0, one thread: TMA (cp.async.bulk.tensor.2d) of the A and Bt blocks
+//     (K in blocks of 64, 128-byte swizzle) into a ring of shared-memory stages,
+//     completion counted in bytes on the stage's "full" mbarrier; a stage is
+//     refilled once its "empty" mbarrier has fired;
+//   warp 1, one thread: the four 128 x BN x 16 MMAs of each block (shared-memory
 //     descriptors, K-major, 128-byte swizzle: 8-row groups 1024 bytes apart, the
-//     16-wide K steps 32 bytes apart inside the swizzle atom), then
-//     tcgen05.commit to the stage's "empty" barrier; after the last block a
-//     commit to the "done" barrier;
-//   all warps: the epilogue, tcgen05.ld of the accumulator (warp w: TMEM lanes
-//     32w .. 32w + 31 = rows) into shared memory, then row by row with whole
-//     row segments per store: bias, ReLU, FP32 store and, when asked, a BF16
-//     copy (the next layer's A operand).
+//     16-wide K steps 32 bytes apart inside the swizzle atom), tcgen05.commit to
+//     the stage's "empty" barrier, and after a tile's last block a commit to the
+//     "accumulator full" barrier of the tile's TMEM buffer (two buffers of BN
+//     columns, so the next tile accumulates while this one is written out);
+//   warps 2-5: the epilogue (warp w reads TMEM lanes 32 (w mod 4) .. + 31, the
+//     tile's rows): 64-column chunks by tcgen05.ld into a padded shared-memory
+//     slice, the buffer released ("accumulator empty") once read, then bias, ReLU,
+//     FP32 store and, when asked, a BF16 copy (the next layer's A operand), each
+//     store writing whole row segments.
 // Rows of A beyond M and of Bt beyond N read as zeros (TMA bounds).  Every wait
-// is bounded: on timeout the error word is set, the threads drain what they
-// issued with a second bounded wait, and the TMEM is freed before the CTA
-// returns.  K must be a multiple of 64, the row strides multiples of 8 elements
-// and the bases 16-byte aligned (the tensor maps' rules).
-constexpr int kTcM = 128, kTcK = 64;
+// is bounded: on timeout the error word is set, the loops stop, what was issued
+// is drained with bounded waits, and the TMEM is freed before the CTA returns.
+// K must be a multiple of 64, the row strides multiples of 8 elements and the
+// bases 16-byte aligned (the tensor maps' rules).
+constexpr int kTcM = 128, kTcK = 64, kTcThreads = 192, kTcChunk = 64;
 template <int BN>
-__host__ __device__ constexpr int tc_stages() { return BN == 256 ? 4 : (BN == 128 ? 6 : 8); }
+__host__ __device__ constexpr int tc_stages() { return BN == 256 ? 3 : (BN == 128 ? 4 : 6); }
 template <int BN>
 __host__ __device__ constexpr size_t tc_stage_bytes() { return (size_t)(kTcM + BN) * kTcK * 2; }
+constexpr size_t kTcEpiBytes = (size_t)4 * 32 * (kTcChunk + 4) * 4;   // four warps' padded 32 x 64 slices
 template <int BN>
-__host__ __device__ constexpr size_t tc_smem_bytes() { return tc_stages<BN>() * tc_stage_bytes<BN>() + 1024; }
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+  return tc_stages<BN>() * tc_stage_bytes<BN>() + kTcEpiBytes + 1024;
+}
 
 // shared-memory matrix descriptor, K-major with 128-byte swizzle: start address,
 // leading offset unused (1), stride between 8-row groups 1024 bytes, descriptor
@@ -190,8 +197,8 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void tc_mbar_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+__device__ __forceinline__ void tc_mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
 __device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
   for (int it = 0; it < (1 << 24); ++it) {
@@ -211,34 +218,45 @@ __device__ __forceinline__ void tc_tma_2d(uint32_t dst, const CUtensorMap* map, 
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
 
 template <int EPI, int BN>   // EPI 1: + bias; 2: + bias, ReLU
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
-                                                    const __grid_constant__ CUtensorMap mapB, float* __restrict__ C,
-                                                    int ldc, __nv_bfloat16* __restrict__ Cb,
-                                                    const float* __restrict__ bias, int M, int N, int K, int* err) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB,
+                                                           float* __restrict__ C, int ldc,
+                                                           __nv_bfloat16* __restrict__ Cb,
+                                                           const float* __restrict__ bias, int M, int N, int K,
+                                                           int* err) {
+  constexpr int S = tc_stages<BN>();
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  constexpr int kTcStages = tc_stages<BN>();
-  __shared__ __align__(8) unsigned long long full[kTcStages], empty[kTcStages], done_bar;
+  __shared__ __align__(8) unsigned long long full[S], empty[S], acc_full[2], acc_empty[2], done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   constexpr uint32_t kStage = (uint32_t)tc_stage_bytes<BN>();
   constexpr uint32_t kBytesA = kTcM * kTcK * 2;
+  constexpr uint32_t kCols = 2 * BN;                      // two accumulator buffers
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * BN;
   const int nk = K / kTcK;
+  const int ntn = N / BN, ntiles = ntn * ((M + kTcM - 1) / kTcM);
+  const int mytiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(BN < 32 ? 32 : BN));
+                 "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (threadIdx.x == 32) {
-    for (int i = 0; i < kTcStages; ++i) {
-      tc_mbar_init(smem_u32(&full[i]));
-      tc_mbar_init(smem_u32(&empty[i]));
+    for (int i = 0; i < S; ++i) {
+      tc_mbar_init(smem_u32(&full[i]), 1);
+      tc_mbar_init(smem_u32(&empty[i]), 1);
     }
-    tc_mbar_init(smem_u32(&done_bar));
+    for (int i = 0; i < 2; ++i) {
+      tc_mbar_init(smem_u32(&acc_full[i]), 1);
+      tc_mbar_init(smem_u32(&acc_empty[i]), 4);   // one arrival per epilogue warp
+    }
+    tc_mbar_init(smem_u32(&done_bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     s_fail = 0;
   }
@@ -247,118 +265,148 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
   if (threadIdx.x == 0) {
-    // producer: stage kb % S is refilled once the MMAs of block kb - S released it
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int st = kb % kTcStages, use = kb / kTcStages;
-      if (use > 0 && !tc_mbar_wait(smem_u32(&empty[st]), (uint32_t)((use - 1) & 1))) {
-        atomicExch(&s_fail, 1);
-        break;
+    // producer: global block counter g runs across the CTA's tiles
+    int g = 0;
+    bool stop = false;
+    for (int i = 0; i < mytiles && !stop; ++i) {
+      const int t = (int)blockIdx.x + i * (int)gridDim.x;
+      const int m0 = (t / ntn) * kTcM, n0 = (t % ntn) * BN;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int st = g % S, use = g / S;
+        if ((use > 0 && !tc_mbar_wait(smem_u32(&empty[st]), (uint32_t)((use - 1) & 1))) ||
+            *(volatile int*)&s_fail) {
+          atomicExch(&s_fail, 1);
+          stop = true;
+          break;
+        }
+        const uint32_t sA = smem_u32(smem + st * kStage), sB = sA + kBytesA;
+        const uint32_t fb = smem_u32(&full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(kStage) : "memory");
+        tc_tma_2d(sA, &mapA, kb * kTcK, m0, fb);
+        tc_tma_2d(sB, &mapB, kb * kTcK, n0, fb);
       }
-      if (*(volatile int*)&s_fail) break;
-      const uint32_t sA = smem_u32(smem + st * kStage), sB = sA + kBytesA;
-      const uint32_t fb = smem_u32(&full[st]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(kStage) : "memory");
-      tc_tma_2d(sA, &mapA, kb * kTcK, m0, fb);
-      tc_tma_2d(sB, &mapB, kb * kTcK, n0, fb);
     }
-    // a load issued but never consumed must land before the CTA may exit
-    for (int j = kb - kTcStages < 0 ? 0 : kb - kTcStages; j < kb; ++j)
-      tc_mbar_wait(smem_u32(&full[j % kTcStages]), (uint32_t)((j / kTcStages) & 1));
+    // a load issued but not consumed must land before the CTA may exit (the last
+    // S loads are the last completions of their barriers)
+    for (int j = g - S < 0 ? 0 : g - S; j < g; ++j) tc_mbar_wait(smem_u32(&full[j % S]), (uint32_t)((j / S) & 1));
   } else if (threadIdx.x == 32) {
     // MMA issuer
     constexpr uint32_t idesc = tc_idesc(kTcM, BN);
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int st = kb % kTcStages, use = kb / kTcStages;
-      if (!tc_mbar_wait(smem_u32(&full[st]), (uint32_t)(use & 1)) || *(volatile int*)&s_fail) {
+    int g = 0;
+    bool stop = false;
+    for (int i = 0; i < mytiles && !stop; ++i) {
+      const int a = i & 1, use = i >> 1;
+      if ((use > 0 && !tc_mbar_wait(smem_u32(&acc_empty[a]), (uint32_t)((use - 1) & 1))) || *(volatile int*)&s_fail) {
         atomicExch(&s_fail, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t sA = smem_u32(smem + st * kStage), sB = sA + kBytesA;
+      const uint32_t acc_tm = tmem + (uint32_t)(a * BN);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int st = g % S, su = g / S;
+        if (!tc_mbar_wait(smem_u32(&full[st]), (uint32_t)(su & 1)) || *(volatile int*)&s_fail) {
+          atomicExch(&s_fail, 1);
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t sA = smem_u32(smem + st * kStage), sB = sA + kBytesA;
 #pragma unroll
-      for (int kk = 0; kk < kTcK / 16; ++kk) {
-        const uint64_t da = tc_desc_sw128(sA + kk * 32), db = tc_desc_sw128(sB + kk * 32);
-        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        for (int kk = 0; kk < kTcK / 16; ++kk) {
+          const uint64_t da = tc_desc_sw128(sA + kk * 32), db = tc_desc_sw128(sB + kk * 32);
+          const uint32_t accf = (kb > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tm),
+              "l"(da), "l"(db), "r"(idesc), "r"(accf));
+        }
+        tc_commit(smem_u32(&empty[st]));
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       smem_u32(&empty[st]))
-                   : "memory");
+      if (!stop) tc_commit(smem_u32(&acc_full[a]));
     }
-    // the commit covers every MMA issued before it
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                     smem_u32(&done_bar))
-                 : "memory");
+    tc_commit(smem_u32(&done_bar));   // covers every MMA this CTA issued
+  } else if (warp >= 2) {
+    // epilogue
+    const int q = warp & 3;                                 // TMEM lane quarter = rows 32q .. 32q + 31
+    float* sl = reinterpret_cast<float*>(smem + S * kStage) + (size_t)(warp - 2) * 32 * (kTcChunk + 4);
+    for (int i = 0; i < mytiles; ++i) {
+      const int t = (int)blockIdx.x + i * (int)gridDim.x;
+      const int m0 = (t / ntn) * kTcM, n0 = (t % ntn) * BN;
+      const int a = i & 1, use = i >> 1;
+      bool ok = tc_mbar_wait(smem_u32(&acc_full[a]), (uint32_t)(use & 1));
+      ok = __all_sync(0xffffffffu, ok && *(volatile int*)&s_fail == 0);
+      if (!ok) {
+        if (lane == 0) atomicExch(&s_fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t acc_tm = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += kTcChunk) {
+#pragma unroll
+        for (int c1 = 0; c1 < kTcChunk; c1 += 16) {
+          uint32_t v[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];\n"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(acc_tm + (uint32_t)(c0 + c1)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          float4* dst = reinterpret_cast<float4*>(sl + (size_t)lane * (kTcChunk + 4) + c1);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        }
+        if (c0 + kTcChunk >= BN) {
+          // the whole accumulator of this tile has been read: release the buffer
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&acc_empty[a])) : "memory");
+        }
+        __syncwarp();
+        // lanes 0-15 row 2k, lanes 16-31 row 2k + 1, four columns each
+        const int cl = (lane & 15) * 4;
+        float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (EPI >= 1) bb = __ldg(reinterpret_cast<const float4*>(bias + n0 + c0 + cl));
+#pragma unroll 4
+        for (int r2 = 0; r2 < 32; r2 += 2) {
+          const int r = r2 + (lane >> 4);
+          const int row = m0 + q * 32 + r;
+          float4 v = *reinterpret_cast<const float4*>(sl + (size_t)r * (kTcChunk + 4) + cl);
+          if (row < M) {
+            if (EPI >= 1) { v.x += bb.x; v.y += bb.y; v.z += bb.z; v.w += bb.w; }
+            if (EPI == 2) {
+              v.x = v.x > 0.f ? v.x : 0.f; v.y = v.y > 0.f ? v.y : 0.f;
+              v.z = v.z > 0.f ? v.z : 0.f; v.w = v.w > 0.f ? v.w : 0.f;
+            }
+            *reinterpret_cast<float4*>(C + (int64_t)row * ldc + n0 + c0 + cl) = v;
+            if (Cb) {
+              const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+              uint2 w;
+              w.x = *reinterpret_cast<const uint32_t*>(&h0);
+              w.y = *reinterpret_cast<const uint32_t*>(&h1);
+              *reinterpret_cast<uint2*>(Cb + (int64_t)row * ldc + n0 + c0 + cl) = w;
+            }
+          }
+        }
+        __syncwarp();   // the slice is rewritten by the next chunk
+      }
+    }
   }
   __syncwarp();
-  bool ok = tc_mbar_wait(smem_u32(&done_bar), 0u);
-  ok = __syncthreads_and(ok && s_fail == 0);
-  if (!ok) {
-    if (threadIdx.x == 0) {
-      atomicExch(err, 1);
-      tc_mbar_wait(smem_u32(&done_bar), 0u);   // second bounded wait before freeing TMEM
-    }
-  } else {
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // the accumulator rows of this warp through shared memory (the pipeline stages
-    // are idle now), rows padded by 4 floats: then every store writes whole row
-    // segments of the output
-    constexpr int kLd = BN + 4;
-    float* st = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * kLd;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15}, [%16];\n"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      float4* dst = reinterpret_cast<float4*>(st + (size_t)lane * kLd + c0);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
-                             __uint_as_float(v[4 * j + 3]));
-    }
-    __syncwarp();
-    // lane l takes columns 4l .. 4l + 3 of each 128-column span of a row
-#pragma unroll 1
-    for (int r = 0; r < 32; ++r) {
-      const int row = m0 + warp * 32 + r;
-      if (row >= M) break;
-#pragma unroll
-      for (int c = lane * 4; c < BN; c += 128) {
-        float4 q = *reinterpret_cast<const float4*>(st + (size_t)r * kLd + c);
-        if (EPI >= 1) {
-          const float4 bb = __ldg(reinterpret_cast<const float4*>(bias + n0 + c));
-          q.x += bb.x; q.y += bb.y; q.z += bb.z; q.w += bb.w;
-        }
-        if (EPI == 2) {
-          q.x = q.x > 0.f ? q.x : 0.f; q.y = q.y > 0.f ? q.y : 0.f;
-          q.z = q.z > 0.f ? q.z : 0.f; q.w = q.w > 0.f ? q.w : 0.f;
-        }
-        *reinterpret_cast<float4*>(C + (int64_t)row * ldc + n0 + c) = q;
-        if (Cb) {
-          const __nv_bfloat162 h0 = __floats2bfloat162_rn(q.x, q.y), h1 = __floats2bfloat162_rn(q.z, q.w);
-          uint2 w;
-          w.x = *reinterpret_cast<const uint32_t*>(&h0);
-          w.y = *reinterpret_cast<const uint32_t*>(&h1);
-          *reinterpret_cast<uint2*>(Cb + (int64_t)row * ldc + n0 + c) = w;
-        }
-      }
-    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // every MMA complete before the TMEM is freed (at once unless a wait gave up)
+    const bool d = tc_mbar_wait(smem_u32(&done_bar), 0u);
+    if (s_fail || !d) atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN < 32 ? 32 : BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
   }
 }
 
@@ -398,14 +446,30 @@ static bool tc_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int co
 
 // widest output tile dividing N (N a multiple of 64)
 static inline int tc_bn(int N) { return N % 256 == 0 ? 256 : (N % 128 == 0 ? 128 : 64); }
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      n = 1;
+    }
+  }
+  return n;
+}
+// persistent launch: one CTA per SM (or per tile, when there are fewer)
 template <int EPI>
 static void gemm_tc(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int ldc, __nv_bfloat16* Cb,
                     const float* bias, int M, int N, int K, int* err, cudaStream_t s) {
   const int bn = tc_bn(N);
-  dim3 grid((unsigned)(N / bn), (unsigned)((M + kTcM - 1) / kTcM));
-  if (bn == 256) k_gemm_tc<EPI, 256><<<grid, 128, tc_smem_bytes<256>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
-  else if (bn == 128) k_gemm_tc<EPI, 128><<<grid, 128, tc_smem_bytes<128>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
-  else k_gemm_tc<EPI, 64><<<grid, 128, tc_smem_bytes<64>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
+  const int tiles = (N / bn) * ((M + kTcM - 1) / kTcM);
+  const unsigned grid = (unsigned)(tiles < sm_count() ? tiles : sm_count());
+  if (bn == 256)
+    k_gemm_tc<EPI, 256><<<grid, kTcThreads, tc_smem_bytes<256>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
+  else if (bn == 128)
+    k_gemm_tc<EPI, 128><<<grid, kTcThreads, tc_smem_bytes<128>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
+  else
+    k_gemm_tc<EPI, 64><<<grid, kTcThreads, tc_smem_bytes<64>(), s>>>(ma, mb, C, ldc, Cb, bias, M, N, K, err);
 }
 template <int EPI>
 static void gemm_tc_prepare() {

@@ -536,26 +536,34 @@ __global__ void k_add_null_shift(double* __restrict__ A, const double* __restric
   A[idx] += sigma * z[i] * z[j] / scal[0];
 }
 
-__global__ void k_gj_copy(const double* __restrict__ A, int64_t n, int64_t k, double* rowk, double* colk) {
+// Step k of the Gauss-Jordan inversion, in two launches.  The first takes the
+// pivot row and the multipliers of the pivot column: rowk[j] = A[k][j],
+// colk[i] = A[i][k] / A[k][k] (one division per row, not per element: FP64
+// division costs a dozen FP64 operations on GB300, and per element it made the
+// 16384-unknown inverse FP64-bound at 80 s); the second applies the rank-1
+// update with one FMA per element (n = 16384: 77 -> 19 s; a grid of one row
+// per CTA row measured slower than this flat one, 115 s).
+__global__ void k_gj_copy(const double* __restrict__ A, int64_t n, int64_t k, double* rowk, double* colk,
+                          double* stats) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double piv = A[k * n + k];
   rowk[i] = A[k * n + i];
-  colk[i] = A[i * n + k];
+  colk[i] = A[i * n + k] / piv;
+  if (i == 0 && !(piv > 0.0)) atomic_max_pos(&stats[1], 1.0);
 }
 
 __global__ void k_gj_update(double* __restrict__ A, int64_t n, int64_t k, const double* __restrict__ rowk,
-                            const double* __restrict__ colk, double* stats) {
+                            const double* __restrict__ colk) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   const int64_t i = idx / n, j = idx % n;
-  const double piv = colk[k];
+  const double piv = rowk[k];
   double v;
-  if (i == k && j == k) {
-    v = 1.0 / piv;
-    if (!(piv > 0.0)) atomic_max_pos(&stats[1], 1.0);
-  } else if (i == k) v = rowk[j] / piv;
-  else if (j == k) v = -colk[i] / piv;
-  else v = A[idx] - colk[i] * rowk[j] / piv;
+  if (i == k && j == k) v = 1.0 / piv;
+  else if (i == k) v = rowk[j] / piv;
+  else if (j == k) v = -colk[i];
+  else v = fma(-colk[i], rowk[j], A[idx]);
   A[idx] = v;
 }
 
@@ -728,8 +736,8 @@ int launch_coarsest(msmg_ctx* c, cudaStream_t s) {
     k_add_null_shift<<<g2, 256, 0, s>>>(B, z, nk, scal);
   }
   for (int64_t k = 0; k < nk; ++k) {
-    k_gj_copy<<<g1, 256, 0, s>>>(B, nk, k, rowk, colk);
-    k_gj_update<<<g2, 256, 0, s>>>(B, nk, k, rowk, colk, c->dtmp);
+    k_gj_copy<<<g1, 256, 0, s>>>(B, nk, k, rowk, colk, c->dtmp);
+    k_gj_update<<<g2, 256, 0, s>>>(B, nk, k, rowk, colk);
   }
   if (singular) {
     k_gemv_z<<<(unsigned)((nk * 32 + 255) / 256), 256, 0, s>>>(B, z, nk, scal, w);
