@@ -581,6 +581,19 @@ def run_batched(args, world, rank, local):
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_step = max_over_ranks(world, float(np.mean(e2e_ms)))
+    # the same problems solved one after another (one call each): what the batched
+    # call's concurrency across problems gains
+    seq_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for S, f, x in zip(solvers, F, X):
+            pkg.msmg_solve_batched([S.ctx], [f], [x], RTOL, 2000, 0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        seq_ms.append(a.elapsed_time(b))
+    seq_step = float(np.mean(seq_ms))
     per = []
     for N, inf in zip(C3_GRIDS, infos):
         its = [i["iterations"] for i in inf]
@@ -597,6 +610,8 @@ def run_batched(args, world, rank, local):
                        "l2": "flushed before each step (256 MiB write); working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "problems": per, "setup_ms": setup_ms, "eig_ms": eig_ms,
+            "sequential": {"ms_per_step": seq_step, "value": total / (seq_step * 1e-3),
+                           "note": "the same problems, one msmg_solve_batched call each, back to back"},
             "e2e": {"value": world * total / (e2e_step * 1e-3), "unit": "DOF/s",
                     "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "ms_per_step": e2e_step},
             "gpu_launches": launches, "clocks": clocks}
