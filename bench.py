@@ -776,6 +776,22 @@ def run_strategy2(args, world, rank, local):
                "dims": i0["dims"], "dims_kept": i0["dims_kept"], "setup_ms": i0["setup_ms"], "options": opts}
         lam = (S.export_basis(1)[1].cpu().numpy(), S.export_basis(2)[1].cpu().numpy()) if export else None
         S.close()
+        # the FP64 form's count beside it: on this contrast-1e8 field the mixed form's
+        # iteration count moves with rounding details (two orders of the same coarse
+        # row sums gave 49 and 62 iterations), the FP64 form's does not
+        base64 = dict(base, precision=pkg.FP64, autotune=False)
+        S = pkg.Solver(kappa, pkg.Options(**base64, **opts))
+        x64 = torch.zeros_like(f)
+        pkg.msmg_solve(S.ctx, f, x64, RTOL, 3000, 0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, info64 = pkg.msmg_solve(S.ctx, f, x64, RTOL, 3000, 0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rec["fp64"] = {"iterations": info64[0]["iterations"], "ms_per_step": a.elapsed_time(b),
+                       "true_rel_residual": info64[0]["true_rel_residual"]}
+        S.close()
         return rec, lam
 
     recs = {}
