@@ -88,9 +88,10 @@ def rhs(shape):
 #   pre:      x, r read+write, p, q read (FP64); r copy and u written (v); T (3), 1/d read (v)
 #   restrict: r copy, u (v); T (3) (v); basis (L values, v)
 #   prolong:  (separate variant) basis (L values, v); u read and written (v)
-#   post:     r copy, u (v); T (3), 1/d (v); the basis (L values, v) only in the
-#             fused variant, where the prolongation runs inside it; r read (FP64);
-#             q read (FP64, flexible beta only); z written (FP64)
+#   post:     r copy (mixed form only; the FP64 form reads r once for both), u (v);
+#             T (3), 1/d (v); the basis (L values, v) only in the fused variant,
+#             where the prolongation runs inside it; r read (FP64); q read (FP64,
+#             flexible beta only); z written (FP64)
 #   pmatvec:  z, p_old read, p_new, q written (FP64); T (3) and the diagonal D (FP64)
 # With R right-hand sides in one launch the coefficients (T, 1/d, D, basis) are read
 # once for all R: bytes per cell and right-hand side.  fused: the variant the
@@ -101,7 +102,8 @@ def kernel_bytes(form: str, L: int, R: int = 1, fused: bool = False) -> dict:
     basis = L * v / R
     return {"pre": 48 + 2 * v + 4 * v / R, "restrict": 2 * v + (3 * v) / R + basis,
             "prolong": 0.0 if fused else basis + 2 * v,
-            "post": 2 * v + (4 * v) / R + (basis if fused else 0.0) + 8 + flex + 8, "pmatvec": 32 + 32 / R}
+            "post": (2 * v if form == "mixed" else v) + (4 * v) / R + (basis if fused else 0.0) + 8 + flex + 8,
+            "pmatvec": 32 + 32 / R}
 
 
 VCYCLE_FINE = ("pre", "restrict", "prolong", "post")
