@@ -21,8 +21,9 @@ def test_mixed_bytes_per_cell(L):
 
 def test_fp64_bytes_per_cell():
     kb = bench.kernel_bytes("fp64", 6)
-    # no flexible beta in the FP64 form: post reads no q
-    assert kb == {"pre": 96, "restrict": 40 + 48, "prolong": 16 + 48, "post": 64, "pmatvec": 64}
+    # no flexible beta in the FP64 form: post reads no q; its right-hand side is r
+    # itself, read once (no V-precision copy)
+    assert kb == {"pre": 96, "restrict": 40 + 48, "prolong": 16 + 48, "post": 56, "pmatvec": 64}
 
 
 def test_batched_bytes_share_coefficients():
