@@ -46,11 +46,16 @@ def layout(net):
 FWD_TOL, GRAD_TOL = 3e-3, 1e-2
 
 
-@pytest.mark.parametrize("hidden,batch", [((256, 128), 64), ((512, 512), 300), ((100, 60), 64)],
-                         ids=["tensor_cores", "tensor_cores_ragged", "cuda_cores"])
+@pytest.mark.parametrize("hidden,batch", [((256, 128), 64), ((512, 512), 300), ((192, 64), 64),
+                                          ((512, 512), 4096), ((100, 60), 64)],
+                         ids=["tensor_cores", "tensor_cores_ragged", "tensor_cores_tile64",
+                              "tensor_cores_persistent", "cuda_cores"])
 def test_forward_loss_gradients_match_oracle(pkg, hidden, batch):
     # widths multiples of 64 run the products on the tensor cores (tcgen05), others on
-    # the CUDA cores; both read BF16 operands and accumulate in FP32
+    # the CUDA cores; both read BF16 operands and accumulate in FP32.  Output tiles
+    # 256, 128 and 64 wide all occur (192 and 64 take the 64-wide tile); at batch 4096
+    # the last product has 320 tiles, more than the SMs, so CTAs take several tiles
+    # and alternate their two accumulators.
     net = make_net(pkg, hidden=hidden, batch_max=batch)
     dims, w_off, b_off = layout(net)
     rng = np.random.default_rng(0)
