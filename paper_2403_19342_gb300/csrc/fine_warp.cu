@@ -714,7 +714,7 @@ template <typename V, typename BT, typename G>
 __global__ void __launch_bounds__(stage_elems<restrict_layout<V>(), V>() * 32, sizeof(V) == 4 ? 7 : 1)
     k_restrict(const V* __restrict__ f, const V* __restrict__ u, const V* __restrict__ T, const V* __restrict__ Wd,
                const BT* __restrict__ Phi, int L, double* __restrict__ rc, int64_t nc, int64_t n, G g, int64_t m,
-               const int* __restrict__ nbr, const PcgScalars* sc, int R) {
+               const int* __restrict__ nbr, const PcgScalars* sc, int R, int pf) {
   const BatchIdx bi = batch_idx(R);
   if (sc) sc += bi.r;
   if (sc && sc->done) return;
@@ -730,6 +730,16 @@ __global__ void __launch_bounds__(stage_elems<restrict_layout<V>(), V>() * 32, s
   const WStage<V> s = w_stage<V, kStageRestrictT>(smem, g, warp);   // used in the FP64 layout only
   V* ut = LAY == kStageRestrictT ? s.ut : reinterpret_cast<V*>(smem) + (size_t)warp * r4(g.P);
   const WElem E = w_elem(e, nbr, g);
+  if (pf && lane == 0 && (g.nb * (int)sizeof(V)) % 16 == 0) {
+    // the element's later loads into L2 now: batched launches (many waves) 215 -> 192 us
+    // at 16 right-hand sides on 128^3; at one right-hand side (one wave) it cost 3 us
+    const unsigned bv = (unsigned)(g.nb * sizeof(V));
+    l2_prefetch(Phi + (size_t)e * L * g.nb, (unsigned)(L * g.nb * sizeof(BT)));
+    l2_prefetch(T + E.base, bv);
+    l2_prefetch(T + n + E.base, bv);
+    l2_prefetch(T + 2 * n + E.base, bv);
+    l2_prefetch(f + E.base, bv);
+  }
   w_cp_padded(ut, u + E.base, g, lane);
   w_cp_halo(ut, u, E, g, lane);
   if constexpr (LAY == kStageRestrictT) w_stage_T(s, T, (const V*)nullptr, n, E, g, lane, false);
@@ -1368,7 +1378,7 @@ static void restrict_t(msmg_ctx* c, const FineOps<V, BT>& o, PcgScalars* sc, cud
   constexpr int W = stage_elems<restrict_layout<V>(), V>();
   k_restrict<V, BT, G><<<fine_wgrid(c, W), W * 32, wsmem<restrict_layout<V>(), V>(g), s>>>(
       (const V*)B.rv, (const V*)B.vu[1], o.T, o.Wd, o.Phi, c->fine.L, (double*)B.vf[2], c->lev[2].n, c->n, g, c->fine.m,
-      c->fine.nbr, sc, B.R);
+      c->fine.nbr, sc, B.R, B.R > 1);
 }
 
 template <typename V, typename BT, typename G>
