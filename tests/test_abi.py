@@ -57,3 +57,31 @@ def test_status_strings_and_validation(lib):
     assert e.value.status == -1
     o = pkg.Options(n_levels=3, block=(2, 2, 2), ratio=[(2, 2, 2)], n_eig=[4, 4]).to_c()
     assert pkg.msmg_workspace_size(g, o) > 8 * 512 * 10
+
+
+def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
+    # every check below returns before any device work, so it runs without a GPU
+    import paper_2403_19342_gb300 as pkg
+    bad = -1                                               # MSMG_ERR_INVALID_ARG
+    dummy = ctypes.c_void_p(256)                           # non-null, never dereferenced
+    out = ctypes.c_double()
+    assert lib.msmg_velocity(None, dummy, dummy, dummy, ctypes.byref(out), None) == bad
+    ok_fluid = pkg.msmg_fluid(0.3, 3.0, 0.2, 0.2)
+    # empty problem, missing fluid, residual saturations summing to one, non-positive viscosity
+    assert lib.msmg_impes_pressure_terms(0, ctypes.byref(ok_fluid), dummy, dummy, dummy, dummy, 4000.0,
+                                         dummy, dummy, dummy, None) == bad
+    assert lib.msmg_impes_pressure_terms(8, None, dummy, dummy, dummy, dummy, 4000.0, dummy, dummy, dummy,
+                                         None) == bad
+    for f in (pkg.msmg_fluid(0.3, 3.0, 0.5, 0.5), pkg.msmg_fluid(0.0, 3.0, 0.2, 0.2)):
+        assert lib.msmg_impes_pressure_terms(8, ctypes.byref(f), dummy, dummy, dummy, dummy, 4000.0, dummy,
+                                             dummy, dummy, None) == bad
+    # transport: no context, negative sub-step count, non-positive saturation step
+    assert lib.msmg_impes_transport(None, ctypes.byref(ok_fluid), dummy, dummy, dummy, 4000.0, dummy, dummy,
+                                    dummy, 1, 1e-3, ctypes.byref(out), None) == bad
+    assert lib.msmg_impes_transport(dummy, ctypes.byref(ok_fluid), dummy, dummy, dummy, 4000.0, dummy, dummy,
+                                    dummy, -1, 1e-3, ctypes.byref(out), None) == bad
+    assert lib.msmg_impes_transport(dummy, ctypes.byref(ok_fluid), dummy, dummy, dummy, 4000.0, dummy, dummy,
+                                    dummy, 1, 0.0, ctypes.byref(out), None) == bad
+    ms = (ctypes.c_double * 3)()
+    assert lib.msmg_net_forward(None, dummy, dummy, 4, None) == bad
+    assert lib.msmg_net_time_products(None, dummy, 4, ms, None) == bad
