@@ -608,6 +608,7 @@ class Solver:
         if cached is not None and opts.autotune:
             copts_opts = dataclasses.replace(opts, autotune=False)
         self.copts = copts_opts.to_c()
+        self.n_rhs = n_rhs
         nbytes = msmg_workspace_size(self.grid, self.copts, n_rhs)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=k.device)
         self.ctx, self.setup_status = msmg_setup(self.grid, k, self.copts, self.workspace, stream)
@@ -619,6 +620,29 @@ class Solver:
             c[key] = self.info["tuning"]
             with open(tuning_cache, "w") as fh:
                 json.dump(c, fh)
+
+    def refresh(self, kappa, cell_diag: torch.Tensor | None = None):
+        """Set up again for new coefficients on the same grid and hierarchy (new
+        permeability, new cell term), in the workspace already held: the step of a
+        time loop such as IMPES, where the operator changes every step."""
+        k = torch.as_tensor(kappa)
+        if not k.is_cuda:
+            k = k.to("cuda")
+        if k.dtype not in (torch.float64, torch.float32):
+            k = k.to(torch.float64)
+        k = k.contiguous()
+        if tuple(k.shape[-3:]) != self.shape:
+            raise ValueError("refresh keeps the grid: the permeability's shape differs")
+        if (cell_diag is None) != (self.opts.cell_diag is None):
+            raise ValueError("refresh keeps the options: a cell term must stay present or absent")
+        opts = dataclasses.replace(self.opts, cell_diag=cell_diag)
+        copts = opts.to_c()
+        if msmg_workspace_size(self.grid, copts, self.n_rhs) > self.workspace.numel():
+            raise ValueError("refresh needs a larger workspace than the solver holds")
+        self.close()
+        self.opts = opts            # keeps the cell term alive while the context uses it
+        self.copts = copts
+        self.ctx, self.setup_status = msmg_setup(self.grid, k, self.copts, self.workspace, self.stream)
 
     def close(self):
         if getattr(self, "ctx", None):

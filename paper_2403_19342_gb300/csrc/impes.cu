@@ -47,11 +47,22 @@ __global__ void k_pressure_terms(int64_t n, Fluid F, const double* __restrict__ 
   b[i] = q_inj[i] + wc * p_bh;
 }
 
+// f_w of every cell at the sub-step's saturation: one evaluation of the fluid
+// model per cell (the face fluxes read it for both sides of every face; evaluated
+// there, its four FP64 divisions per face side made a sub-step FP64-bound)
+__global__ void k_frac_flow(int64_t n, Fluid F, const double* __restrict__ S, double* __restrict__ fw) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double lam, f;
+    fluid_eval(F, S[i], &lam, &f);
+    fw[i] = f;
+  }
+}
+
 // dS/dt of every cell into rate (natural order) and max |dS/dt| -> sc[0] = dt
-__global__ void k_sat_rate(int nx, int ny, int nz, double hx, double hy, double hz, Fluid F,
+__global__ void k_sat_rate(int nx, int ny, int nz, double hx, double hy, double hz,
                            const double* __restrict__ v, const double* __restrict__ p, const double* __restrict__ w,
                            double p_bh, const double* __restrict__ q_inj, const double* __restrict__ phi,
-                           const double* __restrict__ S, double* __restrict__ rate, RedSlot red, double ds_max,
+                           const double* __restrict__ fw, double* __restrict__ rate, RedSlot red, double ds_max,
                            double* sc) {
   const int64_t n = (int64_t)nx * ny * nz;
   const int64_t st[3] = {1, nx, (int64_t)nx * ny};
@@ -60,24 +71,19 @@ __global__ void k_sat_rate(int nx, int ny, int nz, double hx, double hy, double 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int gc[3] = {(int)(i % nx), (int)((i / nx) % ny), (int)(i / ((int64_t)nx * ny))};
     const int nn[3] = {nx, ny, nz};
-    double lam, fwi;
-    fluid_eval(F, S[i], &lam, &fwi);
+    const double fwi = fw[i];
     double div = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       double fp = 0.0, fm = 0.0;
       if (gc[d] + 1 < nn[d]) {                       // +d face: upstream is i when v >= 0
         const double vf = v[(int64_t)d * n + i];
-        double l2, fw2;
-        if (vf >= 0.0) fw2 = fwi;
-        else fluid_eval(F, S[i + st[d]], &l2, &fw2);
+        const double fw2 = vf >= 0.0 ? fwi : fw[i + st[d]];
         fp = fw2 * vf;
       }
       if (gc[d] > 0) {                               // -d face = +d face of the -d neighbour
         const double vf = v[(int64_t)d * n + i - st[d]];
-        double l2, fw2;
-        if (vf >= 0.0) fluid_eval(F, S[i - st[d]], &l2, &fw2);
-        else fw2 = fwi;
+        const double fw2 = vf >= 0.0 ? fw[i - st[d]] : fwi;
         fm = fw2 * vf;
       }
       div += (fp - fm) / h[d];
@@ -153,13 +159,15 @@ int msmg_impes_transport(msmg_ctx* c, const msmg_fluid* fluid, const double* v, 
   const Fluid F{fluid->mu_w, fluid->mu_o, fluid->s_wc, fluid->s_or};
   const int64_t n = c->n;
   double* rate = c->sb.z;             // scratch: the solve buffers are free between solves
+  double* fw = c->sb.q;
   double* sc = c->dtmp + 12;          // [0] dt of the sub-step, [1] their sum
   unsigned grid = (unsigned)((n + 1023) / 1024);
   if (grid > 152 * 8) grid = 152 * 8;
   MSMG_CUDA_TRY(cudaMemsetAsync(sc, 0, 2 * sizeof(double), s));
   for (int m = 0; m < M; ++m) {
-    k_sat_rate<<<grid, 256, 0, s>>>(c->grid.nx, c->grid.ny, c->grid.nz, c->grid.hx, c->grid.hy, c->grid.hz, F, v, p,
-                                    w, p_bh, q_inj, phi, S, rate, c->red, ds_max, sc);
+    k_frac_flow<<<grid, 256, 0, s>>>(n, F, S, fw);
+    k_sat_rate<<<grid, 256, 0, s>>>(c->grid.nx, c->grid.ny, c->grid.nz, c->grid.hx, c->grid.hy, c->grid.hz, v, p, w,
+                                    p_bh, q_inj, phi, fw, rate, c->red, ds_max, sc);
     k_sat_update<<<grid, 256, 0, s>>>(n, S, rate, sc);
   }
   MSMG_CUDA_TRY(cudaGetLastError());

@@ -32,8 +32,7 @@ __global__ void k_eig_l1_jacobi(const double* __restrict__ T, const double* __re
   const int nb = bx * by * bz;
   double* A = sm;
   double* V = A + nb * nb;
-  double* A0 = V + nb * nb;
-  double* isq = A0 + nb * nb;
+  double* isq = V + nb * nb;
   double* cs = isq + nb;
   double* red = cs + nb + 2;
   int* pr = reinterpret_cast<int*>(red + 72);
@@ -64,8 +63,6 @@ __global__ void k_eig_l1_jacobi(const double* __restrict__ T, const double* __re
     A[c * nb + c] = diag * isq[c] * isq[c];
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) A0[i] = A[i];
-  __syncthreads();
   jacobi_eig(A, V, nb, cs, pr, red, 40, 1e-15);
   sort_diag(A, nb, order);
   // Phi = S^{-1/2} y for the L smallest; eigen-residual ||A~ y - theta y||
@@ -80,9 +77,26 @@ __global__ void k_eig_l1_jacobi(const double* __restrict__ T, const double* __re
     const int col = order[k];
     const double th = A[col * nb + col];
     double v[1] = {0.0};
+    // (A~ y)_c from the element's faces (the 7-point stencil), not from a dense copy
+    // of A~: two matrices in shared memory instead of three, so two CTAs share an SM
     for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-      double acc = -th * V[c * nb + col];
-      for (int j = 0; j < nb; ++j) acc += A0[c * nb + j] * V[j * nb + col];
+      const int lx = c % bx, ly = (c / bx) % by, lz = c / (bx * by);
+      const int lc[3] = {lx, ly, lz}, bd[3] = {bx, by, bz}, st[3] = {1, bx, bx * by};
+      double diag = 0.0, off = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        if (lc[d] + 1 < bd[d]) {
+          const double t = Te[(int64_t)d * n + c];
+          diag += t;
+          off += t * isq[c + st[d]] * V[(c + st[d]) * nb + col];
+        }
+        if (lc[d] > 0) {
+          const double t = Te[(int64_t)d * n + c - st[d]];
+          diag += t;
+          off += t * isq[c - st[d]] * V[(c - st[d]) * nb + col];
+        }
+      }
+      if (Wd) diag += Wd[e * nb + c];
+      const double acc = isq[c] * (diag * isq[c] * V[c * nb + col] - off) - th * V[c * nb + col];
       v[0] += acc * acc;
     }
     block_sum<1>(v, red + 2);
@@ -643,7 +657,7 @@ static size_t jac_smem(int n, int extra_mats) {
 int launch_level1_eigen(msmg_ctx* c, cudaStream_t s) {
   FineLevel& f = c->fine;
   if (f.nb > 96) return MSMG_ERR_UNSUPPORTED;   // large elements use the subspace solver
-  const size_t sm = jac_smem(f.nb, 3);
+  const size_t sm = jac_smem(f.nb, 2);
   cudaFuncSetAttribute(k_eig_l1_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_eig_l1_jacobi<<<(unsigned)f.m, 256, sm, s>>>(f.T, f.S, c->n, f.bx, f.by, f.bz, f.m, f.L, f.Phi, f.lam,
                                                   c->dtmp, f.Wd);

@@ -140,3 +140,32 @@ def test_impes_steps_against_oracle(pkg, precision):
         assert ep <= 1e-7 and eS <= 1e-8
         assert abs(dt_g - dt_o) <= 1e-6 * dt_o
         assert S_g.min().item() >= 0.2 - 1e-12 and S_g.max().item() <= 0.8 + 1e-12
+
+
+@pytest.mark.gpu
+def test_refresh_equals_a_fresh_setup(pkg):
+    # a time loop sets up again in the workspace it holds: the same bits as a new solver
+    kappa3, phi, wi, q = reservoir(5)
+    fg = pkg.make_fluid()
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    kg, wig, qg = t(kappa3), t(wi), t(q)
+    ke1, w1, b1 = pkg.msmg_impes_pressure_terms(fg, t(np.full(SHAPE, 0.2)), kg, wig, qg, P_BH)
+    ke2, w2, b2 = pkg.msmg_impes_pressure_terms(fg, t(np.linspace(0.2, 0.8, int(np.prod(SHAPE))).reshape(SHAPE)),
+                                                 kg, wig, qg, P_BH)
+    for precision in (0, 1):
+        Sol = pkg.Solver(ke1, opts(pkg, w1, precision)[0], h=H_CELL)
+        x1, _, _ = Sol.solve(b1, rtol=1e-10)
+        Sol.refresh(ke2, cell_diag=w2)
+        x_ref, info_r, _ = Sol.solve(b2, rtol=1e-10)
+        Sol.close()
+        Fresh = pkg.Solver(ke2, opts(pkg, w2, precision)[0], h=H_CELL)
+        x_new, info_n, _ = Fresh.solve(b2, rtol=1e-10)
+        Fresh.close()
+        assert info_r["iterations"] == info_n["iterations"]
+        assert torch.equal(x_ref, x_new)
+        with pytest.raises(ValueError):                 # the cell term must stay present
+            Fresh2 = pkg.Solver(ke2, opts(pkg, w2, precision)[0], h=H_CELL)
+            try:
+                Fresh2.refresh(ke1, cell_diag=None)
+            finally:
+                Fresh2.close()
