@@ -136,7 +136,7 @@ int plan_and_carve(const msmg_grid* g, const msmg_options* o, int n_rhs, Arena& 
   // common
   c->flags = ar.take<int>(16);
   c->kept = ar.take<unsigned long long>(kMaxLevels + 1);
-  c->dtmp = ar.take<double>(16 + nc * nc + 3 * nc + 64);
+  c->dtmp = ar.take<double>(16 + nc * nc + (4 * kGjBlock + 1) * nc + kGjBlock * kGjBlock + 64);
   // every reducing kernel launches at most one CTA per element and right-hand
   // side, or 1216 CTAs per right-hand side for the grid-stride vector kernels
   int64_t maxgrid = f.m;

@@ -181,6 +181,11 @@ struct SolveBuffers {
 
 }  // namespace msmg
 
+namespace msmg {
+// pivots per pass of the blocked Gauss-Jordan inversion of the coarsest matrix
+constexpr int kGjBlock = 4;
+}
+
 struct msmg_ctx {
   msmg_grid grid;
   msmg_options opts;

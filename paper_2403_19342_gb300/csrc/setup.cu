@@ -550,34 +550,104 @@ __global__ void k_add_null_shift(double* __restrict__ A, const double* __restric
   A[idx] += sigma * z[i] * z[j] / scal[0];
 }
 
-// Step k of the Gauss-Jordan inversion, in two launches.  The first takes the
-// pivot row and the multipliers of the pivot column: rowk[j] = A[k][j],
-// colk[i] = A[i][k] / A[k][k] (one division per row, not per element: FP64
-// division costs a dozen FP64 operations on GB300, and per element it made the
-// 16384-unknown inverse FP64-bound at 80 s); the second applies the rank-1
-// update with one FMA per element (n = 16384: 77 -> 19 s; a grid of one row
-// per CTA row measured slower than this flat one, 115 s).
-__global__ void k_gj_copy(const double* __restrict__ A, int64_t n, int64_t k, double* rowk, double* colk,
-                          double* stats) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double piv = A[k * n + k];
-  rowk[i] = A[k * n + i];
-  colk[i] = A[i * n + k] / piv;
-  if (i == 0 && !(piv > 0.0)) atomic_max_pos(&stats[1], 1.0);
+// Gauss-Jordan inversion in place (no pivoting: the matrix is symmetric positive
+// definite, shifted along its null vector when singular), kGjBlock pivots per pass
+// over the matrix, with the arithmetic of one pivot at a time.  Step k of the
+// single-pivot form: with c_i = A[i][k] / A[k][k] and r_j = A[k][j],
+//   A[i][j] = fma(-c_i, r_j, A[i][j]) for i, j != k,  A[k][j] = r_j / A[k][k],
+//   A[i][k] = -c_i,  A[k][k] = 1 / A[k][k].
+// For the pivots P = {k, .., k + b - 1} the first launch replays these b steps on
+// the rows and columns of P (thread j owns row P's entries in column j and column
+// P's entries in row j; every thread also replays the b x b pivot block) and
+// records each step's c and r; the second applies the b rank-1 updates to the
+// other entries in step order.  Every entry sees the same operations in the same
+// order as with one pivot per pass, so the bits are the same, with one sweep of
+// the matrix per b pivots instead of one per pivot (the 3740-unknown inverse of the
+// IMPES hierarchy: 224 ms with one pivot per pass).
+__global__ void k_gj_panel(const double* __restrict__ A, int64_t n, int64_t k, int b, double* __restrict__ cbuf,
+                           double* __restrict__ rbuf, double* __restrict__ rfin, double* __restrict__ cfin,
+                           double* __restrict__ ppfin, double* stats) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double PP[kGjBlock][kGjBlock];
+#pragma unroll
+  for (int s = 0; s < kGjBlock; ++s)
+#pragma unroll
+    for (int u = 0; u < kGjBlock; ++u) PP[s][u] = (s < b && u < b) ? A[(k + s) * n + k + u] : 0.0;
+  const bool act = j < n && !(j >= k && j < k + b);
+  double R[kGjBlock], Cj[kGjBlock];
+#pragma unroll
+  for (int s = 0; s < kGjBlock; ++s) {
+    R[s] = (act && s < b) ? A[(k + s) * n + j] : 0.0;
+    Cj[s] = (act && s < b) ? A[j * n + k + s] : 0.0;
+  }
+#pragma unroll
+  for (int t = 0; t < kGjBlock; ++t) {
+    if (t >= b) break;
+    const double piv = PP[t][t];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !(piv > 0.0)) atomic_max_pos(&stats[1], 1.0);
+    if (act) {
+      const double c = Cj[t] / piv, r = R[t];
+      cbuf[(int64_t)t * n + j] = c;
+      rbuf[(int64_t)t * n + j] = r;
+#pragma unroll
+      for (int s = 0; s < kGjBlock; ++s)
+        if (s < b && s != t) R[s] = fma(-(PP[s][t] / piv), r, R[s]);
+      R[t] = r / piv;
+#pragma unroll
+      for (int u = 0; u < kGjBlock; ++u)
+        if (u < b && u != t) Cj[u] = fma(-c, PP[t][u], Cj[u]);
+      Cj[t] = -c;
+    }
+    double cs[kGjBlock];
+#pragma unroll
+    for (int s = 0; s < kGjBlock; ++s) cs[s] = PP[s][t] / piv;
+#pragma unroll
+    for (int s = 0; s < kGjBlock; ++s)
+#pragma unroll
+      for (int u = 0; u < kGjBlock; ++u)
+        if (s < b && u < b && s != t && u != t) PP[s][u] = fma(-cs[s], PP[t][u], PP[s][u]);
+#pragma unroll
+    for (int u = 0; u < kGjBlock; ++u)
+      if (u < b && u != t) PP[t][u] = PP[t][u] / piv;
+#pragma unroll
+    for (int s = 0; s < kGjBlock; ++s)
+      if (s < b && s != t) PP[s][t] = -cs[s];
+    PP[t][t] = 1.0 / piv;
+  }
+  if (act) {
+#pragma unroll
+    for (int s = 0; s < kGjBlock; ++s)
+      if (s < b) {
+        rfin[(int64_t)s * n + j] = R[s];
+        cfin[j * kGjBlock + s] = Cj[s];
+      }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int s = 0; s < b; ++s)
+      for (int u = 0; u < b; ++u) ppfin[s * b + u] = PP[s][u];
 }
 
-__global__ void k_gj_update(double* __restrict__ A, int64_t n, int64_t k, const double* __restrict__ rowk,
-                            const double* __restrict__ colk) {
+__global__ void k_gj_block_update(double* __restrict__ A, int64_t n, int64_t k, int b,
+                                  const double* __restrict__ cbuf, const double* __restrict__ rbuf,
+                                  const double* __restrict__ rfin, const double* __restrict__ cfin,
+                                  const double* __restrict__ ppfin) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   const int64_t i = idx / n, j = idx % n;
-  const double piv = rowk[k];
+  const bool pi = i >= k && i < k + b, pj = j >= k && j < k + b;
   double v;
-  if (i == k && j == k) v = 1.0 / piv;
-  else if (i == k) v = rowk[j] / piv;
-  else if (j == k) v = -colk[i];
-  else v = fma(-colk[i], rowk[j], A[idx]);
+  if (pi && pj) {
+    v = ppfin[(i - k) * b + (j - k)];
+  } else if (pi) {
+    v = rfin[(i - k) * n + j];
+  } else if (pj) {
+    v = cfin[i * kGjBlock + (j - k)];
+  } else {
+    v = A[idx];
+#pragma unroll
+    for (int t = 0; t < kGjBlock; ++t)
+      if (t < b) v = fma(-cbuf[(int64_t)t * n + i], rbuf[(int64_t)t * n + j], v);
+  }
   A[idx] = v;
 }
 
@@ -728,9 +798,12 @@ int launch_coarsest(msmg_ctx* c, cudaStream_t s) {
   }
   const int64_t nk = lv.nk;
   double* B = c->dtmp + 16;
-  double* rowk = B + n * n;
-  double* colk = rowk + n;
-  double* w = colk + n;
+  double* cbuf = B + n * n;                  // [kGjBlock][n] each step's multipliers
+  double* rbuf = cbuf + kGjBlock * n;         // [kGjBlock][n] each step's pivot row
+  double* rfin = rbuf + kGjBlock * n;         // [kGjBlock][n] the pivot rows after the pass
+  double* cfin = rfin + kGjBlock * n;         // [n][kGjBlock] the pivot columns after the pass
+  double* ppfin = cfin + kGjBlock * n;        // [kGjBlock^2] the pivot block after the pass
+  double* w = ppfin + kGjBlock * kGjBlock;
   double* scal = c->dtmp + 4;
   MSMG_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)n * n * sizeof(double), s));
   k_assemble_dense<<<(unsigned)lv.me, 64, 0, s>>>(lv, B);
@@ -749,9 +822,10 @@ int launch_coarsest(msmg_ctx* c, cudaStream_t s) {
     k_coarsest_scalars<<<1, 256, 0, s>>>(B, z, nk, scal);
     k_add_null_shift<<<g2, 256, 0, s>>>(B, z, nk, scal);
   }
-  for (int64_t k = 0; k < nk; ++k) {
-    k_gj_copy<<<g1, 256, 0, s>>>(B, nk, k, rowk, colk, c->dtmp);
-    k_gj_update<<<g2, 256, 0, s>>>(B, nk, k, rowk, colk);
+  for (int64_t k = 0; k < nk; k += kGjBlock) {
+    const int b = (int)(nk - k < kGjBlock ? nk - k : kGjBlock);
+    k_gj_panel<<<g1, 256, 0, s>>>(B, nk, k, b, cbuf, rbuf, rfin, cfin, ppfin, c->dtmp);
+    k_gj_block_update<<<g2, 256, 0, s>>>(B, nk, k, b, cbuf, rbuf, rfin, cfin, ppfin);
   }
   if (singular) {
     k_gemv_z<<<(unsigned)((nk * 32 + 255) / 256), 256, 0, s>>>(B, z, nk, scal, w);
