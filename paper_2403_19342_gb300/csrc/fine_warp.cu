@@ -1,4 +1,5 @@
-// Fine-level PCG iteration kernels, one warp per element.
+// Fine-level PCG iteration kernels, one warp per element (two in the FP64 k_post
+// on 8^3 elements, see elem_threads).
 //
 // Each element of E_1 (bx x by x bz cells) is handled by one warp.  Its data is
 // one contiguous chunk of every block-major array; the warp stages what it
@@ -6,8 +7,9 @@
 // the inverse IC(0) pivots) in shared memory with asynchronous copies, all in
 // flight at once, then works out of shared memory.  The incomplete-Cholesky
 // solves of the block-Jacobi smoother (Section 5) sweep the element in
-// wavefronts lx + ly + lz = const; the lanes own the x-lines (ly, lz), so
-// consecutive wavefronts only need a warp-level barrier.
+// wavefronts lx + ly + lz = const; the element's threads take the cells of a
+// wavefront (dealt from a plane table, or on fixed x-lines, see w_ic0_s), so
+// consecutive wavefronts only need a barrier of the element's threads.
 //
 // The element shape is a template parameter: 8^3 and 4^3 elements are compiled
 // with constant geometry (index arithmetic folds to shifts, loops unroll);
